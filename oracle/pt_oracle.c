@@ -1,0 +1,737 @@
+/*
+ * pt_oracle.c -- plain CPU oracle for the P3T long-range force.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or helper
+ * with the CUDA library; the two meet only through the seeded input arrays.
+ *
+ * Everything is float64, written to be read against the paper:
+ *   Wang, Iwasawa, Nitadori & Makino (2020), "PeTar: a high-performance
+ *   N-body code for modelling massive collisional stellar systems".
+ *
+ *   Sec. 5.1, Eq. 11   Hamiltonian split: H_L carries G m_i m_j (1 - W)/r_ij
+ *   Sec. 6.1, Eq. 15   potential changeover W(x)
+ *   Sec. 6.1, Eq. 16   helper f(x), x = (r - r_in)/(r_out - r_in), Lambda
+ *   Sec. 6.1, Eq. 17   force changeover K(x)
+ *   Sec. 6.1, Eq. 18   W = f - f(1) r / r_out,  K = f - (x + r_in/(r_out-r_in)) f'
+ *   Sec. 4, Sec. 5.1 (Fig. 2)  Barnes-Hut tree; a cell "inside theta" acts
+ *                      as a super-particle (centre of mass + multipoles)
+ *   Sec. 6.4.2, Eqs. 30-31  quadrupole tensor and its traceless form
+ *   Sec. 6 (Fig. 3 schedule, step 2)  tree neighbour search within r_out
+ *
+ * Functions:
+ *   orc_f / orc_W / orc_K      changeover functions exactly as printed
+ *   orc_direct                 direct O(N^2) long-range acc and pot
+ *   orc_direct_short           direct short-range part (split-identity pin)
+ *   orc_neighbours_*           brute-force r_out neighbour sets
+ *   orc_tree_*                 keys, stable sort, octree, moments, groups,
+ *                              group-wise walk and tree force
+ *
+ * Readings where the paper is silent (the tree definition, the opening rule,
+ * the key scheme, the treatment of r <= r_in for the potential) are stated
+ * at each function.  Parity status: the changeover functions, the direct
+ * sum, the neighbour sets, keys/sort/topology and the theta = 0 tree are
+ * pinned by tests against closed forms, identities and brute force; the
+ * size of the tree-versus-direct truncation error has no printed value in
+ * the paper (parity unpinned for that magnitude; only its scaling is pinned).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_BITS 21                      /* grid bits per dimension       */
+#define ORC_GRID (1u << ORC_BITS)        /* 2^21 cells per dimension      */
+
+/* ------------------------------------------------------------------------ */
+/* Changeover functions, Sec. 6.1                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 16: f(x) = 1 + Lambda x^5 (14 - 28 x + 20 x^2 - 5 x^3). */
+double orc_f(double x, double lam)
+{
+    double x5 = x * x * x * x * x;
+    return 1.0 + lam * x5 * (14.0 - 28.0 * x + 20.0 * x * x - 5.0 * x * x * x);
+}
+
+/* Eq. 15: W(x) = Lambda (1 - 2x) for x <= 0, Lambda (1 - 2x) - 1 + f(x)
+ * for 0 < x < 1, and 0 for x >= 1. */
+double orc_W(double x, double lam)
+{
+    if (x <= 0.0) return lam * (1.0 - 2.0 * x);
+    if (x < 1.0) return lam * (1.0 - 2.0 * x) - 1.0 + orc_f(x, lam);
+    return 0.0;
+}
+
+/* Eq. 17: K(x) = 1 for x <= 0, (x-1)^4 (1 + 4x + 10x^2 + 20x^3 + 35 Lambda x^4)
+ * for 0 < x < 1, and 0 for x >= 1. */
+double orc_K(double x, double lam)
+{
+    if (x <= 0.0) return 1.0;
+    if (x < 1.0) {
+        double t = x - 1.0;
+        return t * t * t * t *
+               (1.0 + 4.0 * x + 10.0 * x * x + 20.0 * x * x * x + 35.0 * lam * x * x * x * x);
+    }
+    return 0.0;
+}
+
+/* Long-range pull of particle j (mass mj at xj) on the point xi, Eq. 11 with
+ * Eqs. 15-17, without the factor G:
+ *   acc += mj (xj - xi) (1 - K) / r^3,   pot += -mj (1 - W) / r.
+ * For r <= r_in (x <= 0) K = 1, so the force vanishes, and with
+ * W = Lambda (1 - 2x) the identity 1 - Lambda + 2 Lambda x = 2 r / (r_out + r_in)
+ * gives the constant (1 - W)/r = 2/(r_out + r_in); it is used in that form so
+ * that coincident particles (r = 0) give a finite potential. */
+static void pair_longrange(const double *xi, const double *xj, double mj,
+                           double r_in, double r_out, double *acc, double *pot)
+{
+    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double r = sqrt(r2);
+    double lam = (r_out - r_in) / (r_out + r_in);
+    double x = (r - r_in) / (r_out - r_in);
+    if (x <= 0.0) {
+        *pot += -mj * 2.0 / (r_out + r_in);
+        return;
+    }
+    double K = orc_K(x, lam), W = orc_W(x, lam);
+    double r3 = r2 * r;
+    acc[0] += mj * dx * (1.0 - K) / r3;
+    acc[1] += mj * dy * (1.0 - K) / r3;
+    acc[2] += mj * dz * (1.0 - K) / r3;
+    *pot += -mj * (1.0 - W) / r;
+}
+
+/* Short-range part (the H_S side of Eq. 11): acc += mj dx K / r^3,
+ * pot += -mj W / r, for r > 0.  Used only to pin the split identity. */
+static void pair_shortrange(const double *xi, const double *xj, double mj,
+                            double r_in, double r_out, double *acc, double *pot)
+{
+    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return;
+    double r = sqrt(r2);
+    double lam = (r_out - r_in) / (r_out + r_in);
+    double x = (r - r_in) / (r_out - r_in);
+    double K = orc_K(x, lam), W = orc_W(x, lam);
+    double r3 = r2 * r;
+    acc[0] += mj * dx * K / r3;
+    acc[1] += mj * dy * K / r3;
+    acc[2] += mj * dz * K / r3;
+    *pot += -mj * W / r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct summation (the plain definition the tree approximates)            */
+/* ------------------------------------------------------------------------ */
+
+/* For each target t (original index targets[t], or t itself when targets is
+ * NULL): a = G sum_{j != i} m_j (x_j - x_i)(1 - K)/r^3 and
+ * phi = -G sum_{j != i} m_j (1 - W)/r, j in ascending order. */
+void orc_direct(int64_t n, const double *pos, const double *mass, double G,
+                double r_in, double r_out, int64_t nt, const int64_t *targets,
+                double *acc, double *pot, int shortrange)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets ? targets[t] : t;
+        double a[3] = {0.0, 0.0, 0.0}, p = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            if (shortrange)
+                pair_shortrange(pos + 3 * i, pos + 3 * j, mass[j], r_in, r_out, a, &p);
+            else
+                pair_longrange(pos + 3 * i, pos + 3 * j, mass[j], r_in, r_out, a, &p);
+        }
+        acc[3 * t + 0] = G * a[0];
+        acc[3 * t + 1] = G * a[1];
+        acc[3 * t + 2] = G * a[2];
+        pot[t] = G * p;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour sets: j != i with r^2 < r_out^2, r^2 = dx*dx + dy*dy + dz*dz    */
+/* summed left to right (this file is compiled without FMA contraction).    */
+/* ------------------------------------------------------------------------ */
+
+static int is_neighbour(const double *xi, const double *xj, double rout2)
+{
+    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    return r2 < rout2;
+}
+
+/* counts[t] = number of neighbours of target t. */
+void orc_neighbours_count(int64_t n, const double *pos, double r_out, int64_t nt,
+                          const int64_t *targets, int64_t *counts)
+{
+    double rout2 = r_out * r_out;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets ? targets[t] : t, c = 0;
+        for (int64_t j = 0; j < n; j++)
+            if (j != i && is_neighbour(pos + 3 * i, pos + 3 * j, rout2)) c++;
+        counts[t] = c;
+    }
+}
+
+/* Fill idx[offsets[t] ..] with the neighbours of target t, ascending. */
+void orc_neighbours_fill(int64_t n, const double *pos, double r_out, int64_t nt,
+                         const int64_t *targets, const int64_t *offsets, int32_t *idx)
+{
+    double rout2 = r_out * r_out;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets ? targets[t] : t, c = offsets[t];
+        for (int64_t j = 0; j < n; j++)
+            if (j != i && is_neighbour(pos + 3 * i, pos + 3 * j, rout2)) idx[c++] = (int32_t)j;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree.  The paper uses the Barnes-Hut tree of FDPS without defining it;   */
+/* the definition below is this project's reading, fixed so that every      */
+/* structural decision is exactly reproducible:                             */
+/*   root box: o = per-dimension minimum, S = largest extent (1 if 0);       */
+/*   grid:     q_d = clamp(floor((x_d - o_d) * (2^21 / S)), 0, 2^21 - 1);     */
+/*   key:      21 bits per dimension interleaved, bit 3b+2 from q_x,         */
+/*             3b+1 from q_y, 3b from q_z;                                    */
+/*   order:    ascending key, equal keys by ascending original index;       */
+/*   nodes:    the root is all particles (level 0); a node of level l with   */
+/*             more than n_leaf particles and l < 21 is split into the       */
+/*             non-empty runs that share the top 3(l+1) key bits; otherwise  */
+/*             it is a leaf;                                                */
+/*   moments:  M, centre of mass, Q = sum m (3 d d^T - |d|^2 I) about the    */
+/*             centre of mass (Eq. 31 gives A' = Q / 2), and the tight box   */
+/*             of the particles' grid cells.                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t begin, count;       /* particle range in sorted order           */
+    int level, leaf;
+    int64_t first_child;        /* children are stored contiguously         */
+    int nchild;
+    uint32_t qmin[3], qmax[3];  /* tight box in grid cells (inclusive)      */
+    double M, com[3], Q[6];     /* Q order: xx, yy, zz, xy, xz, yz          */
+} orc_node;
+
+typedef struct {
+    int64_t begin, count;
+    uint32_t qmin[3], qmax[3];
+} orc_group;
+
+typedef struct {
+    int64_t n;
+    double origin[3], S, scale;
+    uint64_t *key;              /* per original index                       */
+    uint32_t *q;                /* per original index, 3 each               */
+    int64_t *perm;              /* sorted slot -> original index            */
+    double *spos, *smass;       /* sorted copies                            */
+    uint32_t *sq;               /* sorted grid coordinates                  */
+    uint64_t *skey;
+    orc_node *node;
+    int64_t nnodes, cap;
+    orc_group *group;
+    int64_t ngroups, gcap;
+    int n_leaf, n_group;
+} orc_tree;
+
+static uint64_t interleave(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    uint64_t k = 0;
+    for (int b = 0; b < ORC_BITS; b++) {
+        k |= (uint64_t)((qx >> b) & 1u) << (3 * b + 2);
+        k |= (uint64_t)((qy >> b) & 1u) << (3 * b + 1);
+        k |= (uint64_t)((qz >> b) & 1u) << (3 * b);
+    }
+    return k;
+}
+
+/* Root box and grid coordinates (this project's key scheme, see above). */
+static void compute_keys(orc_tree *t, const double *pos)
+{
+    int64_t n = t->n;
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; d++) { lo[d] = pos[d]; hi[d] = pos[d]; }
+    for (int64_t i = 1; i < n; i++)
+        for (int d = 0; d < 3; d++) {
+            double v = pos[3 * i + d];
+            if (v < lo[d]) lo[d] = v;
+            if (v > hi[d]) hi[d] = v;
+        }
+    double S = 0.0;
+    for (int d = 0; d < 3; d++) {
+        t->origin[d] = lo[d];
+        if (hi[d] - lo[d] > S) S = hi[d] - lo[d];
+    }
+    if (S == 0.0) S = 1.0;
+    t->S = S;
+    t->scale = (double)ORC_GRID / S;
+    for (int64_t i = 0; i < n; i++) {
+        for (int d = 0; d < 3; d++) {
+            double u = floor((pos[3 * i + d] - t->origin[d]) * t->scale);
+            if (u < 0.0) u = 0.0;
+            if (u > (double)(ORC_GRID - 1)) u = (double)(ORC_GRID - 1);
+            t->q[3 * i + d] = (uint32_t)u;
+        }
+        t->key[i] = interleave(t->q[3 * i], t->q[3 * i + 1], t->q[3 * i + 2]);
+    }
+}
+
+static const uint64_t *g_sort_keys;     /* comparator context (single thread) */
+static int cmp_key_then_index(const void *a, const void *b)
+{
+    int64_t ia = *(const int64_t *)a, ib = *(const int64_t *)b;
+    uint64_t ka = g_sort_keys[ia], kb = g_sort_keys[ib];
+    if (ka != kb) return ka < kb ? -1 : 1;
+    return ia < ib ? -1 : (ia > ib ? 1 : 0);
+}
+
+static int64_t node_alloc(orc_tree *t, int64_t k)
+{
+    if (t->nnodes + k > t->cap) {
+        int64_t nc = t->cap * 2 + k + 16;
+        t->node = (orc_node *)realloc(t->node, (size_t)nc * sizeof(orc_node));
+        t->cap = nc;
+    }
+    int64_t first = t->nnodes;
+    t->nnodes += k;
+    return first;
+}
+
+/* Moments of one node straight from its particles (two passes). */
+static void node_moments(orc_tree *t, orc_node *v)
+{
+    double M = 0.0, s[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < 3; d++) { v->qmin[d] = ORC_GRID; v->qmax[d] = 0; }
+    for (int64_t p = v->begin; p < v->begin + v->count; p++) {
+        double m = t->smass[p];
+        M += m;
+        for (int d = 0; d < 3; d++) {
+            s[d] += m * t->spos[3 * p + d];
+            uint32_t qd = t->sq[3 * p + d];
+            if (qd < v->qmin[d]) v->qmin[d] = qd;
+            if (qd > v->qmax[d]) v->qmax[d] = qd;
+        }
+    }
+    v->M = M;
+    for (int d = 0; d < 3; d++)
+        v->com[d] = (M > 0.0) ? s[d] / M : t->spos[3 * v->begin + d];
+    for (int k = 0; k < 6; k++) v->Q[k] = 0.0;
+    for (int64_t p = v->begin; p < v->begin + v->count; p++) {
+        double m = t->smass[p];
+        double d0 = t->spos[3 * p] - v->com[0];
+        double d1 = t->spos[3 * p + 1] - v->com[1];
+        double d2 = t->spos[3 * p + 2] - v->com[2];
+        double dd = d0 * d0 + d1 * d1 + d2 * d2;
+        v->Q[0] += m * (3.0 * d0 * d0 - dd);
+        v->Q[1] += m * (3.0 * d1 * d1 - dd);
+        v->Q[2] += m * (3.0 * d2 * d2 - dd);
+        v->Q[3] += m * (3.0 * d0 * d1);
+        v->Q[4] += m * (3.0 * d0 * d2);
+        v->Q[5] += m * (3.0 * d1 * d2);
+    }
+}
+
+/* The key digit (0..7) of sorted particle p at level l+1. */
+static int digit_at(const orc_tree *t, int64_t p, int l)
+{
+    return (int)((t->skey[p] >> (3 * (ORC_BITS - 1 - l))) & 7u);
+}
+
+/* Split node v (index vi) recursively per the node rule above. */
+static void build_node(orc_tree *t, int64_t vi)
+{
+    orc_node *v = &t->node[vi];
+    node_moments(t, v);
+    if (v->count <= t->n_leaf || v->level >= ORC_BITS) {
+        v->leaf = 1;
+        v->nchild = 0;
+        v->first_child = -1;
+        return;
+    }
+    int64_t b[9];
+    int64_t p = v->begin, end = v->begin + v->count;
+    int nch = 0;
+    int64_t cb[8], cc[8];
+    for (int c = 0; c < 8; c++) {
+        b[c] = p;
+        while (p < end && digit_at(t, p, v->level) == c) p++;
+        if (p > b[c]) { cb[nch] = b[c]; cc[nch] = p - b[c]; nch++; }
+    }
+    int64_t first = node_alloc(t, nch);
+    v = &t->node[vi];                     /* realloc may have moved it */
+    v->leaf = 0;
+    v->nchild = nch;
+    v->first_child = first;
+    int lev = v->level + 1;
+    for (int k = 0; k < nch; k++) {
+        orc_node *c = &t->node[first + k];
+        memset(c, 0, sizeof(*c));
+        c->begin = cb[k];
+        c->count = cc[k];
+        c->level = lev;
+    }
+    for (int k = 0; k < nch; k++) build_node(t, first + k);
+}
+
+/* Groups (this project's reading of "group-wise walk"): going down from the
+ * root, a node with at most n_group particles, or a leaf, is one group;
+ * otherwise its children are taken in key order, each child with more than
+ * n_group particles is handled recursively, and consecutive smaller children
+ * are packed greedily into groups of at most n_group particles. */
+static void group_emit(orc_tree *t, int64_t begin, int64_t count,
+                       const uint32_t *qmin, const uint32_t *qmax)
+{
+    if (t->ngroups == t->gcap) {
+        t->gcap = t->gcap * 2 + 16;
+        t->group = (orc_group *)realloc(t->group, (size_t)t->gcap * sizeof(orc_group));
+    }
+    orc_group *g = &t->group[t->ngroups++];
+    g->begin = begin;
+    g->count = count;
+    for (int d = 0; d < 3; d++) { g->qmin[d] = qmin[d]; g->qmax[d] = qmax[d]; }
+}
+
+static void build_groups(orc_tree *t, int64_t vi)
+{
+    const orc_node *v = &t->node[vi];
+    if (v->count <= t->n_group || v->leaf) {
+        group_emit(t, v->begin, v->count, v->qmin, v->qmax);
+        return;
+    }
+    int64_t pb = 0, pc = 0;
+    uint32_t pmin[3], pmax[3];
+    for (int k = 0; k < v->nchild; k++) {
+        const orc_node *c = &t->node[v->first_child + k];
+        if (c->count > t->n_group) {
+            if (pc) group_emit(t, pb, pc, pmin, pmax);
+            pc = 0;
+            build_groups(t, v->first_child + k);
+            continue;
+        }
+        if (pc && pc + c->count > t->n_group) {
+            group_emit(t, pb, pc, pmin, pmax);
+            pc = 0;
+        }
+        if (pc == 0) {
+            pb = c->begin;
+            for (int d = 0; d < 3; d++) { pmin[d] = c->qmin[d]; pmax[d] = c->qmax[d]; }
+        } else {
+            for (int d = 0; d < 3; d++) {
+                if (c->qmin[d] < pmin[d]) pmin[d] = c->qmin[d];
+                if (c->qmax[d] > pmax[d]) pmax[d] = c->qmax[d];
+            }
+        }
+        pc += c->count;
+    }
+    if (pc) group_emit(t, pb, pc, pmin, pmax);
+}
+
+static int cmp_group_begin(const void *a, const void *b)
+{
+    int64_t x = ((const orc_group *)a)->begin, y = ((const orc_group *)b)->begin;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass,
+                         int n_leaf, int n_group)
+{
+    orc_tree *t = (orc_tree *)calloc(1, sizeof(orc_tree));
+    t->n = n;
+    t->n_leaf = n_leaf;
+    t->n_group = n_group;
+    t->key = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    t->q = (uint32_t *)malloc((size_t)n * 3 * sizeof(uint32_t));
+    t->perm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    t->spos = (double *)malloc((size_t)n * 3 * sizeof(double));
+    t->smass = (double *)malloc((size_t)n * sizeof(double));
+    t->sq = (uint32_t *)malloc((size_t)n * 3 * sizeof(uint32_t));
+    t->skey = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    compute_keys(t, pos);
+    for (int64_t i = 0; i < n; i++) t->perm[i] = i;
+    g_sort_keys = t->key;
+    qsort(t->perm, (size_t)n, sizeof(int64_t), cmp_key_then_index);
+    for (int64_t s = 0; s < n; s++) {
+        int64_t i = t->perm[s];
+        for (int d = 0; d < 3; d++) {
+            t->spos[3 * s + d] = pos[3 * i + d];
+            t->sq[3 * s + d] = t->q[3 * i + d];
+        }
+        t->smass[s] = mass[i];
+        t->skey[s] = t->key[i];
+    }
+    int64_t root = node_alloc(t, 1);
+    memset(&t->node[root], 0, sizeof(orc_node));
+    t->node[root].begin = 0;
+    t->node[root].count = n;
+    t->node[root].level = 0;
+    build_node(t, root);
+    build_groups(t, root);
+    /* depth-first emission is already in key order; sorting makes it explicit */
+    qsort(t->group, (size_t)t->ngroups, sizeof(orc_group), cmp_group_begin);
+    return t;
+}
+
+void orc_tree_free(orc_tree *t)
+{
+    if (!t) return;
+    free(t->key); free(t->q); free(t->perm); free(t->spos); free(t->smass);
+    free(t->sq); free(t->skey); free(t->node); free(t->group);
+    free(t);
+}
+
+/* info[0] = n, info[1] = nodes, info[2] = groups, info[3] = max level;
+ * box[0..2] = origin, box[3] = S, box[4] = scale. */
+void orc_tree_info(const orc_tree *t, int64_t *info, double *box)
+{
+    int maxl = 0;
+    for (int64_t v = 0; v < t->nnodes; v++)
+        if (t->node[v].level > maxl) maxl = t->node[v].level;
+    info[0] = t->n; info[1] = t->nnodes; info[2] = t->ngroups; info[3] = maxl;
+    for (int d = 0; d < 3; d++) box[d] = t->origin[d];
+    box[3] = t->S; box[4] = t->scale;
+}
+
+void orc_tree_keys(const orc_tree *t, uint64_t *key, uint32_t *q, int64_t *perm)
+{
+    memcpy(key, t->key, (size_t)t->n * sizeof(uint64_t));
+    memcpy(q, t->q, (size_t)t->n * 3 * sizeof(uint32_t));
+    memcpy(perm, t->perm, (size_t)t->n * sizeof(int64_t));
+}
+
+/* Node table: ints[v*8 + {0..7}] = begin, count, level, leaf, first_child,
+ * nchild, -, -; q[v*6 + ...] = qmin xyz, qmax xyz; mom[v*10 + ...] = M,
+ * com xyz, Q xx yy zz xy xz yz. */
+void orc_tree_nodes(const orc_tree *t, int64_t *ints, uint32_t *q, double *mom)
+{
+    for (int64_t v = 0; v < t->nnodes; v++) {
+        const orc_node *c = &t->node[v];
+        int64_t *o = ints + 8 * v;
+        o[0] = c->begin; o[1] = c->count; o[2] = c->level; o[3] = c->leaf;
+        o[4] = c->first_child; o[5] = c->nchild; o[6] = 0; o[7] = 0;
+        for (int d = 0; d < 3; d++) { q[6 * v + d] = c->qmin[d]; q[6 * v + 3 + d] = c->qmax[d]; }
+        mom[10 * v] = c->M;
+        for (int d = 0; d < 3; d++) mom[10 * v + 1 + d] = c->com[d];
+        for (int k = 0; k < 6; k++) mom[10 * v + 4 + k] = c->Q[k];
+    }
+}
+
+/* groups: g[k*8 + {0..7}] = begin, count, qmin xyz, qmax xyz. */
+void orc_tree_groups(const orc_tree *t, int64_t *g)
+{
+    for (int64_t k = 0; k < t->ngroups; k++) {
+        const orc_group *p = &t->group[k];
+        int64_t *o = g + 8 * k;
+        o[0] = p->begin; o[1] = p->count;
+        for (int d = 0; d < 3; d++) { o[2 + d] = p->qmin[d]; o[5 + d] = p->qmax[d]; }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Group-wise walk.  A cell C is used as a super-particle for group G when   */
+/* both hold:                                                               */
+/*   (opening angle, Sec. 4 and Sec. 5.1) s^2 < theta^2 d^2, with s the side */
+/*   of C's geometric cube and d the distance from G's box to the cube's    */
+/*   centre, both in units of half a grid cell (so exact integers), and the */
+/*   product theta^2 d^2 formed in float64;                                  */
+/*   (changeover, Sec. 5.1, Eq. 11) every particle of C is at least r_out    */
+/*   from every particle of G, tested conservatively on grid cells: the     */
+/*   squared gap between the two boxes, in whole cells, is at least         */
+/*   floor((r_out * scale)^2) + 2.                                           */
+/* Otherwise a leaf's particles go to the particle-particle (PP) list and   */
+/* an internal cell is opened.  Children are visited in key order.         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t *cells, ncells, ccap;
+    int64_t *pp, npp, pcap;
+} walk_out;
+
+static int64_t rout_threshold(const orc_tree *t, double r_out)
+{
+    double R = r_out * t->scale;
+    double R2 = R * R;
+    if (R2 > 4.0e18) return (int64_t)4000000000000000000LL;  /* no gap that large */
+    return (int64_t)floor(R2) + 2;
+}
+
+static int accept_cell(const orc_group *G, const orc_node *C, double theta2, int64_t r2thr)
+{
+    int sh = ORC_BITS - C->level;
+    int64_t d2 = 0, gap2 = 0;
+    for (int d = 0; d < 3; d++) {
+        int64_t p = (int64_t)(C->qmin[d] >> sh);
+        int64_t c2 = (2 * p + 1) << sh;                 /* centre, half cells */
+        int64_t lo = 2 * (int64_t)G->qmin[d], hi = 2 * ((int64_t)G->qmax[d] + 1);
+        int64_t dd = 0;
+        if (lo - c2 > dd) dd = lo - c2;
+        if (c2 - hi > dd) dd = c2 - hi;
+        d2 += dd * dd;
+        int64_t g = 0;
+        int64_t g1 = (int64_t)C->qmin[d] - (int64_t)G->qmax[d] - 1;
+        int64_t g2 = (int64_t)G->qmin[d] - (int64_t)C->qmax[d] - 1;
+        if (g1 > g) g = g1;
+        if (g2 > g) g = g2;
+        gap2 += g * g;
+    }
+    double s = (double)((int64_t)1 << (ORC_BITS + 1 - C->level));  /* side, half cells */
+    if (!(s * s < theta2 * (double)d2)) return 0;
+    return gap2 >= r2thr;
+}
+
+static void walk_visit(const orc_tree *t, const orc_group *G, int64_t vi,
+                       double theta2, int64_t r2thr, walk_out *w)
+{
+    const orc_node *C = &t->node[vi];
+    if (accept_cell(G, C, theta2, r2thr)) {
+        if (w->cells && w->ncells < w->ccap) w->cells[w->ncells] = vi;
+        w->ncells++;
+        return;
+    }
+    if (C->leaf) {
+        for (int64_t p = C->begin; p < C->begin + C->count; p++) {
+            if (w->pp && w->npp < w->pcap) w->pp[w->npp] = p;
+            w->npp++;
+        }
+        return;
+    }
+    for (int k = 0; k < C->nchild; k++)
+        walk_visit(t, G, C->first_child + k, theta2, r2thr, w);
+}
+
+/* Lists of group g: cells (node indices) and PP (sorted particle indices).
+ * Returns 0, or 1 if a capacity was too small (counts are still complete). */
+int orc_tree_walk(const orc_tree *t, int64_t g, double theta, double r_out,
+                  int64_t *cells, int64_t ccap, int64_t *pp, int64_t pcap,
+                  int64_t *ncells, int64_t *npp)
+{
+    walk_out w = {cells, 0, ccap, pp, 0, pcap};
+    walk_visit(t, &t->group[g], 0, theta * theta, rout_threshold(t, r_out), &w);
+    *ncells = w.ncells;
+    *npp = w.npp;
+    return (w.ncells > ccap || w.npp > pcap) ? 1 : 0;
+}
+
+/* Newtonian pull of a cell on point xi, monopole plus (order 2) quadrupole
+ * about the centre of mass, without G; with d = xi - com, r = |d|:
+ *   phi = -M/r - d.Q.d / (2 r^5)
+ *   a   = -M d/r^3 + Q d / r^5 - (5/2) (d.Q.d) d / r^7. */
+static void cell_pull(const orc_node *C, const double *xi, int order, double *acc, double *pot)
+{
+    double d[3] = {xi[0] - C->com[0], xi[1] - C->com[1], xi[2] - C->com[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double r = sqrt(r2);
+    double r3 = r2 * r;
+    for (int k = 0; k < 3; k++) acc[k] += -C->M * d[k] / r3;
+    *pot += -C->M / r;
+    if (order >= 2) {
+        const double *Q = C->Q;     /* xx yy zz xy xz yz */
+        double Qd[3] = {Q[0] * d[0] + Q[3] * d[1] + Q[4] * d[2],
+                        Q[3] * d[0] + Q[1] * d[1] + Q[5] * d[2],
+                        Q[4] * d[0] + Q[5] * d[1] + Q[2] * d[2]};
+        double dQd = d[0] * Qd[0] + d[1] * Qd[1] + d[2] * Qd[2];
+        double r5 = r3 * r2, r7 = r5 * r2;
+        for (int k = 0; k < 3; k++) acc[k] += Qd[k] / r5 - 2.5 * dQd * d[k] / r7;
+        *pot += -dQd / (2.0 * r5);
+    }
+}
+
+/* Exposed for the truncation-scaling pin: pull of node v on point xi. */
+void orc_cell_pull(const orc_tree *t, int64_t v, const double *xi, int order,
+                   double *acc, double *pot)
+{
+    acc[0] = acc[1] = acc[2] = 0.0;
+    *pot = 0.0;
+    cell_pull(&t->node[v], xi, order, acc, pot);
+}
+
+/* Tree force on sorted particle s of group g, given g's lists. */
+static void tree_force_one(const orc_tree *t, int64_t s, const walk_out *w,
+                           double r_in, double r_out, double G, int order,
+                           double *acc, double *pot)
+{
+    double a[3] = {0.0, 0.0, 0.0}, p = 0.0;
+    const double *xi = t->spos + 3 * s;
+    for (int64_t k = 0; k < w->ncells; k++)
+        cell_pull(&t->node[w->cells[k]], xi, order, a, &p);
+    for (int64_t k = 0; k < w->npp; k++) {
+        int64_t j = w->pp[k];
+        if (j == s) continue;
+        pair_longrange(xi, t->spos + 3 * j, t->smass[j], r_in, r_out, a, &p);
+    }
+    for (int k = 0; k < 3; k++) acc[k] = G * a[k];
+    *pot = G * p;
+}
+
+static int64_t group_of(const orc_tree *t, int64_t s)
+{
+    int64_t lo = 0, hi = t->ngroups - 1;
+    while (lo < hi) {   /* last group with begin <= s (groups sorted by begin) */
+        int64_t mid = (lo + hi + 1) / 2;
+        if (t->group[mid].begin <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+
+static void walk_alloc(const orc_tree *t, int64_t g, double theta, double r_out, walk_out *w)
+{
+    walk_out c = {NULL, 0, 0, NULL, 0, 0};
+    walk_visit(t, &t->group[g], 0, theta * theta, rout_threshold(t, r_out), &c);
+    w->ccap = c.ncells; w->pcap = c.npp;
+    w->cells = (int64_t *)malloc((size_t)(c.ncells + 1) * sizeof(int64_t));
+    w->pp = (int64_t *)malloc((size_t)(c.npp + 1) * sizeof(int64_t));
+    w->ncells = 0; w->npp = 0;
+    walk_visit(t, &t->group[g], 0, theta * theta, rout_threshold(t, r_out), w);
+}
+
+/* Tree force.  With targets == NULL every particle is computed (one walk per
+ * group) and results are written per ORIGINAL index; otherwise target t is
+ * original index targets[t] and results go to slot t.  stats (optional):
+ * [0] cell interactions, [1] PP interactions (list entries times targets). */
+void orc_tree_force(orc_tree *t, double theta, double r_in, double r_out, double G,
+                    int order, int64_t nt, const int64_t *targets,
+                    double *acc, double *pot, int64_t *stats)
+{
+    int64_t ci = 0, pi = 0;
+    if (!targets) {
+        int64_t *inv = (int64_t *)malloc((size_t)t->n * sizeof(int64_t));
+        for (int64_t s = 0; s < t->n; s++) inv[s] = t->perm[s];
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : ci, pi)
+        for (int64_t g = 0; g < t->ngroups; g++) {
+            walk_out w;
+            walk_alloc(t, g, theta, r_out, &w);
+            const orc_group *grp = &t->group[g];
+            for (int64_t s = grp->begin; s < grp->begin + grp->count; s++) {
+                int64_t i = inv[s];
+                tree_force_one(t, s, &w, r_in, r_out, G, order, acc + 3 * i, pot + i);
+            }
+            ci += w.ncells * grp->count;
+            pi += w.npp * grp->count;
+            free(w.cells); free(w.pp);
+        }
+        free(inv);
+    } else {
+        int64_t *slot = (int64_t *)malloc((size_t)t->n * sizeof(int64_t));
+        for (int64_t s = 0; s < t->n; s++) slot[t->perm[s]] = s;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : ci, pi)
+        for (int64_t k = 0; k < nt; k++) {
+            int64_t s = slot[targets[k]];
+            int64_t g = group_of(t, s);
+            walk_out w;
+            walk_alloc(t, g, theta, r_out, &w);
+            tree_force_one(t, s, &w, r_in, r_out, G, order, acc + 3 * k, pot + k);
+            ci += w.ncells;
+            pi += w.npp;
+            free(w.cells); free(w.pp);
+        }
+        free(slot);
+    }
+    if (stats) { stats[0] = ci; stats[1] = pi; }
+}
+
+int orc_abi_version(void) { return 1; }

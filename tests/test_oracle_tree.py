@@ -1,0 +1,274 @@
+"""Pins for the oracle's keys, sort, octree, moments, groups, walk and tree force.
+
+Checks are against hand-derived values, brute force on tiny inputs, library
+routines (numpy stable argsort, scipy kd-tree), invariants of the walk, the
+paper's printed quadrupole of a binary (Sec. 6.4.2, Eqs. 36-38) and the
+expected truncation order of monopole and quadrupole expansions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_16560_gb300 import inputs
+
+BITS = 21
+
+
+def _bits_interleave(qx, qy, qz):
+    """Brute-force Morton interleave through binary strings."""
+    sx, sy, sz = (format(int(v), "021b") for v in (qx, qy, qz))
+    return int("".join(a + b + c for a, b, c in zip(sx, sy, sz)), 2)
+
+
+def test_keys_cube_corners():
+    """The 8 unit-cube corners: q is 0 or 2^21-1 per dimension, so the key of
+    corner (a, b, c) is (4a + 2b + c) * (8^21 - 1) / 7."""
+    pos = np.array([[a, b, c] for a in (0, 1) for b in (0, 1) for c in (0, 1)], float)
+    T = oracle.Tree(pos, np.ones(8), 1, 1)
+    key, q, perm = T.keys()
+    rep = (8 ** 21 - 1) // 7
+    for i, (a, b, c) in enumerate(pos.astype(int)):
+        assert int(key[i]) == (4 * a + 2 * b + c) * rep
+    assert list(perm) == list(range(8))
+    assert T.S == 1.0 and T.scale == 2.0 ** 21
+
+
+def test_keys_brute_force_small():
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 7, 64):
+        pos = rng.normal(size=(n, 3)) * rng.uniform(0.1, 10)
+        T = oracle.Tree(pos, np.ones(n), 4, 8)
+        key, q, perm = T.keys()
+        lo = pos.min(0)
+        S = float((pos.max(0) - lo).max()) or 1.0
+        scale = 2.0 ** 21 / S
+        for i in range(n):
+            qq = [min(max(math.floor((float(pos[i, d]) - float(lo[d])) * scale), 0), 2 ** 21 - 1)
+                  for d in range(3)]
+            assert list(q[i]) == qq
+            assert int(key[i]) == _bits_interleave(*qq)
+
+
+def test_sort_is_stable_argsort():
+    rng = np.random.default_rng(2)
+    pos = rng.integers(0, 4, size=(500, 3)).astype(float)   # many equal keys
+    T = oracle.Tree(pos, np.ones(500), 8, 16)
+    key, q, perm = T.keys()
+    assert np.array_equal(perm, np.argsort(key, kind="stable"))
+
+
+def _brute_nodes(skeys, n_leaf):
+    """All (level, begin, count) nodes from the run definition, by brute force."""
+    n = len(skeys)
+    out = set()
+    stack = [(0, 0, n)]
+    while stack:
+        lev, b, c = stack.pop()
+        out.add((lev, b, c))
+        if c <= n_leaf or lev == BITS:
+            continue
+        sh = 3 * (BITS - lev - 1)
+        pref = [int(k) >> sh for k in skeys[b:b + c]]
+        s = 0
+        for i in range(1, c + 1):
+            if i == c or pref[i] != pref[s]:
+                stack.append((lev + 1, b + s, i - s))
+                s = i
+    return out
+
+
+@pytest.mark.parametrize("n,n_leaf", [(1, 1), (2, 1), (64, 1), (64, 4), (200, 8), (150, 3)])
+def test_topology_brute_force(n, n_leaf):
+    rng = np.random.default_rng(n + n_leaf)
+    pos = rng.normal(size=(n, 3)) ** 3            # clustered, uneven
+    T = oracle.Tree(pos, np.ones(n), n_leaf, 4 * n_leaf)
+    key, q, perm = T.keys()
+    nd = T.nodes()
+    got = set(zip(nd["level"].tolist(), nd["begin"].tolist(), nd["count"].tolist()))
+    assert got == _brute_nodes(key[perm], n_leaf)
+    # children tile their parent in key order
+    for v in range(T.nnodes):
+        if nd["leaf"][v]:
+            assert nd["count"][v] <= n_leaf or nd["level"][v] == BITS
+            continue
+        fc, nc = nd["first_child"][v], nd["nchild"][v]
+        b = nd["begin"][v]
+        for c in range(fc, fc + nc):
+            assert nd["begin"][c] == b and nd["level"][c] == nd["level"][v] + 1
+            b += nd["count"][c]
+        assert b == nd["begin"][v] + nd["count"][v]
+
+
+def test_depth_cap_with_coincident_points():
+    pos = np.zeros((40, 3))
+    pos[20:] = 1.0
+    T = oracle.Tree(pos, np.ones(40), 4, 8)
+    nd = T.nodes()
+    leaves = nd["leaf"] == 1
+    assert set(nd["count"][leaves].tolist()) == {20}
+    assert set(nd["level"][leaves].tolist()) == {BITS}
+
+
+def test_moments_mass_com_and_traceless():
+    d = inputs.plummer(2000, 3, masses="kroupa")
+    T = oracle.Tree(d["pos"], d["mass"], 8, 32)
+    key, q, perm = T.keys()
+    nd = T.nodes()
+    sp, sm = d["pos"][perm], d["mass"][perm]
+    for v in range(0, T.nnodes, 7):
+        b, c = nd["begin"][v], nd["count"][v]
+        m, x = sm[b:b + c], sp[b:b + c]
+        assert nd["mass"][v] == pytest.approx(m.sum(), rel=1e-13)
+        np.testing.assert_allclose(nd["com"][v], (m[:, None] * x).sum(0) / m.sum(), rtol=1e-12, atol=1e-14)
+        Q = nd["quad"][v]
+        assert abs(Q[0] + Q[1] + Q[2]) <= 1e-12 * max(1e-300, np.abs(Q).max())
+        assert np.all(nd["qmin"][v] == q[perm[b:b + c]].min(0))
+        assert np.all(nd["qmax"][v] == q[perm[b:b + c]].max(0))
+
+
+def _quad_matrix(Q):
+    xx, yy, zz, xy, xz, yz = Q
+    return np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]])
+
+
+@pytest.mark.parametrize("e", [0.0, 0.3, 0.6, 0.95])
+def test_pseudoparticle_quadrupole_eq37_38(e):
+    """Sec. 6.4.2: three pseudoparticles of mass (m1+m2)/3 at Eq. 38 reproduce
+    the orbit-averaged traceless moment Eq. 37, <A'> = mu a^2/4 diag(9e^2+1,
+    1-6e^2, -3e^2-2).  The oracle's Q is 2 A' (Eq. 31)."""
+    m1, m2, a = 0.7, 0.4, 1.3
+    mu = m1 * m2 / (m1 + m2)
+    s = a * math.sqrt(mu / (m1 + m2))
+    pts = s * np.array([[0, math.sqrt(1 - e * e), 0],
+                        [math.sqrt(3 * e * e + 0.75), -math.sqrt((1 - e * e) / 4), 0],
+                        [-math.sqrt(3 * e * e + 0.75), -math.sqrt((1 - e * e) / 4), 0]])
+    T = oracle.Tree(pts, np.full(3, (m1 + m2) / 3), 8, 8)
+    Q = _quad_matrix(T.nodes()["quad"][0])
+    want = 0.25 * mu * a * a * np.diag([9 * e * e + 1, 1 - 6 * e * e, -3 * e * e - 2])
+    np.testing.assert_allclose(Q, 2 * want, atol=1e-14)
+
+
+@pytest.mark.parametrize("e", [0.0, 0.5, 0.9])
+def test_orbit_average_quadrupole_eq36(e):
+    """Sec. 6.4.2, Eq. 36: a binary sampled uniformly in time (mean anomaly)
+    has <A> = mu a^2 diag(2e^2 + 1/2, 1/2 - e^2/2, 0) about its centre of
+    mass; the oracle's moment of the sampled orbit is 3<A> - tr<A> I."""
+    m1, m2, a, K = 0.6, 0.25, 2.0, 4000
+    M = (np.arange(K) + 0.5) * 2 * math.pi / K
+    E = M.copy()
+    for _ in range(60):
+        E -= (E - e * np.sin(E) - M) / (1 - e * np.cos(E))
+    dr = np.stack([a * (np.cos(E) - e), a * math.sqrt(1 - e * e) * np.sin(E), 0 * E], 1)
+    pos = np.concatenate([-m2 / (m1 + m2) * dr, m1 / (m1 + m2) * dr])
+    mass = np.concatenate([np.full(K, m1 / K), np.full(K, m2 / K)])
+    T = oracle.Tree(pos, mass, 2 * K, 2 * K)
+    nd = T.nodes()
+    mu = m1 * m2 / (m1 + m2)
+    A = mu * a * a * np.diag([2 * e * e + 0.5, 0.5 - e * e / 2, 0.0])
+    # each sample pair has its centre of mass at the origin; the shift below
+    # (parallel axis) only guards against rounding in the computed COM
+    c = nd["com"][0]
+    A_c = A - (m1 + m2) * np.outer(c, c)
+    want = 3 * A_c - np.trace(A_c) * np.eye(3)
+    np.testing.assert_allclose(_quad_matrix(nd["quad"][0]), want, atol=2e-6 * np.abs(want).max())
+
+
+def test_groups_partition():
+    d = inputs.plummer(5000, 8)
+    for n_group in (1, 16, 64, 300):
+        T = oracle.Tree(d["pos"], d["mass"], 8, n_group)
+        g = T.groups()
+        nd = T.nodes()
+        assert g["begin"][0] == 0
+        assert np.all(g["begin"][1:] == g["begin"][:-1] + g["count"][:-1])
+        assert g["begin"][-1] + g["count"][-1] == 5000
+        big = g["count"] > n_group
+        # an oversized group is always a single leaf
+        leaves = {(b, c) for b, c, l in zip(nd["begin"], nd["count"], nd["leaf"]) if l}
+        for b, c in zip(g["begin"][big], g["count"][big]):
+            assert (b, c) in leaves
+
+
+def _brute_min_dist2(A, B):
+    return float(((A[:, None, :] - B[None, :, :]) ** 2).sum(2).min())
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.3, 0.5, 0.9])
+def test_walk_coverage_and_completeness(theta):
+    """Each particle is counted exactly once per group (cells + PP), every
+    pair closer than r_out is in PP, and accepted cells lie >= r_out away."""
+    d = inputs.plummer(1500, 6)
+    r_out = 0.08
+    T = oracle.Tree(d["pos"], d["mass"], 4, 24)
+    key, q, perm = T.keys()
+    sp = d["pos"][perm]
+    nd = T.nodes()
+    g = T.groups()
+    nb_off, nb_idx = oracle.neighbours(sp, r_out)
+    for k in range(0, T.ngroups, 3):
+        cells, pp = T.walk(k, theta, r_out)
+        if theta == 0.0:
+            assert len(cells) == 0
+        cover = np.zeros(1500, int)
+        np.add.at(cover, pp, 1)
+        for v in cells:
+            cover[nd["begin"][v]:nd["begin"][v] + nd["count"][v]] += 1
+        assert np.all(cover == 1)
+        b, c = g["begin"][k], g["count"][k]
+        inpp = np.zeros(1500, bool)
+        inpp[pp] = True
+        for s in range(b, b + c):
+            assert inpp[nb_idx[nb_off[s]:nb_off[s + 1]]].all()
+        for v in cells:
+            assert _brute_min_dist2(sp[b:b + c], sp[nd["begin"][v]:nd["begin"][v] + nd["count"][v]]) >= r_out ** 2
+
+
+def test_tree_theta0_equals_direct():
+    d = inputs.plummer(2048, 1)
+    acc, pot = oracle.direct_force(d["pos"], d["mass"], 0.005, 0.05)
+    T = oracle.Tree(d["pos"], d["mass"], 8, 64)
+    a, p, st = T.force(0.0, 0.005, 0.05, order=2)
+    assert st[0] == 0
+    rel = np.linalg.norm(a - acc, axis=1) / np.linalg.norm(acc, axis=1)
+    assert rel.max() < 1e-12
+    np.testing.assert_allclose(p, pot, rtol=1e-13)
+
+
+def test_tree_error_decreases_with_theta_and_order():
+    d = inputs.plummer(4096, 1)
+    acc, pot = oracle.direct_force(d["pos"], d["mass"], 0.005, 0.05)
+    T = oracle.Tree(d["pos"], d["mass"], 8, 64)
+    err = {}
+    for th in (0.3, 0.6):
+        for order in (0, 2):
+            a, p, _ = T.force(th, 0.005, 0.05, order=order)
+            err[th, order] = np.percentile(np.linalg.norm(a - acc, axis=1) / np.linalg.norm(acc, axis=1), 99)
+    assert err[0.3, 2] < err[0.3, 0] and err[0.6, 2] < err[0.6, 0]
+    assert err[0.3, 0] < err[0.6, 0] and err[0.3, 2] < err[0.6, 2]
+    assert err[0.6, 0] < 0.05
+
+
+def test_cell_truncation_order():
+    """A far cell's monopole error falls as (s/d)^2 and the quadrupole's as
+    (s/d)^3 against the exact Newtonian sum over its particles."""
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(-0.5, 0.5, (50, 3))
+    m = rng.uniform(0.5, 1.5, 50)
+    T = oracle.Tree(pts, m, 64, 64)
+    direction = np.array([0.48, 0.6, 0.64])
+    slopes = {}
+    for order in (0, 2):
+        e = []
+        ds = np.array([8.0, 16.0, 32.0, 64.0])
+        for dist in ds:
+            x = direction * dist
+            a, _ = T.cell_pull(0, x, order)
+            dd = pts - x
+            r = np.linalg.norm(dd, axis=1)
+            exact = (m[:, None] * dd / r[:, None] ** 3).sum(0)
+            e.append(np.linalg.norm(a - exact) / np.linalg.norm(exact))
+        slopes[order] = np.polyfit(np.log(ds), np.log(e), 1)[0]
+    assert slopes[0] == pytest.approx(-2.0, abs=0.25)
+    assert slopes[2] == pytest.approx(-3.0, abs=0.25)
