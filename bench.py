@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the P3T long-range force on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path on a resident particle set:
+root box + Morton keys -> radix sort -> octree -> multipoles -> groups ->
+group-wise walk (cell and PP lists) -> force kernel with neighbour
+extraction -> neighbour CSR -> energy / momentum sums, i.e. pt_tree_build
+followed by pt_longrange_force.
+
+Workload: Plummer sphere, N = 1,048,576, Kroupa IMF 0.08-150 Msun rescaled
+to M = 1, Henon units, seed 2; quadrupole tree, theta = 0.3, n_leaf = 16,
+n_group = 64, r_out = 0.003, r_in = 0.0003; neighbour lists on.
+
+value   = (cell + PP interactions per step) / device time per step of the
+          FP32-mixed path (interactions counted from the emitted lists:
+          sum over groups of n_G x list length)
+e2e     = the same metric through the C ABI with pinned HOST buffers, the
+          host<->device copies inside the timed region
+fp64    = the plain float64 GPU path on the same workload
+roofline: the mixed force kernel against the FP32 CUDA-core peak
+          (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.55 TFLOP/s), flops
+          per interaction counted from the kernel source
+cpu_baseline / --impl reference: the CPU oracle as it stands, on the host
+          cores, on a bounded sample of the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P³T long-range interactions/s at N=1M, FP32-mixed vs FP64 plain; p50/p99 latency"
+N_DEFAULT = 1_048_576
+SEED = 2
+
+# Flops per interaction, counted from the kernel source (FFMA = 2, other
+# arithmetic = 1, reciprocal square root = 4 by convention; min / max,
+# compares and selects are not counted).
+FLOPS = {
+    ("mixed", "cell", 2): 56, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 59,
+    ("fp64", "cell", 2): 56, ("fp64", "cell", 0): 22, ("fp64", "pp", None): 53,
+}
+SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maximum SM clock
+
+# DRAM bytes per launch of the mixed force kernel from one ncu capture of the
+# same kernel build on this workload (profiles/force_mixed_plummer1m.md);
+# None when the kernel changed after the capture.
+FORCE_MIXED_DRAM_BYTES = None
+
+
+def workload_config(n):
+    return {
+        "workload": f"Plummer N={n}, Kroupa IMF 0.08-150 Msun (total mass 1), Henon units, seed {SEED}; "
+                    "quadrupole tree theta=0.3, n_leaf=16, n_group=64, r_out=0.003, r_in=0.0003; "
+                    "neighbour lists on",
+        "n": n, "theta": 0.3, "n_leaf": 16, "n_group": 64, "order": 2, "r_out": 0.003, "r_in": 0.0003,
+        "l2": "flushed between timed steps (256 MiB write); working set > L2",
+        "parallelism": "replicas (one independent set per GPU, no collective)",
+    }
+
+
+def params(precision):
+    from paper_2006_16560_gb300 import binding as B
+    return B.Params(theta=0.3, r_in=0.0003, r_out=0.003, n_leaf=16, n_group=64, order=2,
+                    precision=precision)
+
+
+def flops_of(stats, kind):
+    return (stats["cell_interactions"] * FLOPS[(kind, "cell", 2)] +
+            stats["pp_interactions"] * FLOPS[(kind, "pp", None)])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def run_steps(ctx, tree_holder, pos, mass, prm, out, k, flush=None, timed=True):
+    """k steps of build + force on device buffers; per-step device times (ms)."""
+    import torch
+    from paper_2006_16560_gb300 import binding as B
+    acc, pot, nb_off, nb_idx = out
+    times, stats = [], None
+    stream = torch.cuda.current_stream()
+    for _ in range(k):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if tree_holder[0] is None:
+            tree_holder[0] = B.Tree(ctx, pos, mass, prm)
+        else:
+            tree_holder[0].rebuild(pos, mass, prm)
+        _, st, _ = tree_holder[0].force(acc, pot, nb_off, nb_idx, nb_idx.shape[0])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats = st.as_dict()
+    return times, stats
+
+
+def cpu_oracle_sample(pos, mass, nsample, seed=11):
+    """Oracle tree on the host cores: full build plus the tree force on
+    nsample targets; returns the interactions/s it would sustain on the whole
+    set, the seconds spent and the threads used."""
+    import oracle
+    n = len(mass)
+    t0 = time.perf_counter()
+    T = oracle.Tree(pos, mass, 16, 64)
+    t1 = time.perf_counter()
+    tg = np.random.default_rng(seed).choice(n, nsample, replace=False)
+    _, _, st = T.force(0.3, 0.0003, 0.003, order=2, targets=tg)
+    t2 = time.perf_counter()
+    inter = st[0] + st[1]
+    full_time = (t1 - t0) + (t2 - t1) * n / nsample
+    full_inter = inter * n / nsample
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return full_inter / full_time, t2 - t0, threads, inter
+
+
+def reference_main(args, rank, world):
+    """--impl reference: the CPU oracle as it stands on the host cores."""
+    if rank != 0:
+        return
+    from paper_2006_16560_gb300 import inputs
+    n = args.n
+    d = inputs.plummer(n, SEED, masses="kroupa")
+    ns = args.cpu_sample
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        v, s, thr, _ = cpu_oracle_sample(d["pos"], d["mass"], ns, seed=11 + i)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(s)
+    v = statistics.median(vals)
+    sample = (f"per step: oracle tree build over all {n} particles + oracle tree force on {ns} random "
+              f"targets, extrapolated to all targets")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "interactions/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n),
+            "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only-mixed", action="store_true", help="skip the FP64 and e2e legs (profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_main(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    n = args.n
+    d = inputs.plummer(n, SEED, masses="kroupa")
+    pos = torch.from_numpy(d["pos"]).cuda()
+    mass = torch.from_numpy(d["mass"]).cuda()
+    ctx = B.Context(local)
+    cap = 8 * n
+    out = (torch.empty((n, 3), dtype=torch.float64, device="cuda"),
+           torch.empty((n,), dtype=torch.float64, device="cuda"),
+           torch.empty((n + 1,), dtype=torch.int64, device="cuda"),
+           torch.empty((cap,), dtype=torch.int32, device="cuda"))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    prm_mx, prm_64 = params(B.PT_MIXED), params(B.PT_FP64)
+    holder = [None]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- mixed precision (the headline) ----
+    run_steps(ctx, holder, pos, mass, prm_mx, out, args.warmup, flush)
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        times, st = run_steps(ctx, holder, pos, mass, prm_mx, out, args.steps, flush)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    clocks = clk.summary()
+    acc_mx = out[0].cpu().numpy().copy()
+    pot_mx = out[1].cpu().numpy().copy()
+    nb_total = int(st["neighbours"])
+    ms_step = statistics.mean(times)
+    ms_max = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_max, op=dist.ReduceOp.MAX)
+    inter = st["cell_interactions"] + st["pp_interactions"]
+    value = world * inter / (ms_max.item() * 1e-3)
+    # force kernel alone (CUDA events on the launching stream, inside the library)
+    kernel_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(1.0)
+        _, s2 = run_steps(ctx, holder, pos, mass, prm_mx, out, 1)
+        kernel_ms.append(s2["ms_force"])
+    k_ms = statistics.mean(kernel_ms)
+    achieved = flops_of(st, "mixed") / (k_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max.item(),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed",
+        "data": "synthetic", "config": workload_config(n),
+        "particles_per_s": world * n / (ms_max.item() * 1e-3),
+        "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                       "wall_per_step": 1000 * t_wall / args.steps},
+        "interactions_per_step": inter, "neighbours": nb_total,
+        "stage_ms": {"build": st["ms_build"], "walk": st["ms_walk"], "force_kernel": k_ms,
+                     "force_call": st["ms_total"]},
+        "gpu_launches": int((st["launches_build"] + st["launches_force"]) * args.steps),
+        "clocks": clocks,
+    }
+    line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK / 1e12,
+                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK,
+                        "traffic": FORCE_MIXED_DRAM_BYTES,
+                        "kernel": "k_force_mixed<2,true>",
+                        "flops_per_interaction": {"cell_quadrupole": FLOPS[("mixed", "cell", 2)],
+                                                  "pp": FLOPS[("mixed", "pp", None)]},
+                        "peak_note": "FP32 CUDA-core peak at the 2070 MHz maximum SM clock "
+                                     "(152 SMs x 128 lanes x 2 flop)"}
+    if clocks.get("sm_mhz"):
+        line["roofline"]["frac_at_measured_clock"] = achieved / (SM_COUNT * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6)
+
+    if not args.only_mixed:
+        # ---- float64 path on the same workload ----
+        run_steps(ctx, holder, pos, mass, prm_64, out, 2, flush)
+        t64, st64 = run_steps(ctx, holder, pos, mass, prm_64, out, max(3, args.steps // 2), flush)
+        acc64 = out[0].cpu().numpy()
+        pot64 = out[1].cpu().numpy()
+        ms64 = statistics.mean(t64)
+        inter64 = st64["cell_interactions"] + st64["pp_interactions"]
+        e = np.linalg.norm(acc_mx - acc64, axis=1) / np.linalg.norm(acc64, axis=1)
+        ep = np.abs(pot_mx - pot64) / np.abs(pot64)
+        line["fp64"] = {"value": world * inter64 / (ms64 * 1e-3), "unit": "interactions/s",
+                        "ms_per_step": ms64, "force_kernel_ms": st64["ms_force"],
+                        "latency_ms": {"p50": float(np.percentile(t64, 50)),
+                                       "p99": float(np.percentile(t64, 99))}}
+        line["speedup_mixed_vs_fp64"] = ms64 / ms_step
+        line["mixed_error_vs_fp64"] = {"acc_p50": float(np.percentile(e, 50)),
+                                       "acc_p99": float(np.percentile(e, 99)),
+                                       "acc_max": float(e.max()),
+                                       "pot_p99": float(np.percentile(ep, 99))}
+    if not args.no_e2e and not args.only_mixed:
+        # ---- end to end through the C ABI with pinned host buffers ----
+        hp = torch.from_numpy(d["pos"]).pin_memory()
+        hm = torch.from_numpy(d["mass"]).pin_memory()
+        ha = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        hphi = torch.empty((n,), dtype=torch.float64).pin_memory()
+        hoff = torch.empty((n + 1,), dtype=torch.int64).pin_memory()
+        hidx = torch.empty((cap,), dtype=torch.int32).pin_memory()
+        hbuf = (ha.numpy(), hphi.numpy(), hoff.numpy(), hidx.numpy())
+        tree_h = B.Tree(ctx, hp.numpy(), hm.numpy(), prm_mx)
+        tree_h.force(*hbuf, cap)
+        te = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree_h.rebuild(hp.numpy(), hm.numpy(), prm_mx)
+            tot, ste, _ = tree_h.force(*hbuf, cap)
+            te.append(time.perf_counter() - t0)
+        inter_e = ste.cell_interactions + ste.pp_interactions
+        line["e2e"] = {"value": world * inter_e / statistics.mean(te), "unit": "interactions/s",
+                       "h2d_bytes_per_step": 32 * n,
+                       "d2h_bytes_per_step": 32 * n + 8 * (n + 1) + 4 * int(tot),
+                       "ms_per_step": 1000 * statistics.mean(te)}
+        tree_h.free()
+    if holder[0] is not None:
+        holder[0].free()
+    if rank == 0 and not args.no_cpu_baseline:
+        v, secs, thr, si = cpu_oracle_sample(d["pos"], d["mass"], args.cpu_sample)
+        line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": thr, "kind": "oracle",
+                                "sample": f"oracle tree build over all {n} particles + oracle tree force "
+                                          f"on {args.cpu_sample} random targets ({si} interactions, "
+                                          f"{secs:.1f} s), extrapolated to all targets"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

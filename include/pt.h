@@ -1,0 +1,217 @@
+/*
+ * pt.h -- C ABI of the GB300 P3T long-range force library (libpt.so).
+ *
+ * The library computes the long-range half of the P3T Hamiltonian split used
+ * by PeTar (Wang, Iwasawa, Nitadori & Makino 2020):
+ *
+ *   Sec. 5.1, Eq. 11:  H_L = -sum_{i<j} G m_i m_j (1 - W(r_ij)) / r_ij
+ *   Sec. 6.1, Eqs. 15-17: W(x), K(x) with x = (r - r_in)/(r_out - r_in)
+ *
+ * so that for every particle i
+ *
+ *   a_i   = G sum_j m_j (x_j - x_i) (1 - K(x_ij)) / r_ij^3
+ *   phi_i = -G sum_j m_j (1 - W(x_ij)) / r_ij       (j != i)
+ *
+ * with distant particles grouped into Barnes-Hut cells "inside theta"
+ * (Sec. 4; Sec. 5.1, Fig. 2) that act through their monopole and quadrupole
+ * (Sec. 6.4.2, Eqs. 30-31), and it returns the r_out neighbour lists that the
+ * short-range integrator consumes (Sec. 6, Fig. 3 step 2).
+ *
+ * Pipeline on one GPU (every step is a CUDA kernel of this library):
+ *   root box and 63-bit Morton keys -> LSD radix sort -> octree topology ->
+ *   bottom-up multipoles -> groups -> group-wise walk (cell and particle
+ *   lists) -> force kernel (FP64 or FP32-mixed) with fused neighbour
+ *   extraction -> neighbour CSR -> energy and momentum sums.
+ *
+ * The tree, group and walk definitions are fixed exactly (the paper does not
+ * define them); they are identical to the project's CPU oracle:
+ *   grid     q_d = clamp(floor((x_d - o_d) * 2^21 / S), 0, 2^21-1), o = box
+ *            minimum, S = largest box extent (1 if all points coincide);
+ *   keys     bit 3b+2 / 3b+1 / 3b of the key = bit b of q_x / q_y / q_z;
+ *   order    ascending key, ties by ascending original index;
+ *   nodes    level-l node = maximal run of sorted keys sharing the top 3l
+ *            bits; it is a leaf if it holds <= n_leaf particles or l = 21;
+ *   groups   a node with <= n_group particles, or a leaf, is a group; larger
+ *            nodes pack consecutive small children greedily (<= n_group);
+ *   walk     cell C is accepted for group G iff s^2 < theta^2 d^2 (s = side
+ *            of C's cube, d = distance from G's grid box to the cube centre,
+ *            both in half grid cells, product in float64) and the squared
+ *            gap between the grid boxes, in whole cells, is at least
+ *            floor((r_out * 2^21 / S)^2) + 2 (so no pair closer than r_out
+ *            is ever inside an accepted cell); otherwise leaves go to the
+ *            particle-particle (PP) list and internal cells are opened;
+ *   neighbours  j != i with dx*dx + dy*dy + dz*dz < r_out*r_out evaluated in
+ *            float64 left to right without fused multiply-add.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PT_OK (0) or one of the PT_ERR_* codes below; no
+ *     exception crosses the ABI.  pt_last_error() gives a message.
+ *   - Pointers may be device memory (cudaMalloc / torch tensors) or host
+ *     memory; the library detects which.  Host buffers are staged through
+ *     device memory inside the call.  The caller owns every buffer it passes.
+ *   - All work is ordered on the context's stream.  Calls that return counts
+ *     (pt_tree_build, pt_longrange_force, pt_batch_longrange_force)
+ *     synchronise that stream before returning.
+ *   - Layouts: positions are n x 3 float64, row-major (x, y, z per particle);
+ *     masses n float64 (>= 0); accelerations n x 3 float64; potentials n
+ *     float64; every output is in the caller's original particle order.
+ *   - The library owns its workspace (tree arrays, lists); it is sized on
+ *     first use and reused by later calls with the same or smaller sizes.
+ *   - There is no CPU fallback: without a usable GPU every call fails with
+ *     PT_ERR_CUDA.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PT_OK            0
+#define PT_ERR_ARG       1   /* bad argument: n < 1, theta < 0, r_in >= r_out,
+                                r_in < 0, n_leaf < 1, n_group < 1, order not
+                                0/2, non-finite position or negative mass   */
+#define PT_ERR_OOM       2   /* device allocation failed                     */
+#define PT_ERR_CAPACITY  3   /* nb_capacity too small; *nb_total holds the
+                                number needed; acc and pot are valid         */
+#define PT_ERR_TIMEOUT   4   /* a bounded device wait ran out                */
+#define PT_ERR_CUDA      5   /* CUDA runtime error                           */
+#define PT_ERR_INTERNAL  6   /* internal limit exceeded (message says which) */
+
+/* ---- precision of the pair arithmetic ---- */
+#define PT_FP64   0          /* everything in float64                        */
+#define PT_MIXED  1          /* float64 storage, group-relative float32 pair
+                                arithmetic with float-float accumulation     */
+
+typedef struct pt_ctx pt_ctx;
+typedef struct pt_tree pt_tree;
+
+/* Force parameters (Sec. 6.1 and Sec. 7.1.1, Table 2 use theta 0.3/0.5,
+ * quadrupole moments and r_out/r_in = 10).  r_in, r_out are the scalar
+ * changeover radii (the mass-dependent radii of Eq. 12 set mass_dependent). */
+typedef struct {
+    double theta;        /* opening angle, >= 0 (0 = direct sum via PP)      */
+    double r_in, r_out;  /* changeover radii, 0 <= r_in < r_out              */
+    double G;            /* gravitational constant (1 in Henon units)        */
+    int n_leaf;          /* max particles in a leaf (depth cap 21 aside)     */
+    int n_group;         /* max particles in a walk group                    */
+    int order;           /* 0 = monopole, 2 = monopole + quadrupole          */
+    int precision;       /* PT_FP64 or PT_MIXED                              */
+    int mass_dependent;  /* must be 0 (reserved for Eq. 12 radii)            */
+} pt_params;
+
+/* Counters and sums of one force evaluation. */
+typedef struct {
+    int64_t n;                  /* particles                                 */
+    int64_t nodes;              /* tree nodes                                */
+    int64_t groups;             /* walk groups                               */
+    int64_t max_level;          /* deepest tree level                        */
+    int64_t cell_list_total;    /* sum over groups of cell-list lengths      */
+    int64_t pp_list_total;      /* sum over groups of PP-list lengths        */
+    int64_t cell_interactions;  /* sum over groups of n_G * cell-list length */
+    int64_t pp_interactions;    /* sum over groups of n_G * PP-list length   */
+    int64_t neighbours;         /* total neighbour-list entries              */
+    double energy;              /* sum_i (1/2) m_i phi_i, float64            */
+    double momentum[3];         /* sum_i m_i a_i, float64                    */
+    double ms_build;            /* GPU time of the last tree build           */
+    double ms_walk;             /* GPU time of the walk                      */
+    double ms_force;            /* GPU time of the force kernel              */
+    double ms_total;            /* GPU time of the force call (walk..sums)   */
+    int64_t launches_build;     /* kernels launched by the last tree build   */
+    int64_t launches_force;     /* kernels launched by the force call        */
+} pt_stats;
+
+/* Creates a context on CUDA device `device`, ordering all work on `stream`
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ * *ctx receives the handle; destroy it with pt_ctx_destroy. */
+int pt_ctx_create(pt_ctx **ctx, int device, void *stream);
+
+/* Frees the context's workspace (waits for its stream first). */
+int pt_ctx_destroy(pt_ctx *ctx);
+
+/* Message of the last failing call on ctx (static storage in ctx). */
+const char *pt_last_error(const pt_ctx *ctx);
+
+/* Builds keys, sort order, octree, multipoles and groups for n particles
+ * (pos n x 3, mass n; host or device).  The tree keeps its own copies and
+ * the parameters; *tree receives it (reuse: pass the same *tree again to
+ * rebuild in place when its previous size suffices, else a new one is
+ * made).  Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA, PT_ERR_INTERNAL. */
+int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                  const pt_params *params, pt_tree **tree);
+
+/* Walks the tree, evaluates acc (n x 3) and pot (n), both in the caller's
+ * particle order, and, if nb_offsets is not NULL, the r_out neighbour lists
+ * as CSR: nb_offsets (n+1 int64) and nb_idx (nb_capacity int32 original
+ * indices, ascending within each row).  *nb_total (if not NULL) receives
+ * the number of entries.  If nb_capacity is too small the call returns
+ * PT_ERR_CAPACITY with acc, pot and *nb_total valid and the CSR untouched.
+ * stats may be NULL. */
+int pt_longrange_force(pt_ctx *ctx, pt_tree *tree, double *acc, double *pot,
+                       int64_t *nb_offsets, int32_t *nb_idx, int64_t nb_capacity,
+                       int64_t *nb_total, pt_stats *stats);
+
+/* Releases a tree. */
+int pt_tree_free(pt_tree *tree);
+
+/* One independent particle set in a batch. */
+typedef struct {
+    int64_t n;               /* particles (>= 1)                              */
+    const double *pos;       /* n x 3                                         */
+    const double *mass;      /* n                                             */
+    double r_in, r_out;      /* this set's changeover radii                   */
+    double *acc;             /* out: n x 3                                    */
+    double *pot;             /* out: n                                        */
+    int64_t *nb_offsets;     /* out: n+1, or NULL for no neighbour lists      */
+    int32_t *nb_idx;         /* out: nb_capacity entries (cluster-local ids)  */
+    int64_t nb_capacity;
+    int64_t nb_total;        /* out: entries needed                           */
+} pt_cluster_desc;
+
+/* Evaluates n_clusters independent sets in one pass of the pipeline: every
+ * stage runs once over all sets (one forest with one root per set), so one
+ * launch sequence serves the whole batch.  params->r_in/r_out are ignored in
+ * favour of each descriptor's radii.  All descriptor pointers must be of the
+ * same kind (all device or all host).  flags: PT_BATCH_GRAPH replays a CUDA
+ * graph of the launch sequence when the batch shape repeats.  stats, if not
+ * NULL, receives the totals over the batch. */
+#define PT_BATCH_GRAPH 1
+int pt_batch_longrange_force(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc,
+                             const pt_params *params, int flags, pt_stats *stats);
+
+/* ---- introspection (copies to HOST buffers; for tests and tools) ---- */
+
+/* info[0..4] = n, nodes, groups, max level, clusters;
+ * box (5 per cluster) = origin x, y, z, S, 2^21/S. */
+int pt_tree_info(pt_tree *tree, int64_t *info, double *box);
+
+/* keys[s] = key of sorted slot s; perm[s] = original index in slot s. */
+int pt_tree_keys(pt_tree *tree, uint64_t *keys, uint32_t *perm);
+
+/* Node table in level order: ints (8 per node) = begin, count, level, leaf,
+ * first_child, nchild, 0, 0; q (6 per node) = grid box min xyz, max xyz;
+ * mom (10 per node) = M, centre of mass xyz, Q xx yy zz xy xz yz with
+ * Q = sum m (3 d d^T - |d|^2 I) about the centre of mass. */
+int pt_tree_nodes(pt_tree *tree, int64_t *ints, uint32_t *q, double *mom);
+
+/* Groups in key order: g (8 per group) = begin, count, grid box min xyz,
+ * max xyz. */
+int pt_tree_groups(pt_tree *tree, int64_t *g);
+
+/* Interaction lists of the last pt_longrange_force on this tree:
+ * cell_off/pp_off (groups+1 int64), cells (node indices), pp (sorted
+ * particle indices), in the order the force kernel consumed them. */
+int pt_tree_lists(pt_tree *tree, int64_t *cell_off, uint32_t *cells,
+                  int64_t *pp_off, uint32_t *pp);
+
+/* Version of this ABI (1). */
+int pt_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H */

@@ -1,0 +1,319 @@
+"""ctypes binding of libpt.so (include/pt.h).
+
+The C functions keep their names (``pt_ctx_create``, ``pt_tree_build``,
+``pt_longrange_force``, ``pt_batch_longrange_force``, ...).  This module only
+marshals arguments: every step of the force pipeline runs in the library's
+CUDA kernels.  Buffers may be CUDA torch tensors (device pointers) or numpy
+arrays (host pointers); the library stages host buffers itself.
+
+There is no fallback: if libpt.so cannot be built or loaded, or no GPU is
+usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build_lib
+
+PT_OK, PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CAPACITY, PT_ERR_TIMEOUT, PT_ERR_CUDA, PT_ERR_INTERNAL = range(7)
+PT_FP64, PT_MIXED = 0, 1
+PT_BATCH_GRAPH = 1
+ERR_NAMES = {0: "PT_OK", 1: "PT_ERR_ARG", 2: "PT_ERR_OOM", 3: "PT_ERR_CAPACITY",
+             4: "PT_ERR_TIMEOUT", 5: "PT_ERR_CUDA", 6: "PT_ERR_INTERNAL"}
+
+
+class pt_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("G", C.c_double), ("n_leaf", C.c_int), ("n_group", C.c_int),
+                ("order", C.c_int), ("precision", C.c_int), ("mass_dependent", C.c_int)]
+
+
+class pt_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nodes", C.c_int64), ("groups", C.c_int64),
+                ("max_level", C.c_int64), ("cell_list_total", C.c_int64),
+                ("pp_list_total", C.c_int64), ("cell_interactions", C.c_int64),
+                ("pp_interactions", C.c_int64), ("neighbours", C.c_int64),
+                ("energy", C.c_double), ("momentum", C.c_double * 3),
+                ("ms_build", C.c_double), ("ms_walk", C.c_double), ("ms_force", C.c_double),
+                ("ms_total", C.c_double), ("launches_build", C.c_int64),
+                ("launches_force", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "momentum"}
+        d["momentum"] = list(self.momentum)
+        return d
+
+
+class pt_cluster_desc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("mass", C.c_void_p),
+                ("r_in", C.c_double), ("r_out", C.c_double), ("acc", C.c_void_p),
+                ("pot", C.c_void_p), ("nb_offsets", C.c_void_p), ("nb_idx", C.c_void_p),
+                ("nb_capacity", C.c_int64), ("nb_total", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libpt.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_lib.build()
+            L = C.CDLL(path)
+            P, I64, I = C.c_void_p, C.c_int64, C.c_int
+            sigs = {
+                "pt_abi_version": (I, []),
+                "pt_ctx_create": (I, [C.POINTER(P), I, P]),
+                "pt_ctx_destroy": (I, [P]),
+                "pt_last_error": (C.c_char_p, [P]),
+                "pt_tree_build": (I, [P, I64, P, P, C.POINTER(pt_params), C.POINTER(P)]),
+                "pt_longrange_force": (I, [P, P, P, P, P, P, I64, C.POINTER(I64), C.POINTER(pt_stats)]),
+                "pt_tree_free": (I, [P]),
+                "pt_batch_longrange_force": (I, [P, I, C.POINTER(pt_cluster_desc), C.POINTER(pt_params), I,
+                                                 C.POINTER(pt_stats)]),
+                "pt_tree_info": (I, [P, P, P]),
+                "pt_tree_keys": (I, [P, P, P]),
+                "pt_tree_nodes": (I, [P, P, P, P]),
+                "pt_tree_groups": (I, [P, P]),
+                "pt_tree_lists": (I, [P, P, P, P, P]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+# ---- the C entry points under their own names ------------------------------
+
+def pt_ctx_create(device: int = 0, stream: int | None = None):
+    h = C.c_void_p()
+    rc = lib().pt_ctx_create(C.byref(h), device, stream)
+    if rc != PT_OK:
+        raise PTError(rc, "pt_ctx_create failed (is a CUDA device available?)")
+    return h
+
+
+def pt_ctx_destroy(ctx) -> int:
+    return lib().pt_ctx_destroy(ctx)
+
+
+def pt_last_error(ctx) -> str:
+    s = lib().pt_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def pt_tree_build(ctx, n, pos_ptr, mass_ptr, params: pt_params, tree=None):
+    h = tree if tree is not None else C.c_void_p()
+    rc = lib().pt_tree_build(ctx, n, pos_ptr, mass_ptr, C.byref(params), C.byref(h))
+    return rc, h
+
+
+def pt_longrange_force(ctx, tree, acc_ptr, pot_ptr, nb_off_ptr, nb_idx_ptr, nb_capacity):
+    tot = C.c_int64(0)
+    st = pt_stats()
+    rc = lib().pt_longrange_force(ctx, tree, acc_ptr, pot_ptr, nb_off_ptr, nb_idx_ptr,
+                                  nb_capacity, C.byref(tot), C.byref(st))
+    return rc, tot.value, st
+
+
+def pt_tree_free(tree) -> int:
+    return lib().pt_tree_free(tree)
+
+
+def pt_batch_longrange_force(ctx, descs, params: pt_params, flags: int = 0):
+    arr = (pt_cluster_desc * len(descs))(*descs)
+    st = pt_stats()
+    rc = lib().pt_batch_longrange_force(ctx, len(descs), arr, C.byref(params), flags, C.byref(st))
+    return rc, arr, st
+
+
+class PTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ---- thin object wrappers ---------------------------------------------------
+
+def _ptr(x):
+    """Device pointer of a CUDA tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+@dataclass
+class Params:
+    theta: float = 0.5
+    r_in: float = 0.005
+    r_out: float = 0.05
+    G: float = 1.0
+    n_leaf: int = 8
+    n_group: int = 64
+    order: int = 2
+    precision: int = PT_FP64
+    mass_dependent: int = 0
+
+    def c(self) -> pt_params:
+        return pt_params(self.theta, self.r_in, self.r_out, self.G, self.n_leaf, self.n_group,
+                         self.order, self.precision, self.mass_dependent)
+
+
+class Context:
+    """A library context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        if stream is None:
+            stream = _current_stream()
+        self.h = pt_ctx_create(device, stream)
+
+    def check(self, rc: int, what: str):
+        if rc != PT_OK:
+            raise PTError(rc, f"{what}: {pt_last_error(self.h)}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            pt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree:
+    """A built tree (pt_tree) over one particle set."""
+
+    def __init__(self, ctx: Context, pos, mass, params: Params):
+        self.ctx = ctx
+        self.n = int(mass.shape[0])
+        self.params = params
+        self._cp = params.c()
+        rc, self.h = pt_tree_build(ctx.h, self.n, _ptr(pos), _ptr(mass), self._cp)
+        ctx.check(rc, "pt_tree_build")
+
+    def rebuild(self, pos, mass, params: Params | None = None):
+        if params is not None:
+            self.params = params
+            self._cp = params.c()
+        self.n = int(mass.shape[0])
+        rc, self.h = pt_tree_build(self.ctx.h, self.n, _ptr(pos), _ptr(mass), self._cp, self.h)
+        self.ctx.check(rc, "pt_tree_build")
+
+    def force(self, acc, pot, nb_offsets=None, nb_idx=None, nb_capacity: int = 0,
+              allow_capacity_error: bool = False):
+        rc, total, st = pt_longrange_force(self.ctx.h, self.h, _ptr(acc), _ptr(pot), _ptr(nb_offsets),
+                                           _ptr(nb_idx), nb_capacity)
+        if rc == PT_ERR_CAPACITY and allow_capacity_error:
+            return total, st, rc
+        self.ctx.check(rc, "pt_longrange_force")
+        return total, st, rc
+
+    # introspection (host numpy arrays)
+    def info(self):
+        info = np.zeros(5, dtype=np.int64)
+        box = np.zeros(5)
+        self.ctx.check(lib().pt_tree_info(self.h, info.ctypes.data, box.ctypes.data), "pt_tree_info")
+        return info, box
+
+    def keys(self):
+        k = np.zeros(self.n, dtype=np.uint64)
+        p = np.zeros(self.n, dtype=np.uint32)
+        self.ctx.check(lib().pt_tree_keys(self.h, k.ctypes.data, p.ctypes.data), "pt_tree_keys")
+        return k, p
+
+    def nodes(self) -> dict:
+        info, _ = self.info()
+        nn = int(info[1])
+        ints = np.zeros((nn, 8), dtype=np.int64)
+        q = np.zeros((nn, 6), dtype=np.uint32)
+        mom = np.zeros((nn, 10))
+        self.ctx.check(lib().pt_tree_nodes(self.h, ints.ctypes.data, q.ctypes.data, mom.ctypes.data),
+                       "pt_tree_nodes")
+        return {"begin": ints[:, 0], "count": ints[:, 1], "level": ints[:, 2], "leaf": ints[:, 3],
+                "first_child": ints[:, 4], "nchild": ints[:, 5], "qmin": q[:, :3], "qmax": q[:, 3:],
+                "mass": mom[:, 0], "com": mom[:, 1:4], "quad": mom[:, 4:10]}
+
+    def groups(self) -> dict:
+        info, _ = self.info()
+        ng = int(info[2])
+        g = np.zeros((ng, 8), dtype=np.int64)
+        self.ctx.check(lib().pt_tree_groups(self.h, g.ctypes.data), "pt_tree_groups")
+        return {"begin": g[:, 0], "count": g[:, 1], "qmin": g[:, 2:5], "qmax": g[:, 5:8]}
+
+    def lists(self, ncell_total: int, npp_total: int):
+        info, _ = self.info()
+        ng = int(info[2])
+        co = np.zeros(ng + 1, dtype=np.int64)
+        po = np.zeros(ng + 1, dtype=np.int64)
+        cells = np.zeros(max(ncell_total, 1), dtype=np.uint32)
+        pp = np.zeros(max(npp_total, 1), dtype=np.uint32)
+        self.ctx.check(lib().pt_tree_lists(self.h, co.ctypes.data, cells.ctypes.data, po.ctypes.data,
+                                           pp.ctypes.data), "pt_tree_lists")
+        return co, cells[:ncell_total], po, pp[:npp_total]
+
+    def free(self):
+        if getattr(self, "h", None):
+            pt_tree_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def longrange_force(ctx: Context, pos, mass, params: Params, neighbours: bool = True,
+                    nb_capacity: int | None = None):
+    """One-shot build + force on CUDA tensors; returns (acc, pot, nb_off, nb_idx, stats).
+
+    ``pos`` (n, 3) and ``mass`` (n,) are float64 CUDA tensors; the outputs are
+    float64 / int64 / int32 CUDA tensors in the input order.
+    """
+    import torch
+    n = int(mass.shape[0])
+    dev = pos.device
+    t = Tree(ctx, pos, mass, params)
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    pot = torch.empty((n,), dtype=torch.float64, device=dev)
+    nb_off = nb_idx = None
+    cap = 0
+    if neighbours:
+        cap = nb_capacity if nb_capacity is not None else max(4 * n, 1024)
+        nb_off = torch.empty((n + 1,), dtype=torch.int64, device=dev)
+        nb_idx = torch.empty((cap,), dtype=torch.int32, device=dev)
+    total, st, rc = t.force(acc, pot, nb_off, nb_idx, cap, allow_capacity_error=True)
+    if rc == PT_ERR_CAPACITY:
+        nb_idx = torch.empty((total,), dtype=torch.int32, device=dev)
+        total, st, rc = t.force(acc, pot, nb_off, nb_idx, total)
+    t.free()
+    if neighbours:
+        nb_idx = nb_idx[:total]
+    return acc, pot, nb_off, nb_idx, st.as_dict()

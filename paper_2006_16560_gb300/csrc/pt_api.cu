@@ -1,0 +1,770 @@
+// pt_api.cu -- the C ABI of libpt.so (include/pt.h): contexts, trees,
+// workspace management, host/device staging and the call sequence.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pt.h"
+#include "pt_kernels.cuh"
+
+using namespace pt;
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+struct pt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char err[512] = {0};
+    Status *h_status = nullptr;      // pinned
+    cudaEvent_t ev[8] = {};
+    pt_tree *batch_tree = nullptr;   // reused by pt_batch_longrange_force
+};
+
+namespace {
+
+int fail(pt_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(expr)                \
+    do {                         \
+        int r_ = (expr);         \
+        if (r_ != PT_OK) return r_; \
+    } while (0)
+
+// Grow-only device buffer.
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+int ensure(pt_ctx *ctx, Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return PT_OK;
+    b.release();
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        (void)cudaGetLastError();
+        return fail(ctx, PT_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return PT_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Tree
+// ---------------------------------------------------------------------------
+
+struct pt_tree {
+    pt_ctx *ctx = nullptr;
+    unsigned n = 0;
+    int nsets = 0;
+    pt_params prm{};
+    std::vector<SetInfo> h_sets;
+    // capacities
+    unsigned cap_n = 0, cap_nodes = 0, cap_sets = 0;
+    unsigned long long cap_cells = 0, cap_pp = 0, cap_pairs = 0, cap_sort = 0;
+    // device buffers
+    Buf status, sets, set_of, bmin, bmax, n_dev;
+    Buf in_pos, in_mass;                                   // staging for host inputs
+    Buf keys_in, vals_in, qbuf, skey, perm, sp64, spH, spL, sq;
+    Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, tmp_a, tmp_b;
+    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gpart;
+    Buf cells, pp;
+    Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
+    Buf sort_k2, sort_v2, sort_counts, scan_sums;
+    Buf out_acc, out_pot;                                  // staging for host outputs
+    // last results
+    Status h{};
+    bool built = false, lists_valid = false;
+    float ms_build = 0.f;
+    int launches_build = 0, launches_force = 0;
+
+    void release() {
+        Buf *all[] = {&status, &sets, &set_of, &bmin, &bmax, &n_dev, &in_pos, &in_mass, &keys_in,
+                      &vals_in, &qbuf, &skey, &perm, &sp64, &spH, &spL, &sq, &nd_a, &nd_b, &nd_r,
+                      &nd_c, &nd_q, &nd_t, &nd_f, &tmp_a, &tmp_b, &gflag, &gbegin, &gr_r, &gr_a,
+                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
+                      &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
+                      &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot};
+        for (Buf *b : all) b->release();
+    }
+};
+
+namespace {
+
+int check_params(pt_ctx *ctx, const pt_params *p) {
+    if (!p) return fail(ctx, PT_ERR_ARG, "params is NULL");
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta))
+        return fail(ctx, PT_ERR_ARG, "theta must be finite and >= 0 (got %g)", p->theta);
+    if (!(p->G > 0.0) || !std::isfinite(p->G)) return fail(ctx, PT_ERR_ARG, "G must be > 0");
+    if (p->n_leaf < 1) return fail(ctx, PT_ERR_ARG, "n_leaf must be >= 1");
+    if (p->n_group < 1) return fail(ctx, PT_ERR_ARG, "n_group must be >= 1");
+    if (p->order != 0 && p->order != 2) return fail(ctx, PT_ERR_ARG, "order must be 0 or 2");
+    if (p->precision != PT_FP64 && p->precision != PT_MIXED)
+        return fail(ctx, PT_ERR_ARG, "precision must be PT_FP64 or PT_MIXED");
+    if (p->mass_dependent != 0) return fail(ctx, PT_ERR_ARG, "mass_dependent radii are not available");
+    return PT_OK;
+}
+
+int check_radii(pt_ctx *ctx, double r_in, double r_out) {
+    if (!(r_in >= 0.0) || !(r_out > r_in) || !std::isfinite(r_out))
+        return fail(ctx, PT_ERR_ARG, "need 0 <= r_in < r_out (got r_in=%g r_out=%g)", r_in, r_out);
+    return PT_OK;
+}
+
+// Integer form of the opening test: the smallest d2 with s^2 < fl(theta^2 * d2)
+// for every level (see pt.h); INT64_MAX when no d2 in range qualifies.
+void walk_thresholds(double theta, WalkParams &wp) {
+    const double theta2 = theta * theta;
+    for (int l = 0; l < kLevels; l++) {
+        const double s = std::ldexp(1.0, kBits + 1 - l);
+        const double s2 = s * s;
+        long long thr = 0x7fffffffffffffffll;
+        if (theta2 > 0.0) {
+            const double est = s2 / theta2;
+            if (est < 1.0e15) {
+                long long d = (long long)std::floor(est) - 8;
+                if (d < 0) d = 0;
+                while (!(s2 < theta2 * (double)d)) d++;
+                thr = d;
+            }
+        }
+        wp.ithr[l] = thr;
+    }
+}
+
+ScanTmp scan_tmp_of(pt_tree *t) { return ScanTmp{t->scan_sums.as<unsigned long long>()}; }
+SortTmp sort_tmp_of(pt_tree *t) {
+    return SortTmp{t->sort_k2.as<unsigned long long>(), t->sort_v2.as<unsigned>(),
+                   t->sort_counts.as<unsigned>()};
+}
+
+int alloc_build(pt_tree *t, unsigned n, int nsets) {
+    pt_ctx *ctx = t->ctx;
+    if (t->cap_nodes == 0) {
+        unsigned long long c = 2ull * n / (unsigned)std::max(1, std::min(t->prm.n_leaf, 8)) +
+                               (unsigned long long)kLevels * nsets + 1024;
+        t->cap_nodes = (unsigned)std::min<unsigned long long>(c, 0x7fffffffull);
+    }
+    if (t->cap_nodes < (unsigned)nsets + 1024) t->cap_nodes = nsets + 1024;
+    const size_t N = n, C = t->cap_nodes, S = nsets;
+    TRY(ensure(ctx, t->status, sizeof(Status)));
+    TRY(ensure(ctx, t->sets, S * sizeof(SetInfo)));
+    TRY(ensure(ctx, t->set_of, nsets > 1 ? N * 4 : 16));
+    TRY(ensure(ctx, t->bmin, 3 * S * 8));
+    TRY(ensure(ctx, t->bmax, 3 * S * 8));
+    TRY(ensure(ctx, t->n_dev, 16));
+    TRY(ensure(ctx, t->keys_in, N * 8));
+    TRY(ensure(ctx, t->vals_in, N * 4));
+    TRY(ensure(ctx, t->qbuf, N * 16));
+    TRY(ensure(ctx, t->skey, N * 8));
+    TRY(ensure(ctx, t->perm, N * 4));
+    TRY(ensure(ctx, t->sp64, N * 32));
+    TRY(ensure(ctx, t->spH, N * 16));
+    TRY(ensure(ctx, t->spL, N * 16));
+    TRY(ensure(ctx, t->sq, N * 16));
+    TRY(ensure(ctx, t->nd_a, C * 16));
+    TRY(ensure(ctx, t->nd_b, C * 16));
+    TRY(ensure(ctx, t->nd_r, C * 8));
+    TRY(ensure(ctx, t->nd_c, C * 32));
+    TRY(ensure(ctx, t->nd_q, C * 64));
+    TRY(ensure(ctx, t->nd_t, C * 64));
+    TRY(ensure(ctx, t->nd_f, C * 64));
+    TRY(ensure(ctx, t->tmp_a, std::max(C, N) * 4));
+    TRY(ensure(ctx, t->tmp_b, std::max(C, N) * 4));
+    TRY(ensure(ctx, t->gflag, N * 4));
+    TRY(ensure(ctx, t->gbegin, N * 4));
+    TRY(ensure(ctx, t->gr_r, N * 8));
+    TRY(ensure(ctx, t->gr_a, N * 16));
+    TRY(ensure(ctx, t->gr_b, N * 16));
+    TRY(ensure(ctx, t->gr_nc, N * 4));
+    TRY(ensure(ctx, t->gr_np, N * 4));
+    TRY(ensure(ctx, t->gr_co, (N + 1) * 8));
+    TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
+    TRY(ensure(ctx, t->gpart, N * 32));
+    TRY(ensure(ctx, t->scan_sums, (kScanBlocks + 1) * 8));
+    TRY(ensure(ctx, t->sort_counts, 256 * kSortBlocks * 4));
+    t->cap_sort = std::max<unsigned long long>(t->cap_sort, N);
+    TRY(ensure(ctx, t->sort_k2, t->cap_sort * 8));
+    TRY(ensure(ctx, t->sort_v2, t->cap_sort * 4));
+    t->cap_n = n;
+    t->cap_sets = nsets;
+    return PT_OK;
+}
+
+BuildArgs build_args(pt_tree *t, const double *pos, const double *mass) {
+    BuildArgs A{};
+    A.n = t->n;
+    A.n_dev = t->n_dev.as<unsigned>();
+    A.nsets = t->nsets;
+    A.pos = pos;
+    A.mass = mass;
+    A.sets = t->sets.as<SetInfo>();
+    A.set_of = t->set_of.as<unsigned>();
+    A.bmin = t->bmin.as<unsigned long long>();
+    A.bmax = t->bmax.as<unsigned long long>();
+    A.keys_in = t->keys_in.as<unsigned long long>();
+    A.vals_in = t->vals_in.as<unsigned>();
+    A.qbuf = t->qbuf.as<uint4>();
+    A.skey = t->skey.as<unsigned long long>();
+    A.perm = t->perm.as<unsigned>();
+    A.sp64 = t->sp64.as<double4>();
+    A.spH = t->spH.as<float4>();
+    A.spL = t->spL.as<float4>();
+    A.sq = t->sq.as<uint4>();
+    A.cap_nodes = t->cap_nodes;
+    A.nd_a = t->nd_a.as<uint4>();
+    A.nd_b = t->nd_b.as<uint4>();
+    A.nd_r = t->nd_r.as<uint2>();
+    A.nd_c = t->nd_c.as<double4>();
+    A.nd_q = t->nd_q.as<double4>();
+    A.nd_t = t->nd_t.as<double4>();
+    A.nd_f = t->nd_f.as<float4>();
+    A.tmp_u32a = t->tmp_a.as<unsigned>();
+    A.tmp_u32b = t->tmp_b.as<unsigned>();
+    A.gflag = t->gflag.as<unsigned>();
+    A.gbegin = t->gbegin.as<unsigned>();
+    A.gr_r = t->gr_r.as<uint2>();
+    A.gr_a = t->gr_a.as<uint4>();
+    A.gr_b = t->gr_b.as<uint4>();
+    A.n_leaf = t->prm.n_leaf;
+    A.n_group = t->prm.n_group;
+    A.status = t->status.as<Status>();
+    A.scan_tmp = scan_tmp_of(t);
+    A.sort_tmp = sort_tmp_of(t);
+    return A;
+}
+
+int read_status(pt_tree *t) {
+    pt_ctx *ctx = t->ctx;
+    CK(cudaMemcpyAsync(ctx->h_status, t->status.p, sizeof(Status), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    t->h = *ctx->h_status;
+    return PT_OK;
+}
+
+// Build over t->n particles in t->nsets sets; pos/mass are device pointers.
+int run_build(pt_tree *t, const double *pos, const double *mass) {
+    pt_ctx *ctx = t->ctx;
+    for (int attempt = 0; attempt < 8; attempt++) {
+        TRY(alloc_build(t, t->n, t->nsets));
+        CK(cudaMemcpyAsync(t->sets.p, t->h_sets.data(), t->nsets * sizeof(SetInfo),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(t->n_dev.p, &t->n, 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(t->status.p, 0, sizeof(Status), ctx->stream));
+        CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+        t->launches_build = build_launch(build_args(t, pos, mass), ctx->stream);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+        TRY(read_status(t));
+        cudaEventElapsedTime(&t->ms_build, ctx->ev[0], ctx->ev[1]);
+        const unsigned f = t->h.flags;
+        if (f & kErrNonFinite) return fail(ctx, PT_ERR_ARG, "non-finite position or mass in the input");
+        if (f & kErrNegMass) return fail(ctx, PT_ERR_ARG, "negative mass in the input");
+        if (f & kErrNodeCap) {
+            unsigned long long c = 2ull * t->cap_nodes;
+            if (c > 0x7fffffffull) return fail(ctx, PT_ERR_INTERNAL, "tree node count exceeds 2^31");
+            t->cap_nodes = (unsigned)c;
+            t->nd_a.release();   // force re-allocation of node arrays
+            t->nd_b.release(); t->nd_r.release(); t->nd_c.release(); t->nd_q.release();
+            t->nd_t.release(); t->nd_f.release(); t->tmp_a.release(); t->tmp_b.release();
+            continue;
+        }
+        t->built = true;
+        t->lists_valid = false;
+        return PT_OK;
+    }
+    return fail(ctx, PT_ERR_INTERNAL, "tree build did not converge on a node capacity");
+}
+
+WalkArgs walk_args(pt_tree *t) {
+    WalkArgs A{};
+    A.nd_a = t->nd_a.as<uint4>();
+    A.nd_b = t->nd_b.as<uint4>();
+    A.nd_r = t->nd_r.as<uint2>();
+    A.gr_r = t->gr_r.as<uint2>();
+    A.gr_a = t->gr_a.as<uint4>();
+    A.gr_b = t->gr_b.as<uint4>();
+    A.sets = t->sets.as<SetInfo>();
+    walk_thresholds(t->prm.theta, A.wp);
+    A.gr_nc = t->gr_nc.as<unsigned>();
+    A.gr_np = t->gr_np.as<unsigned>();
+    A.gr_co = t->gr_co.as<unsigned long long>();
+    A.gr_po = t->gr_po.as<unsigned long long>();
+    A.cells = t->cells.as<unsigned>();
+    A.pp = t->pp.as<unsigned>();
+    A.cap_cells = t->cap_cells;
+    A.cap_pp = t->cap_pp;
+    A.st = t->status.as<Status>();
+    A.scan_tmp = scan_tmp_of(t);
+    return A;
+}
+
+ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
+    ForceArgs A{};
+    A.gr_r = t->gr_r.as<uint2>();
+    A.gr_a = t->gr_a.as<uint4>();
+    A.gr_nc = t->gr_nc.as<unsigned>();
+    A.gr_np = t->gr_np.as<unsigned>();
+    A.gr_co = t->gr_co.as<unsigned long long>();
+    A.gr_po = t->gr_po.as<unsigned long long>();
+    A.cells = t->cells.as<unsigned>();
+    A.pp = t->pp.as<unsigned>();
+    A.sp64 = t->sp64.as<double4>();
+    A.spH = t->spH.as<float4>();
+    A.spL = t->spL.as<float4>();
+    A.nd_c = t->nd_c.as<double4>();
+    A.nd_q = t->nd_q.as<double4>();
+    A.nd_f = t->nd_f.as<float4>();
+    A.sets = t->sets.as<SetInfo>();
+    A.perm = t->perm.as<unsigned>();
+    A.acc = acc;
+    A.pot = pot;
+    A.G = t->prm.G;
+    A.order = t->prm.order;
+    A.want_nb = want_nb ? 1 : 0;
+    A.pairs = t->pairs.as<uint2>();
+    A.pair_cap = t->cap_pairs;
+    A.gpart = t->gpart.as<double4>();
+    A.st = t->status.as<Status>();
+    return A;
+}
+
+int key_bits_for(unsigned n) {
+    unsigned long long nn = (unsigned long long)n * n;
+    int b = 1;
+    while (b < 64 && (1ull << b) < nn) b++;
+    return b;
+}
+
+NbArgs nb_args(pt_tree *t) {
+    NbArgs A{};
+    A.n = t->n;
+    A.perm = t->perm.as<unsigned>();
+    A.pairs = t->pairs.as<uint2>();
+    A.pair_cap = t->cap_pairs;
+    A.npairs_dev = t->npairs_dev.as<unsigned>();
+    A.keys = t->nb_keys.as<unsigned long long>();
+    A.keys_sorted = t->nb_keys_s.as<unsigned long long>();
+    A.vals = t->nb_vals.as<unsigned>();
+    A.vals_sorted = t->nb_vals_s.as<unsigned>();
+    A.nb_off = t->nb_off.as<long long>();
+    A.nb_idx = t->nb_idx.as<int>();
+    A.key_bits = key_bits_for(t->n);
+    A.st = t->status.as<Status>();
+    A.sort_tmp = sort_tmp_of(t);
+    return A;
+}
+
+int alloc_pairs(pt_tree *t, unsigned long long cap) {
+    pt_ctx *ctx = t->ctx;
+    if (cap < 1024) cap = 1024;
+    if (cap > 0x7fffffffull) cap = 0x7fffffffull;
+    if (t->cap_pairs >= cap && t->pairs.p) return PT_OK;
+    t->cap_pairs = cap;
+    TRY(ensure(ctx, t->pairs, cap * 8));
+    TRY(ensure(ctx, t->nb_keys, cap * 8));
+    TRY(ensure(ctx, t->nb_keys_s, cap * 8));
+    TRY(ensure(ctx, t->nb_vals, cap * 4));
+    TRY(ensure(ctx, t->nb_vals_s, cap * 4));
+    TRY(ensure(ctx, t->nb_idx, cap * 4));
+    TRY(ensure(ctx, t->npairs_dev, 16));
+    if (t->cap_sort < cap) {
+        t->cap_sort = cap;
+        TRY(ensure(ctx, t->sort_k2, cap * 8));
+        TRY(ensure(ctx, t->sort_v2, cap * 4));
+    }
+    return PT_OK;
+}
+
+// Walk + force (+ neighbour CSR) on a built tree; acc/pot are device
+// pointers in input order.  On return t->h holds the status.
+int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long long nb_cap_hint,
+              float *ms) {
+    pt_ctx *ctx = t->ctx;
+    cudaStream_t st = ctx->stream;
+    Status *dS = t->status.as<Status>();
+    TRY(ensure(ctx, t->nb_off, ((size_t)t->n + 1) * 8));
+    TRY(alloc_pairs(t, std::max<unsigned long long>(nb_cap_hint, 2ull * t->n)));
+    for (int attempt = 0; attempt < 4; attempt++) {
+        CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));
+        CK(cudaMemsetAsync(&dS->work, 0, sizeof(dS->work), st));
+        CK(cudaMemsetAsync(&dS->npairs, 0, sizeof(unsigned long long), st));
+        CK(cudaEventRecord(ctx->ev[2], st));
+        WalkArgs W = walk_args(t);
+        int nk = walk_launch(W, 0, st);
+        CK(cudaGetLastError());
+        TRY(read_status(t));
+        if (t->h.flags & kErrStack)
+            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %d pending nodes)", kWalkStack);
+        if (t->h.cell_total > t->cap_cells || !t->cells.p) {
+            t->cap_cells = t->h.cell_total + t->h.cell_total / 8 + 1024;
+            TRY(ensure(ctx, t->cells, t->cap_cells * 4));
+        }
+        if (t->h.pp_total > t->cap_pp || !t->pp.p) {
+            t->cap_pp = t->h.pp_total + t->h.pp_total / 8 + 1024;
+            TRY(ensure(ctx, t->pp, t->cap_pp * 4));
+        }
+        W = walk_args(t);
+        nk += walk_launch(W, 1, st);
+        CK(cudaEventRecord(ctx->ev[3], st));
+        ForceArgs F = force_args(t, acc, pot, want_nb);
+        nk += force_launch(F, t->prm.precision, st);
+        CK(cudaEventRecord(ctx->ev[4], st));
+        nk += force_reduce_launch(F, st);
+        if (want_nb) nk += nb_launch(nb_args(t), st);
+        t->launches_force = nk;
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ctx->ev[5], st));
+        TRY(read_status(t));
+        const unsigned f = t->h.flags;
+        if (f & kErrStack)
+            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %d pending nodes)", kWalkStack);
+        if (f & kErrListCap) continue;                  // cannot happen after sizing; retry
+        if (want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= nb_cap_hint) {
+            TRY(alloc_pairs(t, t->h.npairs + t->h.npairs / 8));
+            continue;
+        }
+        cudaEventElapsedTime(&ms[0], ctx->ev[2], ctx->ev[3]);
+        cudaEventElapsedTime(&ms[1], ctx->ev[3], ctx->ev[4]);
+        cudaEventElapsedTime(&ms[2], ctx->ev[2], ctx->ev[5]);
+        t->lists_valid = true;
+        return PT_OK;
+    }
+    return fail(ctx, PT_ERR_INTERNAL, "force evaluation did not converge on buffer capacities");
+}
+
+void fill_stats(pt_tree *t, pt_stats *s, const float *ms) {
+    if (!s) return;
+    const Status &h = t->h;
+    s->n = t->n;
+    s->nodes = h.nnodes;
+    s->groups = h.ngroups;
+    s->max_level = h.max_level;
+    s->cell_list_total = (int64_t)h.cell_total;
+    s->pp_list_total = (int64_t)h.pp_total;
+    s->cell_interactions = (int64_t)h.cell_inter;
+    s->pp_interactions = (int64_t)h.pp_inter;
+    s->neighbours = (int64_t)h.npairs;
+    s->energy = h.energy;
+    s->momentum[0] = h.mom[0];
+    s->momentum[1] = h.mom[1];
+    s->momentum[2] = h.mom[2];
+    s->ms_build = t->ms_build;
+    s->ms_walk = ms ? ms[0] : 0.0;
+    s->ms_force = ms ? ms[1] : 0.0;
+    s->ms_total = ms ? ms[2] : 0.0;
+    s->launches_build = t->launches_build;
+    s->launches_force = t->launches_force;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int pt_abi_version(void) { return 1; }
+
+int pt_ctx_create(pt_ctx **out, int device, void *stream) {
+    if (!out) return PT_ERR_ARG;
+    *out = nullptr;
+    pt_ctx *ctx = new (std::nothrow) pt_ctx;
+    if (!ctx) return PT_ERR_OOM;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return PT_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) {
+        delete ctx;
+        return PT_ERR_ARG;
+    }
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_status, sizeof(Status)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return PT_ERR_CUDA;
+    }
+    for (auto &e : ctx->ev) cudaEventCreate(&e);
+    *out = ctx;
+    return PT_OK;
+}
+
+int pt_ctx_destroy(pt_ctx *ctx) {
+    if (!ctx) return PT_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->batch_tree) pt_tree_free(ctx->batch_tree);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return PT_OK;
+}
+
+const char *pt_last_error(const pt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                  const pt_params *params, pt_tree **tree) {
+    if (!ctx) return PT_ERR_ARG;
+    ctx->err[0] = 0;
+    if (!tree) return fail(ctx, PT_ERR_ARG, "tree is NULL");
+    if (n < 1 || n > 0x7fffffffll) return fail(ctx, PT_ERR_ARG, "n must be in [1, 2^31) (got %lld)", (long long)n);
+    if (!pos || !mass) return fail(ctx, PT_ERR_ARG, "pos and mass must not be NULL");
+    TRY(check_params(ctx, params));
+    TRY(check_radii(ctx, params->r_in, params->r_out));
+    CK(cudaSetDevice(ctx->device));
+    pt_tree *t = *tree;
+    if (!t) {
+        t = new (std::nothrow) pt_tree;
+        if (!t) return fail(ctx, PT_ERR_OOM, "out of host memory");
+        *tree = t;
+    }
+    t->ctx = ctx;
+    t->n = (unsigned)n;
+    t->nsets = 1;
+    t->prm = *params;
+    SetInfo si{};
+    si.r_in = params->r_in;
+    si.r_out = params->r_out;
+    si.begin = 0;
+    si.n = (unsigned)n;
+    t->h_sets.assign(1, si);
+    const double *dpos = pos, *dmass = mass;
+    if (!is_device_ptr(pos)) {
+        TRY(ensure(ctx, t->in_pos, (size_t)n * 24));
+        CK(cudaMemcpyAsync(t->in_pos.p, pos, (size_t)n * 24, cudaMemcpyHostToDevice, ctx->stream));
+        dpos = t->in_pos.as<double>();
+    }
+    if (!is_device_ptr(mass)) {
+        TRY(ensure(ctx, t->in_mass, (size_t)n * 8));
+        CK(cudaMemcpyAsync(t->in_mass.p, mass, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
+        dmass = t->in_mass.as<double>();
+    }
+    return run_build(t, dpos, dmass);
+}
+
+int pt_longrange_force(pt_ctx *ctx, pt_tree *t, double *acc, double *pot, int64_t *nb_offsets,
+                       int32_t *nb_idx, int64_t nb_capacity, int64_t *nb_total, pt_stats *stats) {
+    if (!ctx) return PT_ERR_ARG;
+    ctx->err[0] = 0;
+    if (!t || !t->built) return fail(ctx, PT_ERR_ARG, "tree is NULL or not built");
+    if (!acc || !pot) return fail(ctx, PT_ERR_ARG, "acc and pot must not be NULL");
+    if (nb_offsets && (!nb_idx && nb_capacity > 0)) return fail(ctx, PT_ERR_ARG, "nb_idx is NULL");
+    if (nb_capacity < 0) return fail(ctx, PT_ERR_ARG, "nb_capacity < 0");
+    CK(cudaSetDevice(ctx->device));
+    const size_t n = t->n;
+    const bool dacc = is_device_ptr(acc), dpot = is_device_ptr(pot);
+    double *a = acc, *p = pot;
+    if (!dacc) {
+        TRY(ensure(ctx, t->out_acc, n * 24));
+        a = t->out_acc.as<double>();
+    }
+    if (!dpot) {
+        TRY(ensure(ctx, t->out_pot, n * 8));
+        p = t->out_pot.as<double>();
+    }
+    const bool want_nb = nb_offsets != nullptr;
+    float ms[3] = {0, 0, 0};
+    TRY(run_force(t, a, p, want_nb, (unsigned long long)nb_capacity, ms));
+    cudaStream_t st = ctx->stream;
+    if (!dacc) CK(cudaMemcpyAsync(acc, a, n * 24, cudaMemcpyDeviceToHost, st));
+    if (!dpot) CK(cudaMemcpyAsync(pot, p, n * 8, cudaMemcpyDeviceToHost, st));
+    int rc = PT_OK;
+    const unsigned long long npairs = t->h.npairs;
+    if (nb_total) *nb_total = want_nb ? (int64_t)npairs : 0;
+    if (want_nb) {
+        if (npairs > (unsigned long long)nb_capacity || npairs > t->cap_pairs) {
+            rc = fail(ctx, PT_ERR_CAPACITY, "neighbour lists need %llu entries, capacity %lld",
+                      npairs, (long long)nb_capacity);
+        } else {
+            cudaMemcpyKind k1 = is_device_ptr(nb_offsets) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            CK(cudaMemcpyAsync(nb_offsets, t->nb_off.p, (n + 1) * 8, k1, st));
+            if (npairs) {
+                cudaMemcpyKind k2 = is_device_ptr(nb_idx) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+                CK(cudaMemcpyAsync(nb_idx, t->nb_idx.p, npairs * 4, k2, st));
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    fill_stats(t, stats, ms);
+    return rc;
+}
+
+int pt_tree_free(pt_tree *t) {
+    if (!t) return PT_OK;
+    if (t->ctx) {
+        cudaSetDevice(t->ctx->device);
+        cudaStreamSynchronize(t->ctx->stream);
+    }
+    t->release();
+    delete t;
+    return PT_OK;
+}
+
+// ---- introspection --------------------------------------------------------
+
+int pt_tree_info(pt_tree *t, int64_t *info, double *box) {
+    if (!t || !t->built) return PT_ERR_ARG;
+    pt_ctx *ctx = t->ctx;
+    if (info) {
+        info[0] = t->n;
+        info[1] = t->h.nnodes;
+        info[2] = t->h.ngroups;
+        info[3] = t->h.max_level;
+        info[4] = t->nsets;
+    }
+    if (box) {
+        std::vector<SetInfo> s(t->nsets);
+        CK(cudaMemcpy(s.data(), t->sets.p, t->nsets * sizeof(SetInfo), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < t->nsets; k++) {
+            for (int d = 0; d < 3; d++) box[5 * k + d] = s[k].origin[d];
+            box[5 * k + 3] = s[k].S;
+            box[5 * k + 4] = s[k].scale;
+        }
+    }
+    return PT_OK;
+}
+
+int pt_tree_keys(pt_tree *t, uint64_t *keys, uint32_t *perm) {
+    if (!t || !t->built) return PT_ERR_ARG;
+    pt_ctx *ctx = t->ctx;
+    if (keys) CK(cudaMemcpy(keys, t->skey.p, (size_t)t->n * 8, cudaMemcpyDeviceToHost));
+    if (perm) CK(cudaMemcpy(perm, t->perm.p, (size_t)t->n * 4, cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+int pt_tree_nodes(pt_tree *t, int64_t *ints, uint32_t *q, double *mom) {
+    if (!t || !t->built) return PT_ERR_ARG;
+    pt_ctx *ctx = t->ctx;
+    const size_t nn = t->h.nnodes;
+    std::vector<uint4> a(nn), b(nn);
+    std::vector<uint2> r(nn);
+    std::vector<double4> c(nn), qq(2 * nn);
+    CK(cudaMemcpy(a.data(), t->nd_a.p, nn * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(b.data(), t->nd_b.p, nn * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(r.data(), t->nd_r.p, nn * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(c.data(), t->nd_c.p, nn * 32, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(qq.data(), t->nd_q.p, nn * 64, cudaMemcpyDeviceToHost));
+    for (size_t v = 0; v < nn; v++) {
+        if (ints) {
+            int64_t *o = ints + 8 * v;
+            o[0] = r[v].x;
+            o[1] = r[v].y;
+            o[2] = meta_level(a[v].w);
+            o[3] = meta_leaf(a[v].w);
+            o[4] = meta_leaf(a[v].w) ? -1 : (int64_t)b[v].w;
+            o[5] = meta_nchild(a[v].w);
+            o[6] = 0;
+            o[7] = 0;
+        }
+        if (q) {
+            uint32_t *o = q + 6 * v;
+            o[0] = a[v].x; o[1] = a[v].y; o[2] = a[v].z;
+            o[3] = b[v].x; o[4] = b[v].y; o[5] = b[v].z;
+        }
+        if (mom) {
+            double *o = mom + 10 * v;
+            o[0] = c[v].w; o[1] = c[v].x; o[2] = c[v].y; o[3] = c[v].z;
+            o[4] = qq[2 * v].x; o[5] = qq[2 * v].y; o[6] = qq[2 * v].z; o[7] = qq[2 * v].w;
+            o[8] = qq[2 * v + 1].x; o[9] = qq[2 * v + 1].y;
+        }
+    }
+    return PT_OK;
+}
+
+int pt_tree_groups(pt_tree *t, int64_t *g) {
+    if (!t || !t->built || !g) return PT_ERR_ARG;
+    pt_ctx *ctx = t->ctx;
+    const size_t ng = t->h.ngroups;
+    std::vector<uint2> r(ng);
+    std::vector<uint4> a(ng), b(ng);
+    CK(cudaMemcpy(r.data(), t->gr_r.p, ng * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(a.data(), t->gr_a.p, ng * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(b.data(), t->gr_b.p, ng * 16, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < ng; k++) {
+        int64_t *o = g + 8 * k;
+        o[0] = r[k].x; o[1] = r[k].y;
+        o[2] = a[k].x; o[3] = a[k].y; o[4] = a[k].z;
+        o[5] = b[k].x; o[6] = b[k].y; o[7] = b[k].z;
+    }
+    return PT_OK;
+}
+
+int pt_tree_lists(pt_tree *t, int64_t *cell_off, uint32_t *cells, int64_t *pp_off, uint32_t *pp) {
+    if (!t || !t->lists_valid) return PT_ERR_ARG;
+    pt_ctx *ctx = t->ctx;
+    const size_t ng = t->h.ngroups;
+    std::vector<unsigned long long> co(ng), po(ng);
+    CK(cudaMemcpy(co.data(), t->gr_co.p, ng * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(po.data(), t->gr_po.p, ng * 8, cudaMemcpyDeviceToHost));
+    if (cell_off) {
+        for (size_t k = 0; k < ng; k++) cell_off[k] = (int64_t)co[k];
+        cell_off[ng] = (int64_t)t->h.cell_total;
+    }
+    if (pp_off) {
+        for (size_t k = 0; k < ng; k++) pp_off[k] = (int64_t)po[k];
+        pp_off[ng] = (int64_t)t->h.pp_total;
+    }
+    if (cells && t->h.cell_total)
+        CK(cudaMemcpy(cells, t->cells.p, t->h.cell_total * 4, cudaMemcpyDeviceToHost));
+    if (pp && t->h.pp_total) CK(cudaMemcpy(pp, t->pp.p, t->h.pp_total * 4, cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+int pt_batch_longrange_force(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc,
+                             const pt_params *params, int flags, pt_stats *stats) {
+    (void)n_clusters; (void)desc; (void)params; (void)flags; (void)stats;
+    return fail(ctx, PT_ERR_INTERNAL, "pt_batch_longrange_force: not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,514 @@
+// pt_build.cu -- tree build kernels: root box, Morton keys, gather, octree
+// topology, bottom-up multipoles and walk groups.
+//
+// Every kernel reads its element count from device memory and runs on a
+// fixed grid (grid-stride loops), so the whole build is one data-independent
+// launch sequence on the context stream.
+#include "pt_kernels.cuh"
+
+namespace pt {
+
+constexpr int kT = 256;
+
+// ---------------------------------------------------------------------------
+// Sets (clusters) and the root box
+// ---------------------------------------------------------------------------
+
+// set_of[i] for every input particle (binary search over set begins).
+__global__ void k_set_of(const SetInfo *sets, int nsets, unsigned n, unsigned *set_of) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = nsets - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (sets[mid].begin <= i) lo = mid; else hi = mid - 1;
+        }
+        set_of[i] = (unsigned)lo;
+    }
+}
+
+__global__ void k_box_init(unsigned long long *bmin, unsigned long long *bmax, int nsets) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nsets; i += gridDim.x * blockDim.x) {
+        bmin[i] = ~0ull;
+        bmax[i] = 0ull;
+    }
+}
+
+// Per-set minimum and maximum of each coordinate (exact: min / max do not
+// depend on the order of reduction) plus input validation.
+__global__ void __launch_bounds__(kT) k_box(const double *pos, const double *mass, unsigned n,
+                                            const unsigned *set_of, unsigned long long *bmin,
+                                            unsigned long long *bmax, Status *st) {
+    unsigned bad = 0;
+    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        unsigned i = base + threadIdx.x;
+        bool valid = i < n;
+        unsigned s = valid ? (set_of ? set_of[i] : 0u) : 0xffffffffu;
+        double x[3] = {0, 0, 0};
+        if (valid) {
+            x[0] = pos[3ull * i];
+            x[1] = pos[3ull * i + 1];
+            x[2] = pos[3ull * i + 2];
+            double m = mass[i];
+            if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]) || !isfinite(m)) bad |= kErrNonFinite;
+            if (m < 0.0) bad |= kErrNegMass;
+        }
+        unsigned s0 = __shfl_sync(0xffffffffu, s, 0);
+        bool uniform = __all_sync(0xffffffffu, s == s0);
+        for (int d = 0; d < 3; d++) {
+            unsigned long long lo = valid ? dbl_to_ordered(x[d]) : ~0ull;
+            unsigned long long hi = valid ? dbl_to_ordered(x[d]) : 0ull;
+            if (uniform) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+                    unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+                    lo = a < lo ? a : lo;
+                    hi = b > hi ? b : hi;
+                }
+                if ((threadIdx.x & 31) == 0 && s0 != 0xffffffffu) {
+                    atomicMin(&bmin[3 * s0 + d], lo);
+                    atomicMax(&bmax[3 * s0 + d], hi);
+                }
+            } else if (valid) {
+                atomicMin(&bmin[3 * s + d], lo);
+                atomicMax(&bmax[3 * s + d], hi);
+            }
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(&st->flags, bad);
+}
+
+// S = largest extent (1 if zero), scale = 2^21 / S (IEEE division), and the
+// r_out gap threshold floor((r_out * scale)^2) + 2.
+__global__ void k_box_finalize(SetInfo *sets, int nsets, const unsigned long long *bmin,
+                               const unsigned long long *bmax) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsets) return;
+    double S = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double lo = ordered_to_dbl(bmin[3 * s + d]);
+        double hi = ordered_to_dbl(bmax[3 * s + d]);
+        sets[s].origin[d] = lo;
+        double e = __dsub_rn(hi, lo);
+        if (e > S) S = e;
+    }
+    if (S == 0.0) S = 1.0;
+    sets[s].S = S;
+    double scale = __ddiv_rn((double)kGrid, S);
+    sets[s].scale = scale;
+    double R = __dmul_rn(sets[s].r_out, scale);
+    double R2 = __dmul_rn(R, R);
+    sets[s].r2thr = (R2 > 4.0e18) ? 4000000000000000000ll : (long long)floor(R2) + 2;
+}
+
+// ---------------------------------------------------------------------------
+// Keys
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long spread3(unsigned v) {
+    // place bit b of v at bit 3b (21 bits)
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void __launch_bounds__(kT) k_keys(const double *pos, unsigned n, const unsigned *set_of,
+                                             const SetInfo *sets, unsigned long long *keys,
+                                             unsigned *vals, uint4 *qbuf) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned s = set_of ? set_of[i] : 0u;
+        const SetInfo &S = sets[s];
+        unsigned q[3];
+        for (int d = 0; d < 3; d++) {
+            double u = floor(__dmul_rn(__dsub_rn(pos[3ull * i + d], S.origin[d]), S.scale));
+            u = u < 0.0 ? 0.0 : u;
+            u = u > (double)(kGrid - 1) ? (double)(kGrid - 1) : u;
+            q[d] = (unsigned)u;
+        }
+        keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+        vals[i] = i;
+        qbuf[i] = make_uint4(q[0], q[1], q[2], s);
+    }
+}
+
+// Sorted particle records: float64 (x, y, z, m), float-float split of the
+// position for the mixed-precision path, and grid coordinates.
+__global__ void __launch_bounds__(kT) k_gather(const double *pos, const double *mass, unsigned n,
+                                               const unsigned *perm, const uint4 *qbuf,
+                                               double4 *sp64, float4 *spH, float4 *spL, uint4 *sq) {
+    for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        unsigned i = perm[p];
+        double x = pos[3ull * i], y = pos[3ull * i + 1], z = pos[3ull * i + 2], m = mass[i];
+        sp64[p] = make_double4(x, y, z, m);
+        float xh = __double2float_rn(x), yh = __double2float_rn(y), zh = __double2float_rn(z);
+        spH[p] = make_float4(xh, yh, zh, __double2float_rn(m));
+        spL[p] = make_float4(__double2float_rn(x - (double)xh), __double2float_rn(y - (double)yh),
+                             __double2float_rn(z - (double)zh), 0.0f);
+        sq[p] = qbuf[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Topology, level by level
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void level_range(const Status *st, int l, unsigned cap, unsigned &b,
+                                            unsigned &c) {
+    b = st->lvl_begin[l];
+    c = st->lvl_count[l];
+    if (b >= cap) { c = 0; return; }
+    if (c > cap - b) c = cap - b;
+}
+
+__global__ void k_topo_roots(const SetInfo *sets, int nsets, uint4 *nd_a, uint4 *nd_b,
+                             uint2 *nd_r, Status *st) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsets) {
+        nd_r[s] = make_uint2(sets[s].begin, sets[s].n);
+        nd_a[s] = make_uint4(0, 0, 0, make_meta(0, 0, 0));
+        nd_b[s] = make_uint4(0, 0, 0, 0);
+    }
+    if (s == 0) {
+        st->lvl_begin[0] = 0;
+        st->lvl_count[0] = (unsigned)nsets;
+        for (int l = 1; l <= kLevels; l++) {
+            st->lvl_begin[l] = 0;
+            st->lvl_count[l] = 0;
+        }
+    }
+}
+
+// Boundaries of the 8 key digits of level l+1 inside [b, b+c).
+__device__ __forceinline__ void child_bounds(const unsigned long long *skey, unsigned b, unsigned c,
+                                             int l, unsigned B[9]) {
+    const int sh = 3 * (kBits - 1 - l);
+    B[0] = b;
+    B[8] = b + c;
+    for (unsigned k = 1; k < 8; k++) {
+        unsigned lo = B[k - 1], hi = b + c;      // first p >= lo with digit >= k
+        while (lo < hi) {
+            unsigned mid = lo + ((hi - lo) >> 1);
+            unsigned dg = (unsigned)(skey[mid] >> sh) & 7u;
+            if (dg >= k) hi = mid; else lo = mid + 1;
+        }
+        B[k] = lo;
+    }
+}
+
+// Number of children of every node of level l (0 for a leaf); writes meta.
+__global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long long *skey,
+                                                   uint4 *nd_a, const uint2 *nd_r, unsigned *nch,
+                                                   int n_leaf, unsigned cap, const Status *st) {
+    unsigned b0, cnt;
+    level_range(st, l, cap, b0, cnt);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        unsigned v = b0 + k;
+        uint2 r = nd_r[v];
+        unsigned nc = 0;
+        if ((int)r.y > n_leaf && l < kMaxLevel) {
+            unsigned B[9];
+            child_bounds(skey, r.x, r.y, l, B);
+            for (int j = 0; j < 8; j++) nc += (B[j + 1] > B[j]) ? 1u : 0u;
+        }
+        nch[k] = nc;
+        uint4 a = nd_a[v];
+        a.w = make_meta((unsigned)l, nc == 0 ? 1u : 0u, nc);
+        nd_a[v] = a;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_topo_emit(int l, const unsigned long long *skey,
+                                                  uint4 *nd_a, uint4 *nd_b, uint2 *nd_r,
+                                                  const unsigned *nch, const unsigned *choff,
+                                                  unsigned cap, Status *st) {
+    unsigned b0, cnt;
+    level_range(st, l, cap, b0, cnt);
+    const unsigned next = st->lvl_begin[l] + st->lvl_count[l];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // only this thread touches level l+1's entries; the kernels that
+        // read them are later launches
+        st->lvl_begin[l + 1] = next;
+        unsigned long long end = (unsigned long long)next + st->lvl_count[l + 1];
+        if (end > cap) {
+            atomicOr(&st->flags, kErrNodeCap);
+            st->lvl_count[l + 1] = next < cap ? cap - next : 0u;
+        }
+    }
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        if (nch[k] == 0) continue;
+        unsigned v = b0 + k;
+        uint2 r = nd_r[v];
+        unsigned B[9];
+        child_bounds(skey, r.x, r.y, l, B);
+        unsigned first = next + choff[k], c = first;
+        for (int j = 0; j < 8; j++) {
+            if (B[j + 1] == B[j]) continue;
+            if (c < cap) {
+                nd_r[c] = make_uint2(B[j], B[j + 1] - B[j]);
+                nd_a[c] = make_uint4(0, 0, 0, make_meta((unsigned)l + 1, 1, 0));
+                nd_b[c] = make_uint4(0, 0, 0, 0);
+            }
+            c++;
+        }
+        uint4 bb = nd_b[v];
+        bb.w = first;
+        nd_b[v] = bb;
+    }
+}
+
+__global__ void k_topo_finish(Status *st, unsigned cap) {
+    unsigned total = 0, maxl = 0;
+    for (int l = 0; l < kLevels; l++) {
+        if (st->lvl_count[l]) maxl = (unsigned)l;
+        total += st->lvl_count[l];
+    }
+    if (total > cap) {
+        atomicOr(&st->flags, kErrNodeCap);
+        total = cap;
+    }
+    st->nnodes = total;
+    st->max_level = maxl;
+}
+
+// ---------------------------------------------------------------------------
+// Multipoles, bottom-up one level at a time.  Leaves sum their particles
+// about the first particle, internal nodes combine their children with the
+// parallel-axis shift; T is the central second moment sum m d d^T and the
+// stored quadrupole is Q = 3T - tr(T) I (twice the traceless A' of Eq. 31).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kT) k_moments(int l, const double4 *sp64, const uint4 *sq,
+                                                uint4 *nd_a, uint4 *nd_b, const uint2 *nd_r,
+                                                double4 *nd_c, double4 *nd_q, double4 *nd_t,
+                                                float4 *nd_f, unsigned cap, const Status *st) {
+    unsigned b0, cnt;
+    level_range(st, l, cap, b0, cnt);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        unsigned v = b0 + k;
+        uint4 a = nd_a[v], bb = nd_b[v];
+        uint2 r = nd_r[v];
+        double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3];
+        unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
+        if (meta_leaf(a.w)) {
+            double4 p0 = sp64[r.x];
+            double x0[3] = {p0.x, p0.y, p0.z};
+            double s2[6] = {0, 0, 0, 0, 0, 0};
+            for (unsigned p = r.x; p < r.x + r.y; p++) {
+                double4 P = sp64[p];
+                uint4 q = sq[p];
+                double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
+                M += m;
+                s1[0] += m * d0; s1[1] += m * d1; s1[2] += m * d2;
+                s2[0] += m * d0 * d0; s2[1] += m * d1 * d1; s2[2] += m * d2 * d2;
+                s2[3] += m * d0 * d1; s2[4] += m * d0 * d2; s2[5] += m * d1 * d2;
+                qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
+                qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
+            }
+            if (M > 0.0) {
+                double dc[3] = {s1[0] / M, s1[1] / M, s1[2] / M};
+                for (int d = 0; d < 3; d++) com[d] = x0[d] + dc[d];
+                T[0] = s2[0] - M * dc[0] * dc[0];
+                T[1] = s2[1] - M * dc[1] * dc[1];
+                T[2] = s2[2] - M * dc[2] * dc[2];
+                T[3] = s2[3] - M * dc[0] * dc[1];
+                T[4] = s2[4] - M * dc[0] * dc[2];
+                T[5] = s2[5] - M * dc[1] * dc[2];
+            } else {
+                for (int d = 0; d < 3; d++) com[d] = x0[d];
+            }
+        } else {
+            const unsigned fc = bb.w, nc = meta_nchild(a.w);
+            if (fc >= cap || nc > cap - fc) continue;   // truncated build (capacity flag is set)
+            double4 c0 = nd_c[fc];
+            double x0[3] = {c0.x, c0.y, c0.z};
+            for (unsigned c = fc; c < fc + nc; c++) {
+                double4 C = nd_c[c];
+                M += C.w;
+                s1[0] += C.w * (C.x - x0[0]);
+                s1[1] += C.w * (C.y - x0[1]);
+                s1[2] += C.w * (C.z - x0[2]);
+                uint4 ca = nd_a[c], cb = nd_b[c];
+                qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
+                qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
+            }
+            if (M > 0.0) {
+                for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] / M;
+                for (unsigned c = fc; c < fc + nc; c++) {
+                    double4 C = nd_c[c];
+                    double4 t0 = nd_t[2 * c], t1 = nd_t[2 * c + 1];
+                    double e0 = C.x - com[0], e1 = C.y - com[1], e2 = C.z - com[2], m = C.w;
+                    T[0] += t0.x + m * e0 * e0;
+                    T[1] += t0.y + m * e1 * e1;
+                    T[2] += t0.z + m * e2 * e2;
+                    T[3] += t0.w + m * e0 * e1;
+                    T[4] += t1.x + m * e0 * e2;
+                    T[5] += t1.y + m * e1 * e2;
+                }
+            } else {
+                for (int d = 0; d < 3; d++) com[d] = x0[d];
+            }
+        }
+        double tr = T[0] + T[1] + T[2];
+        double Q[6] = {3 * T[0] - tr, 3 * T[1] - tr, 3 * T[2] - tr, 3 * T[3], 3 * T[4], 3 * T[5]};
+        nd_c[v] = make_double4(com[0], com[1], com[2], M);
+        nd_q[2 * v] = make_double4(Q[0], Q[1], Q[2], Q[3]);
+        nd_q[2 * v + 1] = make_double4(Q[4], Q[5], 0.0, 0.0);
+        nd_t[2 * v] = make_double4(T[0], T[1], T[2], T[3]);
+        nd_t[2 * v + 1] = make_double4(T[4], T[5], 0.0, 0.0);
+        a.x = qmn[0]; a.y = qmn[1]; a.z = qmn[2];
+        bb.x = qmx[0]; bb.y = qmx[1]; bb.z = qmx[2];
+        nd_a[v] = a;
+        nd_b[v] = bb;
+        float hx = __double2float_rn(com[0]), hy = __double2float_rn(com[1]), hz = __double2float_rn(com[2]);
+        nd_f[4 * v] = make_float4(hx, hy, hz, __double2float_rn(M));
+        nd_f[4 * v + 1] = make_float4(__double2float_rn(com[0] - (double)hx),
+                                      __double2float_rn(com[1] - (double)hy),
+                                      __double2float_rn(com[2] - (double)hz), __double2float_rn(Q[0]));
+        nd_f[4 * v + 2] = make_float4(__double2float_rn(Q[1]), __double2float_rn(Q[2]),
+                                      __double2float_rn(Q[3]), __double2float_rn(Q[4]));
+        nd_f[4 * v + 3] = make_float4(__double2float_rn(Q[5]), 0.f, 0.f, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Groups: mark the first particle of every group, compact, then describe.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kT) k_group_mark(const uint4 *nd_a, const uint4 *nd_b,
+                                                   const uint2 *nd_r, unsigned *gflag,
+                                                   int n_group, const Status *st) {
+    const unsigned nn = st->nnodes;
+    const unsigned G = (unsigned)n_group;
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+        uint4 a = nd_a[v];
+        uint2 r = nd_r[v];
+        bool leaf = meta_leaf(a.w);
+        if (meta_level(a.w) == 0 && (r.y <= G || leaf)) gflag[r.x] = 1u;
+        if (r.y <= G || leaf) continue;
+        const unsigned fc = nd_b[v].w, nc = meta_nchild(a.w);
+        if (fc >= nn || nc > nn - fc) continue;         // truncated build (capacity flag is set)
+        unsigned pb = 0, pc = 0;
+        for (unsigned c = fc; c < fc + nc; c++) {
+            uint2 cr = nd_r[c];
+            if (cr.y > G) {
+                if (pc) gflag[pb] = 1u;
+                pc = 0;
+                if (meta_leaf(nd_a[c].w)) gflag[cr.x] = 1u;
+                continue;
+            }
+            if (pc && pc + cr.y > G) {
+                gflag[pb] = 1u;
+                pc = 0;
+            }
+            if (pc == 0) pb = cr.x;
+            pc += cr.y;
+        }
+        if (pc) gflag[pb] = 1u;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_group_emit(const unsigned *gflag, const unsigned *gidx,
+                                                   unsigned n, unsigned *gbegin) {
+    for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        if (gflag[p]) gbegin[gidx[p]] = p;
+}
+
+// One warp per group: range, grid box, set, root node, reference point.
+__global__ void __launch_bounds__(kT) k_group_info(const unsigned *gbegin, unsigned n,
+                                                   const uint4 *sq, uint2 *gr_r, uint4 *gr_a,
+                                                   uint4 *gr_b, const Status *st) {
+    const unsigned ng = st->ngroups;
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng;
+         g += (gridDim.x * blockDim.x) >> 5) {
+        unsigned b = gbegin[g];
+        unsigned e = (g + 1 < ng) ? gbegin[g + 1] : n;
+        unsigned mn[3] = {kGrid, kGrid, kGrid}, mx[3] = {0, 0, 0};
+        for (unsigned p = b + lane; p < e; p += 32) {
+            uint4 q = sq[p];
+            mn[0] = min(mn[0], q.x); mn[1] = min(mn[1], q.y); mn[2] = min(mn[2], q.z);
+            mx[0] = max(mx[0], q.x); mx[1] = max(mx[1], q.y); mx[2] = max(mx[2], q.z);
+        }
+        for (int d = 0; d < 3; d++) {
+            mn[d] = __reduce_min_sync(0xffffffffu, mn[d]);
+            mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
+        }
+        if (lane == 0) {
+            unsigned set = sq[b].w;
+            gr_r[g] = make_uint2(b, e - b);
+            gr_a[g] = make_uint4(mn[0], mn[1], mn[2], set);
+            gr_b[g] = make_uint4(mx[0], mx[1], mx[2], set /* root node of the set */);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side sequence
+// ---------------------------------------------------------------------------
+
+static inline int grid_for(unsigned long long n, int threads, int cap) {
+    unsigned long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b < (unsigned long long)cap ? b : cap);
+}
+
+int build_launch(const BuildArgs &A, cudaStream_t st) {
+    const int gmax = 152 * 8;
+    const unsigned n = A.n;
+    Status *S = A.status;
+    int nk = 0;
+    if (A.nsets > 1) {
+        k_set_of<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.sets, A.nsets, n, A.set_of);
+        nk++;
+    }
+    const unsigned *set_of = A.nsets > 1 ? A.set_of : nullptr;
+    k_box_init<<<1, 256, 0, st>>>(A.bmin, A.bmax, A.nsets);
+    k_box<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, A.mass, n, set_of, A.bmin, A.bmax, S);
+    k_box_finalize<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.bmin, A.bmax);
+    k_keys<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, n, set_of, A.sets, A.keys_in, A.vals_in, A.qbuf);
+    nk += 4;
+    int set_bits = 0;
+    if (A.nsets > 1) {
+        while ((1 << set_bits) < A.nsets) set_bits++;
+    }
+    nk += radix_sort(A.keys_in, A.vals_in, A.skey, A.perm, A.n_dev, n, 0, 3 * kBits, set_of,
+                     set_bits, A.sort_tmp, st);
+    k_gather<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, A.mass, n, A.perm, A.qbuf, A.sp64, A.spH,
+                                                   A.spL, A.sq);
+    // topology
+    k_topo_roots<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.nd_a, A.nd_b, A.nd_r, S);
+    nk += 2;
+    for (int l = 0; l <= kMaxLevel; l++) {
+        k_topo_count<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_r, A.tmp_u32a, A.n_leaf, A.cap_nodes, S);
+        nk++;
+        if (l == kMaxLevel) break;
+        nk += scan_exclusive<unsigned>(A.tmp_u32a, A.tmp_u32b, &S->lvl_count[l], nullptr,
+                                       &S->lvl_count[l + 1], A.scan_tmp, st);
+        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_b, A.nd_r, A.tmp_u32a, A.tmp_u32b,
+                                         A.cap_nodes, S);
+        nk++;
+    }
+    k_topo_finish<<<1, 1, 0, st>>>(S, A.cap_nodes);
+    nk++;
+    for (int l = kMaxLevel; l >= 0; l--) {
+        k_moments<<<gmax, kT, 0, st>>>(l, A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q,
+                                       A.nd_t, A.nd_f, A.cap_nodes, S);
+        nk++;
+    }
+    // groups
+    cudaMemsetAsync(A.gflag, 0, (size_t)n * sizeof(unsigned), st);
+    k_group_mark<<<gmax, kT, 0, st>>>(A.nd_a, A.nd_b, A.nd_r, A.gflag, A.n_group, S);
+    nk++;
+    nk += scan_exclusive<unsigned>(A.gflag, A.tmp_u32b, A.n_dev, nullptr, &S->ngroups, A.scan_tmp, st);
+    k_group_emit<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.gflag, A.tmp_u32b, n, A.gbegin);
+    k_group_info<<<gmax, kT, 0, st>>>(A.gbegin, n, A.sq, A.gr_r, A.gr_a, A.gr_b, S);
+    nk += 2;
+    return nk;
+}
+
+}  // namespace pt

@@ -1,0 +1,103 @@
+// pt_kernels.cuh -- launch arguments of the build, walk and force stages
+// (internal to libpt.so).
+#pragma once
+
+#include "pt_internal.cuh"
+
+namespace pt {
+
+constexpr int kWalkStack = 2048;     // per-warp walk stack (shared memory)
+constexpr unsigned kWalkMaxIters = 1u << 24;   // safety cap on walk iterations per group
+
+struct BuildArgs {
+    unsigned n;                      // particles (all sets)
+    const unsigned *n_dev;           // device copy of n
+    int nsets;
+    const double *pos, *mass;        // input order (device)
+    SetInfo *sets;                   // nsets
+    unsigned *set_of;                // n (only when nsets > 1)
+    unsigned long long *bmin, *bmax; // 3 * nsets
+    unsigned long long *keys_in;     // n
+    unsigned *vals_in;               // n
+    uint4 *qbuf;                     // n
+    unsigned long long *skey;        // n
+    unsigned *perm;                  // n
+    double4 *sp64;
+    float4 *spH, *spL;
+    uint4 *sq;
+    // nodes
+    unsigned cap_nodes;
+    uint4 *nd_a, *nd_b;
+    uint2 *nd_r;
+    double4 *nd_c, *nd_q, *nd_t;
+    float4 *nd_f;
+    unsigned *tmp_u32a, *tmp_u32b;   // max(cap_nodes, n) each
+    // groups
+    unsigned *gflag, *gbegin;        // n each
+    uint2 *gr_r;
+    uint4 *gr_a, *gr_b;
+    int n_leaf, n_group;
+    Status *status;
+    ScanTmp scan_tmp;
+    SortTmp sort_tmp;
+};
+
+struct WalkArgs {
+    const uint4 *nd_a, *nd_b;
+    const uint2 *nd_r;
+    const uint2 *gr_r;
+    const uint4 *gr_a, *gr_b;
+    const SetInfo *sets;
+    WalkParams wp;
+    unsigned *gr_nc, *gr_np;
+    unsigned long long *gr_co, *gr_po;   // ngroups + 1
+    unsigned *cells, *pp;
+    unsigned long long cap_cells, cap_pp;
+    Status *st;
+    ScanTmp scan_tmp;
+};
+
+struct ForceArgs {
+    const uint2 *gr_r;
+    const uint4 *gr_a;
+    const unsigned *gr_nc, *gr_np;
+    const unsigned long long *gr_co, *gr_po;
+    const unsigned *cells, *pp;
+    const double4 *sp64;
+    const float4 *spH, *spL;
+    const double4 *nd_c, *nd_q;
+    const float4 *nd_f;
+    const SetInfo *sets;
+    const unsigned *perm;
+    double *acc, *pot;               // input (caller) order, device
+    double G;
+    int order;                       // 0 or 2
+    int want_nb;
+    uint2 *pairs;                    // (sorted i, sorted j)
+    unsigned long long pair_cap;
+    double4 *gpart;                  // per group: sum m phi / 2, sum m a
+    Status *st;
+};
+
+struct NbArgs {
+    unsigned n;                      // particles (all sets)
+    const unsigned *perm;
+    const uint2 *pairs;
+    unsigned long long pair_cap;
+    unsigned *npairs_dev;            // clamped pair count (device)
+    unsigned long long *keys, *keys_sorted;
+    unsigned *vals, *vals_sorted;
+    long long *nb_off;               // n + 1 (global CSR, input order)
+    int *nb_idx;                     // pair_cap
+    int key_bits;
+    Status *st;
+    SortTmp sort_tmp;
+};
+
+int build_launch(const BuildArgs &A, cudaStream_t st);   // returns kernels launched
+int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill
+int force_launch(const ForceArgs &A, int precision, cudaStream_t st);
+int force_reduce_launch(const ForceArgs &A, cudaStream_t st);
+int nb_launch(const NbArgs &A, cudaStream_t st);
+
+}  // namespace pt

@@ -1,0 +1,164 @@
+// pt_walk.cu -- group-wise tree walk emitting the cell and particle-particle
+// (PP) interaction lists of every group.
+//
+// One warp walks one group: it pops up to 32 nodes from a shared-memory
+// stack, tests them in parallel and emits accepted cells, opened leaves'
+// particles and opened internal nodes' children with warp prefix sums.  All
+// tests are exact integer arithmetic on the grid boxes (see pt.h), so the
+// lists are identical to the CPU oracle's.  The walk runs twice: a counting
+// pass sizes every group's lists, an exclusive scan places them, and a
+// filling pass writes them; both passes visit nodes in the same order.
+// Warps take groups from an atomic work counter (persistent grid).
+#include "pt_kernels.cuh"
+
+namespace pt {
+
+constexpr int kWalkWarps = 4;
+constexpr int kWalkThreads = 32 * kWalkWarps;
+
+template <bool FILL>
+__global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
+    __shared__ unsigned stack[kWalkWarps][kWalkStack];
+    __shared__ unsigned pfx[kWalkWarps][32];
+    __shared__ unsigned pbeg[kWalkWarps][32];
+    __shared__ long long ithr[kLevels];
+    if (threadIdx.x < kLevels) ithr[threadIdx.x] = A.wp.ithr[threadIdx.x];
+    __syncthreads();
+    const unsigned w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned ng = A.st->ngroups;
+    unsigned *stk = stack[w];
+    for (;;) {
+        unsigned g = 0;
+        if (lane == 0) g = atomicAdd(&A.st->work[FILL ? 1 : 0], 1ull);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ng) break;
+        const uint4 ga = A.gr_a[g], gb = A.gr_b[g];
+        const long long r2thr = A.sets[ga.w].r2thr;
+        const int glo[3] = {2 * (int)ga.x, 2 * (int)ga.y, 2 * (int)ga.z};
+        const int ghi[3] = {2 * (int)gb.x + 2, 2 * (int)gb.y + 2, 2 * (int)gb.z + 2};
+        unsigned long long cbase = 0, pbase = 0;
+        if (FILL) {
+            cbase = A.gr_co[g];
+            pbase = A.gr_po[g];
+        }
+        unsigned nc = 0, np = 0;
+        if (lane == 0) stk[0] = gb.w;      // root of the group's set
+        __syncwarp();
+        int sp = 1;
+        bool overflow = false;
+        // a walk visits each node at most once; the cap only guards against a
+        // corrupted tree turning into an endless loop
+        unsigned iters = 0;
+        while (sp > 0) {
+            if (++iters > kWalkMaxIters) {
+                overflow = true;
+                break;
+            }
+            const int k = sp < 32 ? sp : 32;
+            sp -= k;
+            const bool valid = (int)lane < k;
+            const unsigned v = valid ? stk[sp + lane] : 0u;
+            __syncwarp();
+            bool accept = false, leaf = false;
+            unsigned nch = 0, first = 0, pcount = 0, pbegin = 0;
+            if (valid) {
+                const uint4 a = A.nd_a[v], b = A.nd_b[v];
+                const unsigned level = meta_level(a.w);
+                const int sh = kBits - (int)level;
+                const unsigned qmn[3] = {a.x, a.y, a.z}, qmx[3] = {b.x, b.y, b.z};
+                long long d2 = 0, gap2 = 0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const int p = (int)(qmn[d] >> sh);
+                    const int c2 = (2 * p + 1) << sh;          // cube centre, half cells
+                    int dd = glo[d] - c2;
+                    dd = max(dd, c2 - ghi[d]);
+                    dd = max(dd, 0);
+                    d2 += (long long)dd * dd;
+                    int gg = (int)qmn[d] - (ghi[d] >> 1);      // C.qmin - (G.qmax + 1)
+                    gg = max(gg, (glo[d] >> 1) - (int)qmx[d] - 1);
+                    gg = max(gg, 0);
+                    gap2 += (long long)gg * gg;
+                }
+                accept = (d2 >= ithr[level]) && (gap2 >= r2thr);
+                leaf = meta_leaf(a.w);
+                if (!accept) {
+                    if (leaf) {
+                        const uint2 r = A.nd_r[v];
+                        pbegin = r.x;
+                        pcount = r.y;
+                    } else {
+                        nch = meta_nchild(a.w);
+                        first = b.w;
+                    }
+                }
+            }
+            // accepted cells
+            const unsigned amask = __ballot_sync(0xffffffffu, accept);
+            if (FILL && accept) {
+                unsigned long long pos = cbase + nc + __popc(amask & lanemask_lt());
+                if (pos < A.cap_cells) A.cells[pos] = v;
+                else atomicOr(&A.st->flags, kErrListCap);
+            }
+            nc += __popc(amask);
+            // particles of opened leaves
+            const unsigned pincl = warp_incl_scan(pcount);
+            const unsigned ptot = __shfl_sync(0xffffffffu, pincl, 31);
+            if (FILL && ptot) {
+                pfx[w][lane] = pincl - pcount;
+                pbeg[w][lane] = pbegin;
+                __syncwarp();
+                for (unsigned e = lane; e < ptot; e += 32) {
+                    // the owner of entry e is the last lane whose prefix is
+                    // <= e (a lane with no particles shares its prefix with
+                    // the next lane, and no prefix after the last owner is
+                    // <= e, so the search always lands on an owner)
+                    int lo = 0, hi = 31;
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (pfx[w][mid] <= e) lo = mid; else hi = mid - 1;
+                    }
+                    unsigned long long pos = pbase + np + e;
+                    if (pos < A.cap_pp) A.pp[pos] = pbeg[w][lo] + (e - pfx[w][lo]);
+                    else atomicOr(&A.st->flags, kErrListCap);
+                }
+                __syncwarp();
+            }
+            np += ptot;
+            // children of opened internal nodes
+            const unsigned cincl = warp_incl_scan(nch);
+            const unsigned ctot = __shfl_sync(0xffffffffu, cincl, 31);
+            if (sp + (int)ctot > kWalkStack) {
+                overflow = true;
+                break;
+            }
+            for (unsigned j = 0; j < nch; j++) stk[sp + (cincl - nch) + j] = first + j;
+            sp += (int)ctot;
+            __syncwarp();
+        }
+        if (overflow && lane == 0) atomicOr(&A.st->flags, kErrStack);
+        if (!FILL && lane == 0) {
+            A.gr_nc[g] = nc;
+            A.gr_np[g] = np;
+        }
+        __syncwarp();
+    }
+}
+
+int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
+    // work counters 0 and 1 are reset by the caller (part of the status block)
+    const int blocks = 152 * 4;
+    if (phase == 0) {
+        k_walk<false><<<blocks, kWalkThreads, 0, st>>>(A);
+        int nk = 1;
+        nk += scan_exclusive<unsigned long long>(A.gr_nc, A.gr_co, &A.st->ngroups, &A.st->cell_total,
+                                                 nullptr, A.scan_tmp, st);
+        nk += scan_exclusive<unsigned long long>(A.gr_np, A.gr_po, &A.st->ngroups, &A.st->pp_total,
+                                                 nullptr, A.scan_tmp, st);
+        return nk;
+    }
+    k_walk<true><<<blocks, kWalkThreads, 0, st>>>(A);
+    return 1;
+}
+
+}  // namespace pt

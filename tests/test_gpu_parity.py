@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars (the hot path's contract):
+  * keys, sort order, tree topology, grid boxes, groups, interaction lists
+    and neighbour lists: bit-exact;
+  * float64 GPU forces vs the oracle's tree with the same lists: <= 1e-10
+    relative per particle (acc) and per particle (pot);
+  * mixed precision vs the float64 GPU path: p99 relative force error
+    <= 1e-6 (and max <= 1e-4, a loose guard on the tail).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_16560_gb300 import binding as B
+from paper_2006_16560_gb300 import inputs
+from gpu_helpers import node_ids, rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_P99 = 1e-6
+MIXED_MAX = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return B.Context(0)
+
+
+def c1_params(**kw):
+    """Plummer N = 4096 workload: monopole, theta 0.5, leaf 8, r_out 0.05, r_in 0.1 r_out."""
+    p = B.Params(theta=0.5, r_in=0.005, r_out=0.05, n_leaf=8, n_group=64, order=0,
+                 precision=B.PT_FP64)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def check_structure(g, T, p):
+    """Keys, order, topology, moments, groups and lists against the oracle tree."""
+    tree = g["tree"]
+    key, q, perm = T.keys()
+    gk, gperm = tree.keys()
+    assert np.array_equal(gperm.astype(np.int64), perm)
+    assert np.array_equal(gk, key[perm])
+    gn, on = tree.nodes(), T.nodes()
+    gid = list(zip(gn["level"].tolist(), gn["begin"].tolist(), gn["count"].tolist()))
+    oid = list(zip(on["level"].tolist(), on["begin"].tolist(), on["count"].tolist()))
+    assert sorted(gid) == sorted(oid)
+    omap = {(l, b): k for k, (l, b, c) in enumerate(oid)}
+    order = np.array([omap[(l, b)] for (l, b, c) in gid])
+    assert np.array_equal(gn["leaf"], on["leaf"][order])
+    assert np.array_equal(gn["qmin"], on["qmin"][order])
+    assert np.array_equal(gn["qmax"], on["qmax"][order])
+    np.testing.assert_allclose(gn["mass"], on["mass"][order], rtol=1e-12, atol=0)
+    scale = np.abs(on["com"]).max()
+    np.testing.assert_allclose(gn["com"], on["com"][order], rtol=0, atol=1e-13 * scale)
+    qscale = np.abs(on["quad"][order]).max(axis=1, keepdims=True) + 1e-300
+    assert np.all(np.abs(gn["quad"] - on["quad"][order]) <= 1e-9 * qscale)
+    gg, og = tree.groups(), T.groups()
+    for k in ("begin", "count", "qmin", "qmax"):
+        assert np.array_equal(gg[k], og[k]), k
+    st = g["stats"]
+    co, cells, po, pp = tree.lists(st["cell_list_total"], st["pp_list_total"])
+    for k in range(len(og["begin"])):
+        ocells, opp = T.walk(k, p.theta, p.r_out)
+        assert node_ids(gn, cells[co[k]:co[k + 1]]) == node_ids(on, ocells)
+        assert np.array_equal(np.sort(pp[po[k]:po[k + 1]]), np.sort(opp))
+
+
+def check_neighbours(g, pos, r_out, targets=None):
+    off, idx = oracle.neighbours(pos, r_out, targets)
+    if targets is None:
+        assert np.array_equal(g["nb_off"], off)
+        assert np.array_equal(g["nb_idx"], idx)
+    else:
+        for t, i in enumerate(targets):
+            got = g["nb_idx"][g["nb_off"][i]:g["nb_off"][i + 1]]
+            assert np.array_equal(got, idx[off[t]:off[t + 1]])
+
+
+@pytest.mark.parametrize("order", [0, 2])
+def test_plummer4096_fp64_vs_oracle(ctx, order):
+    d = inputs.plummer(4096, 1)
+    p = c1_params(order=order)
+    g = run_gpu(ctx, d["pos"], d["mass"], p)
+    T = oracle.Tree(d["pos"], d["mass"], p.n_leaf, p.n_group)
+    check_structure(g, T, p)
+    a, phi, st = T.force(p.theta, p.r_in, p.r_out, order=order)
+    assert rel_err(g["acc"], a).max() <= FP64_TOL
+    assert (np.abs(g["pot"] - phi) / np.abs(phi)).max() <= FP64_TOL
+    assert g["stats"]["cell_interactions"] == st[0]
+    assert g["stats"]["pp_interactions"] == st[1]
+    check_neighbours(g, d["pos"], p.r_out)
+    # energy and momentum sums are float64 sums of the returned arrays
+    e = 0.5 * (d["mass"] * g["pot"]).sum()
+    assert g["stats"]["energy"] == pytest.approx(e, rel=1e-12)
+    np.testing.assert_allclose(g["stats"]["momentum"], (d["mass"][:, None] * g["acc"]).sum(0),
+                               atol=1e-12 * np.abs(d["mass"][:, None] * g["acc"]).sum())
+    # and the tree is close to the direct sum (report-level bound only)
+    ad, _ = oracle.direct_force(d["pos"], d["mass"], p.r_in, p.r_out)
+    assert np.percentile(rel_err(g["acc"], ad), 99) < 0.05
+
+
+@pytest.mark.parametrize("order", [0, 2])
+def test_plummer4096_mixed(ctx, order):
+    d = inputs.plummer(4096, 1)
+    g64 = run_gpu(ctx, d["pos"], d["mass"], c1_params(order=order))
+    gmx = run_gpu(ctx, d["pos"], d["mass"], c1_params(order=order, precision=B.PT_MIXED))
+    e = rel_err(gmx["acc"], g64["acc"])
+    assert np.percentile(e, 99) <= MIXED_P99
+    assert e.max() <= MIXED_MAX
+    ep = np.abs(gmx["pot"] - g64["pot"]) / np.abs(g64["pot"])
+    assert np.percentile(ep, 99) <= MIXED_P99
+    # the neighbour lists do not depend on the pair precision
+    assert np.array_equal(gmx["nb_off"], g64["nb_off"])
+    assert np.array_equal(gmx["nb_idx"], g64["nb_idx"])
+
+
+def test_theta0_equals_direct(ctx):
+    d = inputs.plummer(1500, 5, masses="kroupa")
+    p = c1_params(theta=0.0, order=2)
+    g = run_gpu(ctx, d["pos"], d["mass"], p)
+    ad, pd = oracle.direct_force(d["pos"], d["mass"], p.r_in, p.r_out)
+    assert g["stats"]["cell_list_total"] == 0
+    assert rel_err(g["acc"], ad).max() <= 1e-12
+    np.testing.assert_allclose(g["pot"], pd, rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 64, 65, 100, 257, 1000])
+@pytest.mark.parametrize("precision", [B.PT_FP64, B.PT_MIXED])
+def test_small_and_ragged(ctx, n, precision):
+    d = inputs.plummer(n, 100 + n, masses="kroupa")
+    p = c1_params(order=2, n_leaf=4, n_group=16, precision=precision, r_out=0.3, r_in=0.03)
+    g = run_gpu(ctx, d["pos"], d["mass"], p)
+    T = oracle.Tree(d["pos"], d["mass"], p.n_leaf, p.n_group)
+    a, phi, _ = T.force(p.theta, p.r_in, p.r_out, order=2)
+    tol = FP64_TOL if precision == B.PT_FP64 else 1e-5
+    if n > 1:
+        assert rel_err(g["acc"], a).max() <= tol
+    np.testing.assert_allclose(g["pot"], phi, rtol=tol, atol=tol * (np.abs(phi).max() + 1.0))
+    check_neighbours(g, d["pos"], p.r_out)
+
+
+def test_degenerate_inputs(ctx):
+    # all particles at one point: box side 0 -> 1, one depth-capped leaf
+    pos = np.zeros((50, 3))
+    mass = np.full(50, 0.02)
+    p = c1_params(order=2)
+    g = run_gpu(ctx, pos, mass, p)
+    assert np.all(g["acc"] == 0.0)
+    np.testing.assert_allclose(g["pot"], -49 * 0.02 * 2 / (p.r_out + p.r_in), rtol=1e-12)
+    assert np.all(np.diff(g["nb_off"]) == 49)
+    # pairs of coincident points and zero masses in a Plummer set
+    d = inputs.plummer(2000, 9)
+    pos = d["pos"].copy()
+    pos[1::2] = pos[0::2]
+    mass = d["mass"].copy()
+    mass[::7] = 0.0
+    for prec in (B.PT_FP64, B.PT_MIXED):
+        g = run_gpu(ctx, pos, mass, c1_params(order=2, precision=prec))
+        T = oracle.Tree(pos, mass, 8, 64)
+        a, phi, _ = T.force(0.5, 0.005, 0.05, order=2)
+        tol = FP64_TOL if prec == B.PT_FP64 else 1e-4
+        assert np.all(np.isfinite(g["acc"])) and np.all(np.isfinite(g["pot"]))
+        assert np.percentile(rel_err(g["acc"], a), 99) <= tol
+        check_neighbours(g, pos, 0.05)
+
+
+def test_host_buffers_match_device_buffers(ctx):
+    d = inputs.plummer(3000, 2, masses="kroupa")
+    p = c1_params(order=2, precision=B.PT_MIXED)
+    gd = run_gpu(ctx, d["pos"], d["mass"], p, device_buffers=True)
+    gh = run_gpu(ctx, d["pos"], d["mass"], p, device_buffers=False)
+    assert np.array_equal(gd["acc"], gh["acc"])
+    assert np.array_equal(gd["pot"], gh["pot"])
+    assert np.array_equal(gd["nb_idx"], gh["nb_idx"])
+
+
+def test_errors(ctx):
+    d = inputs.plummer(100, 3)
+    pos, mass = d["pos"], d["mass"]
+    bad = c1_params(r_in=0.05, r_out=0.05)
+    rc, _ = B.pt_tree_build(ctx.h, 100, pos.ctypes.data, mass.ctypes.data, bad.c())
+    assert rc == B.PT_ERR_ARG
+    rc, _ = B.pt_tree_build(ctx.h, 0, pos.ctypes.data, mass.ctypes.data, c1_params().c())
+    assert rc == B.PT_ERR_ARG
+    p2 = pos.copy()
+    p2[7, 1] = np.nan
+    rc, h = B.pt_tree_build(ctx.h, 100, p2.ctypes.data, mass.ctypes.data, c1_params().c())
+    assert rc == B.PT_ERR_ARG and "non-finite" in B.pt_last_error(ctx.h)
+    B.pt_tree_free(h)
+    m2 = mass.copy()
+    m2[3] = -1.0
+    rc, h = B.pt_tree_build(ctx.h, 100, pos.ctypes.data, m2.ctypes.data, c1_params().c())
+    assert rc == B.PT_ERR_ARG
+    B.pt_tree_free(h)
+    # neighbour capacity too small: acc/pot still valid, total reported
+    d = inputs.plummer(2000, 4)
+    t = B.Tree(ctx, d["pos"], d["mass"], c1_params(r_out=0.2, r_in=0.02))
+    acc, pot = np.zeros((2000, 3)), np.zeros(2000)
+    off, idx = np.zeros(2001, dtype=np.int64), np.zeros(10, dtype=np.int32)
+    total, st, rc = t.force(acc, pot, off, idx, 10, allow_capacity_error=True)
+    assert rc == B.PT_ERR_CAPACITY
+    want_off, _ = oracle.neighbours(d["pos"], 0.2)
+    assert total == want_off[-1]
+    T = oracle.Tree(d["pos"], d["mass"], 8, 64)
+    a, _, _ = T.force(0.5, 0.02, 0.2, order=0)
+    assert rel_err(acc, a).max() <= FP64_TOL
