@@ -211,6 +211,35 @@ int pt_tree_lists(pt_tree *tree, int64_t *cell_off, uint32_t *cells,
 /* Version of this ABI (1). */
 int pt_abi_version(void);
 
+/* ---- allocation-free entry point ---- */
+
+/* Stable ascending sort of n 64-bit keys: keys_sorted[s] is the s-th
+ * smallest key and perm[s] its index in `keys`; equal keys keep their input
+ * order.  This is the same radix sort that orders the Morton keys inside
+ * pt_tree_build, offered for callers that cannot allocate device memory: a
+ * process whose GPU memory belongs to another allocator (a framework's
+ * caching allocator or a fixed arena), a loop that must never allocate, or
+ * work that will later be captured into a CUDA graph.  The paper has no
+ * counterpart; it is a service of this library.
+ *
+ * It allocates nothing.  Its scratch space is a fixed array of about
+ * 4.3 MiB inside the library image, which every GPU that loads the library
+ * keeps until the process exits; hence the size limit 1 <= n <= 262144
+ * (2^18); larger n returns PT_ERR_ARG.
+ *   keys, keys_sorted (n each, uint64) and perm (n, uint32): device memory
+ *     on the calling thread's current device, owned by the caller; keys is
+ *     only read.  Any other pointer kind returns PT_ERR_ARG.
+ *   stream: the cudaStream_t (as void*) on which the sort is ordered; the
+ *     call returns without waiting for it.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the one scratch array, so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Returns PT_OK, PT_ERR_ARG or
+ * PT_ERR_CUDA (launch failure). */
+int pt_sort_keys_noalloc(int64_t n, const uint64_t *keys, uint64_t *keys_sorted,
+                         uint32_t *perm, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
