@@ -46,9 +46,12 @@ SEED = 2
 
 # Flops per interaction, counted from the kernel source (FFMA = 2, other
 # arithmetic = 1, reciprocal square root = 4 by convention; min / max,
-# compares and selects are not counted).
+# compares and selects are not counted).  Mixed PP pairs take either the
+# changeover path ("pp") or, when no pair of the warp's iteration is within
+# r_out, the plain Newtonian pair ("pp_newton"), which is exact there.
 FLOPS = {
     ("mixed", "cell", 2): 56, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 59,
+    ("mixed", "pp_newton", None): 28,
     ("fp64", "cell", 2): 56, ("fp64", "cell", 0): 22, ("fp64", "pp", None): 53,
 }
 SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
@@ -78,8 +81,12 @@ def params(precision):
 
 
 def flops_of(stats, kind):
-    return (stats["cell_interactions"] * FLOPS[(kind, "cell", 2)] +
-            stats["pp_interactions"] * FLOPS[(kind, "pp", None)])
+    cells = stats["cell_interactions"] * FLOPS[(kind, "cell", 2)]
+    if kind == "mixed":
+        full = stats["pp_changeover_interactions"]
+        fast = stats["pp_interactions"] - full
+        return cells + full * FLOPS[(kind, "pp", None)] + fast * FLOPS[(kind, "pp_newton", None)]
+    return cells + stats["pp_interactions"] * FLOPS[(kind, "pp", None)]
 
 
 class ClockSampler:
@@ -296,7 +303,11 @@ def main():
         "particles_per_s": world * n / (ms_max.item() * 1e-3),
         "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                        "wall_per_step": 1000 * t_wall / args.steps},
-        "interactions_per_step": inter, "neighbours": nb_total,
+        "interactions_per_step": inter, "cell_interactions": st["cell_interactions"],
+        "pp_interactions": st["pp_interactions"],
+        "pp_changeover_interactions": st["pp_changeover_interactions"],
+        "groups": st["groups"], "nodes": st["nodes"], "max_walk_stack": st["max_walk_stack"],
+        "neighbours": nb_total,
         "stage_ms": {"build": st["ms_build"], "walk": st["ms_walk"], "force_kernel": k_ms,
                      "force_call": st["ms_total"]},
         "gpu_launches": int((st["launches_build"] + st["launches_force"]) * args.steps),
@@ -307,7 +318,8 @@ def main():
                         "traffic": FORCE_MIXED_DRAM_BYTES,
                         "kernel": "k_force_mixed<2,true>",
                         "flops_per_interaction": {"cell_quadrupole": FLOPS[("mixed", "cell", 2)],
-                                                  "pp": FLOPS[("mixed", "pp", None)]},
+                                                  "pp_changeover": FLOPS[("mixed", "pp", None)],
+                                                  "pp_newton": FLOPS[("mixed", "pp_newton", None)]},
                         "peak_note": "FP32 CUDA-core peak at the 2070 MHz maximum SM clock "
                                      "(152 SMs x 128 lanes x 2 flop)"}
     if clocks.get("sm_mhz"):

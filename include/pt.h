@@ -121,6 +121,12 @@ typedef struct {
     double ms_walk;             /* GPU time of the walk                      */
     double ms_force;            /* GPU time of the force kernel              */
     double ms_total;            /* GPU time of the force call (walk..sums)   */
+    int64_t pp_changeover_interactions; /* mixed path: PP interactions evaluated
+                                   with the changeover (a warp takes that path
+                                   when any of its pairs is within r_out); the
+                                   others used the plain Newtonian pair, which
+                                   is exact beyond r_out (K = W = 0)         */
+    int64_t max_walk_stack;     /* deepest walk stack (pending nodes per warp) */
     int64_t launches_build;     /* kernels launched by the last tree build   */
     int64_t launches_force;     /* kernels launched by the force call        */
 } pt_stats;

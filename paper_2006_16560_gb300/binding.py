@@ -39,7 +39,8 @@ class pt_stats(C.Structure):
                 ("pp_interactions", C.c_int64), ("neighbours", C.c_int64),
                 ("energy", C.c_double), ("momentum", C.c_double * 3),
                 ("ms_build", C.c_double), ("ms_walk", C.c_double), ("ms_force", C.c_double),
-                ("ms_total", C.c_double), ("launches_build", C.c_int64),
+                ("ms_total", C.c_double), ("pp_changeover_interactions", C.c_int64),
+                ("max_walk_stack", C.c_int64), ("launches_build", C.c_int64),
                 ("launches_force", C.c_int64)]
 
     def as_dict(self) -> dict:

@@ -49,8 +49,9 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-ftz=true",
                     "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                    "-Xcompiler", "-Wno-deprecated-declarations", "-diag-suppress", "1444",
                     "-I", os.path.join(ROOT, "include")] + (extra or [])
     objs = []
 

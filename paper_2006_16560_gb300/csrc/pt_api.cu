@@ -116,8 +116,25 @@ struct pt_tree {
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
     Buf out_acc, out_pot;                                  // staging for host outputs
+    // batch state (the context's batch tree only)
+    Buf d_tab, d_totals, d_acc, d_pot;
+    BatchTab *h_tab = nullptr;                 // pinned, cap_tab entries
+    SetInfo *h_sets_pin = nullptr;             // pinned, cap_tab entries
+    long long *h_totals = nullptr;             // pinned, cap_tab entries
+    unsigned *h_n = nullptr;                   // pinned
+    int cap_tab = 0;
+    double *h_io = nullptr;                    // pinned host staging (4 doubles per particle)
+    long long *h_nboff = nullptr;              // pinned, n + 1
+    int *h_nbidx = nullptr;                    // pinned, cap_h_nb
+    size_t cap_h_io = 0, cap_h_nboff = 0, cap_h_nb = 0;
+    cudaGraphExec_t gexec = nullptr;           // captured launch sequence
+    std::vector<unsigned> gkey_n;
+    std::vector<double> gkey_r;
+    pt_params gkey_p{};
+    int gkey_mode = -1;
     // last results
     Status h{};
+    unsigned walk_stack = kWalkStackSmall;
     bool built = false, lists_valid = false;
     float ms_build = 0.f;
     int launches_build = 0, launches_force = 0;
@@ -130,6 +147,15 @@ struct pt_tree {
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot};
         for (Buf *b : all) b->release();
+        d_tab.release(); d_totals.release(); d_acc.release(); d_pot.release();
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        void *pinned[] = {h_tab, h_sets_pin, h_totals, h_n, h_io, h_nboff, h_nbidx};
+        for (void *q : pinned)
+            if (q) cudaFreeHost(q);
+        h_tab = nullptr; h_sets_pin = nullptr; h_totals = nullptr; h_n = nullptr;
+        h_io = nullptr; h_nboff = nullptr; h_nbidx = nullptr;
+        cap_tab = 0; cap_h_io = cap_h_nboff = cap_h_nb = 0;
     }
 };
 
@@ -226,7 +252,7 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
     TRY(ensure(ctx, t->gpart, N * 32));
     TRY(ensure(ctx, t->scan_sums, (kScanBlocks + 1) * 8));
-    TRY(ensure(ctx, t->sort_counts, 256 * kSortBlocks * 4));
+    TRY(ensure(ctx, t->sort_counts, (size_t)kSortCountsLen * 4));
     t->cap_sort = std::max<unsigned long long>(t->cap_sort, N);
     TRY(ensure(ctx, t->sort_k2, t->cap_sort * 8));
     TRY(ensure(ctx, t->sort_v2, t->cap_sort * 4));
@@ -338,6 +364,7 @@ WalkArgs walk_args(pt_tree *t) {
     A.pp = t->pp.as<unsigned>();
     A.cap_cells = t->cap_cells;
     A.cap_pp = t->cap_pp;
+    A.stack_cap = t->walk_stack;
     A.st = t->status.as<Status>();
     A.scan_tmp = scan_tmp_of(t);
     return A;
@@ -429,17 +456,24 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
     Status *dS = t->status.as<Status>();
     TRY(ensure(ctx, t->nb_off, ((size_t)t->n + 1) * 8));
     TRY(alloc_pairs(t, std::max<unsigned long long>(nb_cap_hint, 2ull * t->n)));
-    for (int attempt = 0; attempt < 4; attempt++) {
+    for (int attempt = 0; attempt < 6; attempt++) {
         CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));
+        CK(cudaMemsetAsync(&dS->max_stack, 0, sizeof(unsigned), st));
         CK(cudaMemsetAsync(&dS->work, 0, sizeof(dS->work), st));
-        CK(cudaMemsetAsync(&dS->npairs, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&dS->npairs, 0, 3 * sizeof(unsigned long long), st));   // npairs, pp_full, pp_fast
         CK(cudaEventRecord(ctx->ev[2], st));
         WalkArgs W = walk_args(t);
         int nk = walk_launch(W, 0, st);
         CK(cudaGetLastError());
         TRY(read_status(t));
-        if (t->h.flags & kErrStack)
-            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %d pending nodes)", kWalkStack);
+        if (t->h.flags & kErrStack) {
+            if (t->walk_stack < kWalkStackLarge) {   // rare: deep or very unbalanced tree
+                t->walk_stack = kWalkStackLarge;
+                continue;
+            }
+            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %u pending nodes)",
+                        kWalkStackLarge);
+        }
         if (t->h.cell_total > t->cap_cells || !t->cells.p) {
             t->cap_cells = t->h.cell_total + t->h.cell_total / 8 + 1024;
             TRY(ensure(ctx, t->cells, t->cap_cells * 4));
@@ -462,7 +496,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         TRY(read_status(t));
         const unsigned f = t->h.flags;
         if (f & kErrStack)
-            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %d pending nodes)", kWalkStack);
+            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %u pending nodes)", t->walk_stack);
         if (f & kErrListCap) continue;                  // cannot happen after sizing; retry
         if (want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= nb_cap_hint) {
             TRY(alloc_pairs(t, t->h.npairs + t->h.npairs / 8));
@@ -497,8 +531,317 @@ void fill_stats(pt_tree *t, pt_stats *s, const float *ms) {
     s->ms_walk = ms ? ms[0] : 0.0;
     s->ms_force = ms ? ms[1] : 0.0;
     s->ms_total = ms ? ms[2] : 0.0;
+    s->pp_changeover_interactions = (int64_t)h.pp_full;
+    s->max_walk_stack = h.max_stack;
     s->launches_build = t->launches_build;
     s->launches_force = t->launches_force;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches (pt_batch_longrange_force): one forest over all sets.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+int ensure_pinned(pt_ctx *ctx, T *&p, size_t &cap, size_t n) {
+    if (n <= cap && p) return PT_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void **)&p, n * sizeof(T)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, PT_ERR_OOM, "cudaMallocHost(%zu bytes) failed", n * sizeof(T));
+    }
+    cap = n;
+    return PT_OK;
+}
+
+int batch_tables(pt_tree *t, int nsets) {
+    pt_ctx *ctx = t->ctx;
+    if (t->cap_tab < nsets) {
+        if (t->h_tab) cudaFreeHost(t->h_tab);
+        if (t->h_sets_pin) cudaFreeHost(t->h_sets_pin);
+        if (t->h_totals) cudaFreeHost(t->h_totals);
+        t->h_tab = nullptr; t->h_sets_pin = nullptr; t->h_totals = nullptr; t->cap_tab = 0;
+        if (cudaMallocHost((void **)&t->h_tab, nsets * sizeof(BatchTab)) != cudaSuccess ||
+            cudaMallocHost((void **)&t->h_sets_pin, nsets * sizeof(SetInfo)) != cudaSuccess ||
+            cudaMallocHost((void **)&t->h_totals, nsets * sizeof(long long)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ctx, PT_ERR_OOM, "pinned batch tables");
+        }
+        t->cap_tab = nsets;
+    }
+    if (!t->h_n && cudaMallocHost((void **)&t->h_n, 16) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, PT_ERR_OOM, "pinned batch tables");
+    }
+    TRY(ensure(ctx, t->d_tab, (size_t)nsets * sizeof(BatchTab)));
+    TRY(ensure(ctx, t->d_totals, (size_t)nsets * 8));
+    TRY(ensure(ctx, t->d_acc, (size_t)t->n * 24));
+    TRY(ensure(ctx, t->d_pot, (size_t)t->n * 8));
+    return PT_OK;
+}
+
+// Everything a batch enqueues after the tables are filled, without any host
+// synchronisation (this is what a CUDA graph captures).
+int enqueue_batch(pt_tree *t, bool host_io, bool want_nb) {
+    pt_ctx *ctx = t->ctx;
+    cudaStream_t st = ctx->stream;
+    const unsigned n = t->n;
+    const int C = t->nsets;
+    Status *dS = t->status.as<Status>();
+    BatchTab *dtab = t->d_tab.as<BatchTab>();
+    SetInfo *dsets = t->sets.as<SetInfo>();
+    double *ip = t->in_pos.as<double>(), *im = t->in_mass.as<double>();
+    CK(cudaMemcpyAsync(dtab, t->h_tab, C * sizeof(BatchTab), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dsets, t->h_sets_pin, C * sizeof(SetInfo), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t->n_dev.p, t->h_n, 4, cudaMemcpyHostToDevice, st));
+    int nk = 0;
+    if (host_io) {
+        CK(cudaMemcpyAsync(ip, t->h_io, (size_t)n * 24, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(im, t->h_io + 3ull * n, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    } else {
+        nk += batch_gather_launch(dtab, dsets, C, n, ip, im, st);
+    }
+    CK(cudaMemsetAsync(dS, 0, sizeof(Status), st));
+    nk += build_launch(build_args(t, ip, im), st);
+    CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));
+    WalkArgs W = walk_args(t);
+    nk += walk_launch(W, 0, st);
+    nk += walk_launch(W, 1, st);
+    ForceArgs F = force_args(t, t->d_acc.as<double>(), t->d_pot.as<double>(), want_nb);
+    nk += force_launch(F, t->prm.precision, st);
+    nk += force_reduce_launch(F, st);
+    if (want_nb) {
+        nk += nb_launch(nb_args(t), st);
+        nk += batch_nb_launch(dtab, dsets, C, n, t->nb_off.as<long long>(), t->nb_idx.as<int>(),
+                              t->d_totals.as<long long>(), !host_io, st);
+    }
+    if (host_io) {
+        CK(cudaMemcpyAsync(t->h_io, t->d_acc.p, (size_t)n * 24, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(t->h_io + 3ull * n, t->d_pot.p, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    } else {
+        nk += batch_scatter_launch(dtab, dsets, C, n, t->d_acc.as<double>(), t->d_pot.as<double>(), st);
+    }
+    if (want_nb)
+        CK(cudaMemcpyAsync(t->h_totals, t->d_totals.p, C * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_status, dS, sizeof(Status), cudaMemcpyDeviceToHost, st));
+    t->launches_force = nk;
+    t->launches_build = 0;
+    return PT_OK;
+}
+
+bool graph_matches(pt_tree *t, int C, const pt_cluster_desc *d, const pt_params *p, int mode) {
+    if (!t->gexec || t->gkey_mode != mode || (int)t->gkey_n.size() != C) return false;
+    if (std::memcmp(&t->gkey_p, p, sizeof(pt_params)) != 0) return false;
+    for (int c = 0; c < C; c++)
+        if (t->gkey_n[c] != (unsigned)d[c].n || t->gkey_r[2 * c] != d[c].r_in ||
+            t->gkey_r[2 * c + 1] != d[c].r_out)
+            return false;
+    return true;
+}
+
+int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, int flags,
+               pt_stats *stats) {
+    if (C < 1 || !d) return fail(ctx, PT_ERR_ARG, "n_clusters must be >= 1");
+    TRY(check_params(ctx, params));
+    unsigned long long ntot = 0;
+    bool want_nb = false, any_dev = false, any_host = false;
+    for (int c = 0; c < C; c++) {
+        if (d[c].n < 1) return fail(ctx, PT_ERR_ARG, "cluster %d: n must be >= 1", c);
+        if (!d[c].pos || !d[c].mass || !d[c].acc || !d[c].pot)
+            return fail(ctx, PT_ERR_ARG, "cluster %d: NULL buffer", c);
+        TRY(check_radii(ctx, d[c].r_in, d[c].r_out));
+        if (d[c].nb_offsets) {
+            want_nb = true;
+            if (d[c].nb_capacity < 0 || (d[c].nb_capacity > 0 && !d[c].nb_idx))
+                return fail(ctx, PT_ERR_ARG, "cluster %d: bad neighbour buffers", c);
+        }
+        ntot += (unsigned long long)d[c].n;
+        (is_device_ptr(d[c].pos) ? any_dev : any_host) = true;
+    }
+    if (any_dev && any_host) return fail(ctx, PT_ERR_ARG, "mixing host and device buffers in one batch");
+    if (ntot > 0x7fffffffull) return fail(ctx, PT_ERR_ARG, "batch holds more than 2^31 particles");
+    const bool host_io = any_host;
+    CK(cudaSetDevice(ctx->device));
+    pt_tree *t = ctx->batch_tree;
+    if (!t) {
+        t = new (std::nothrow) pt_tree;
+        if (!t) return fail(ctx, PT_ERR_OOM, "out of host memory");
+        ctx->batch_tree = t;
+        t->ctx = ctx;
+    }
+    const unsigned n = (unsigned)ntot;
+    t->n = n;
+    t->nsets = C;
+    t->prm = *params;
+    t->h_sets.resize(C);
+    unsigned long long nb_hint = 0;
+    {
+        unsigned b = 0;
+        for (int c = 0; c < C; c++) {
+            SetInfo si{};
+            si.r_in = d[c].r_in;
+            si.r_out = d[c].r_out;
+            si.begin = b;
+            si.n = (unsigned)d[c].n;
+            t->h_sets[c] = si;
+            b += (unsigned)d[c].n;
+            nb_hint += d[c].nb_offsets ? (unsigned long long)d[c].nb_capacity : 0ull;
+        }
+    }
+    TRY(alloc_build(t, n, C));
+    TRY(batch_tables(t, C));
+    TRY(ensure(ctx, t->in_pos, (size_t)n * 24));
+    TRY(ensure(ctx, t->in_mass, (size_t)n * 8));
+    TRY(ensure(ctx, t->nb_off, ((size_t)n + 1) * 8));
+    if (host_io) TRY(ensure_pinned(ctx, t->h_io, t->cap_h_io, 4ull * n));
+    // tables (pinned) and host inputs
+    for (int c = 0; c < C; c++) {
+        BatchTab e{};
+        e.pos = d[c].pos;
+        e.mass = d[c].mass;
+        e.acc = d[c].acc;
+        e.pot = d[c].pot;
+        e.nb_off = (long long *)d[c].nb_offsets;
+        e.nb_idx = (int *)d[c].nb_idx;
+        e.nb_cap = d[c].nb_offsets ? (unsigned long long)d[c].nb_capacity : 0ull;
+        t->h_tab[c] = e;
+        t->h_sets_pin[c] = t->h_sets[c];
+        t->h_totals[c] = 0;
+        if (host_io) {
+            const size_t b = t->h_sets[c].begin, m = (size_t)d[c].n;
+            std::memcpy(t->h_io + 3 * b, d[c].pos, m * 24);
+            std::memcpy(t->h_io + 3ull * n + b, d[c].mass, m * 8);
+        }
+    }
+    *t->h_n = n;
+    const int mode = (host_io ? 1 : 0) | (want_nb ? 2 : 0);
+    cudaStream_t st = ctx->stream;
+    bool done = false;
+    float ms[3] = {0, 0, 0};
+    if ((flags & PT_BATCH_GRAPH) && graph_matches(t, C, d, params, mode)) {
+        CK(cudaEventRecord(ctx->ev[6], st));
+        CK(cudaGraphLaunch(t->gexec, st));
+        CK(cudaEventRecord(ctx->ev[7], st));
+        CK(cudaStreamSynchronize(st));
+        t->h = *ctx->h_status;
+        const unsigned f = t->h.flags;
+        const bool pair_short = want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= nb_hint;
+        if (f & (kErrNonFinite | kErrNegMass)) return fail(ctx, PT_ERR_ARG, "non-finite position or negative mass");
+        if (!(f & (kErrNodeCap | kErrStack | kErrListCap)) && !pair_short) {
+            done = true;
+            cudaEventElapsedTime(&ms[2], ctx->ev[6], ctx->ev[7]);
+        } else {
+            cudaGraphExecDestroy(t->gexec);   // capacities outgrown: rebuild below
+            t->gexec = nullptr;
+        }
+    }
+    if (!done) {
+        // uncaptured path: sizes every buffer, then (optionally) captures a graph
+        CK(cudaMemcpyAsync(t->d_tab.p, t->h_tab, C * sizeof(BatchTab), cudaMemcpyHostToDevice, st));
+        double *ip = t->in_pos.as<double>(), *im = t->in_mass.as<double>();
+        if (host_io) {
+            CK(cudaMemcpyAsync(ip, t->h_io, (size_t)n * 24, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(im, t->h_io + 3ull * n, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+        } else {
+            CK(cudaMemcpyAsync(t->sets.p, t->h_sets_pin, C * sizeof(SetInfo), cudaMemcpyHostToDevice, st));
+            batch_gather_launch(t->d_tab.as<BatchTab>(), t->sets.as<SetInfo>(), C, n, ip, im, st);
+        }
+        TRY(run_build(t, ip, im));
+        TRY(run_force(t, t->d_acc.as<double>(), t->d_pot.as<double>(), want_nb, nb_hint, ms));
+        BatchTab *dtab = t->d_tab.as<BatchTab>();
+        SetInfo *dsets = t->sets.as<SetInfo>();
+        if (want_nb)
+            batch_nb_launch(dtab, dsets, C, n, t->nb_off.as<long long>(), t->nb_idx.as<int>(),
+                            t->d_totals.as<long long>(), !host_io, st);
+        if (host_io) {
+            CK(cudaMemcpyAsync(t->h_io, t->d_acc.p, (size_t)n * 24, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(t->h_io + 3ull * n, t->d_pot.p, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+        } else {
+            batch_scatter_launch(dtab, dsets, C, n, t->d_acc.as<double>(), t->d_pot.as<double>(), st);
+        }
+        if (want_nb) CK(cudaMemcpyAsync(t->h_totals, t->d_totals.p, C * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        if (flags & PT_BATCH_GRAPH) {
+            // leave head room so that later steps of the same shape fit
+            const unsigned long long cc = t->h.cell_total + t->h.cell_total / 4 + 4096;
+            const unsigned long long pc = t->h.pp_total + t->h.pp_total / 4 + 4096;
+            if (cc > t->cap_cells) { t->cap_cells = cc; TRY(ensure(ctx, t->cells, cc * 4)); }
+            if (pc > t->cap_pp) { t->cap_pp = pc; TRY(ensure(ctx, t->pp, pc * 4)); }
+            if (t->h.nnodes + t->h.nnodes / 4 > t->cap_nodes) {
+                t->cap_nodes = t->h.nnodes + t->h.nnodes / 4 + 1024;
+                t->nd_a.release(); t->nd_b.release(); t->nd_r.release(); t->nd_c.release();
+                t->nd_q.release(); t->nd_t.release(); t->nd_f.release(); t->tmp_a.release(); t->tmp_b.release();
+                TRY(alloc_build(t, n, C));
+            }
+            if (want_nb) TRY(alloc_pairs(t, std::max<unsigned long long>(t->cap_pairs, t->h.npairs * 2 + 1024)));
+            if (t->gexec) cudaGraphExecDestroy(t->gexec);
+            t->gexec = nullptr;
+            const Status keep = t->h;
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            int rc = enqueue_batch(t, host_io, want_nb);
+            cudaError_t ec = cudaStreamEndCapture(st, &g);
+            if (rc != PT_OK) return rc;
+            if (ec != cudaSuccess) return fail(ctx, PT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+            ec = cudaGraphInstantiate(&t->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ec != cudaSuccess) {
+                t->gexec = nullptr;
+                return fail(ctx, PT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+            }
+            t->gkey_mode = mode;
+            t->gkey_p = *params;
+            t->gkey_n.resize(C);
+            t->gkey_r.resize(2 * C);
+            for (int c = 0; c < C; c++) {
+                t->gkey_n[c] = (unsigned)d[c].n;
+                t->gkey_r[2 * c] = d[c].r_in;
+                t->gkey_r[2 * c + 1] = d[c].r_out;
+            }
+            t->h = keep;
+        }
+    }
+    // outputs
+    int rc = PT_OK;
+    if (host_io) {
+        for (int c = 0; c < C; c++) {
+            const size_t b = t->h_sets[c].begin, m = (size_t)d[c].n;
+            std::memcpy(d[c].acc, t->h_io + 3 * b, m * 24);
+            std::memcpy(d[c].pot, t->h_io + 3ull * n + b, m * 8);
+        }
+    }
+    if (want_nb) {
+        if (host_io) {
+            const unsigned long long np = std::min<unsigned long long>(t->h.npairs, t->cap_pairs);
+            TRY(ensure_pinned(ctx, t->h_nboff, t->cap_h_nboff, (size_t)n + 1));
+            TRY(ensure_pinned(ctx, t->h_nbidx, t->cap_h_nb, std::max<size_t>(np, 1)));
+            CK(cudaMemcpyAsync(t->h_nboff, t->nb_off.p, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, st));
+            if (np) CK(cudaMemcpyAsync(t->h_nbidx, t->nb_idx.p, np * 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        for (int c = 0; c < C; c++) {
+            d[c].nb_total = d[c].nb_offsets ? t->h_totals[c] : 0;
+            if (!d[c].nb_offsets) continue;
+            if (d[c].nb_total > d[c].nb_capacity || t->h.npairs > t->cap_pairs) {
+                rc = fail(ctx, PT_ERR_CAPACITY, "cluster %d: neighbour lists need %lld entries, capacity %lld",
+                          c, (long long)d[c].nb_total, (long long)d[c].nb_capacity);
+                continue;
+            }
+            if (host_io) {
+                const size_t b = t->h_sets[c].begin, m = (size_t)d[c].n;
+                const long long o0 = t->h_nboff[b];
+                for (size_t k = 0; k <= m; k++) d[c].nb_offsets[k] = t->h_nboff[b + k] - o0;
+                for (long long e = 0; e < d[c].nb_total; e++) d[c].nb_idx[e] = t->h_nbidx[o0 + e] - (int)b;
+            }
+        }
+    } else {
+        for (int c = 0; c < C; c++) d[c].nb_total = 0;
+    }
+    fill_stats(t, stats, ms);
+    return rc;
 }
 
 }  // namespace
@@ -763,8 +1106,9 @@ int pt_tree_lists(pt_tree *t, int64_t *cell_off, uint32_t *cells, int64_t *pp_of
 
 int pt_batch_longrange_force(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc,
                              const pt_params *params, int flags, pt_stats *stats) {
-    (void)n_clusters; (void)desc; (void)params; (void)flags; (void)stats;
-    return fail(ctx, PT_ERR_INTERNAL, "pt_batch_longrange_force: not built yet");
+    if (!ctx) return PT_ERR_ARG;
+    ctx->err[0] = 0;
+    return batch_impl(ctx, n_clusters, desc, params, flags, stats);
 }
 
 }  // extern "C"

@@ -33,7 +33,8 @@ namespace pt {
 constexpr int kFWarps = 4;
 constexpr int kFThreads = 32 * kFWarps;
 constexpr int kJ = 64;        // list entries per warp tile
-constexpr int kIB = 64;       // targets per pass (two per lane)
+constexpr int kIB = 64;       // targets per pass of the float64 kernel (two per lane)
+constexpr int kSlotMax = 96;  // largest pass of the mixed kernel
 
 __device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
     const float s = __fadd_rn(hi, x);
@@ -76,15 +77,23 @@ __device__ __forceinline__ Chg make_chg(const SetInfo &S) {
 // ===========================================================================
 
 struct ChgF {
-    float invw, c0, c2, lam, c35l, tiny, rout2m;
+    float invw, c0, c2, c35l, w0, w1, w2, w3, tiny, rout2m;
 };
 
-template <int NI, int ORDER>
+// Lane layout of one warp for a pass over up to NI * L targets: the warp's
+// lanes form J = 32 / L sub-streams of L lanes; lane (s, l) holds targets
+// l, l + L, .., l + (NI-1) L and takes list entries s, s + J, .. of every
+// tile, so all lanes of a sub-stream read the same entry (shared-memory
+// broadcast).  The configuration is picked per pass as the smallest slot
+// count NI * L that covers the remaining targets, which keeps most lanes busy
+// for the uneven group sizes a tree produces.
+template <int NI, int J, int ORDER>
 __device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB, const float2 *sC,
-                                             int cnt, const float (&ox)[2], const float (&oy)[2],
-                                             const float (&oz)[2], float (&pa)[2][4]) {
+                                             int s, int cnt, const float (&ox)[NI],
+                                             const float (&oy)[NI], const float (&oz)[NI],
+                                             float (&pa)[NI][4]) {
 #pragma unroll 2
-    for (int j = 0; j < cnt; j++) {
+    for (int j = s; j < cnt; j += J) {
         const float4 c = sA[j];
         float4 q;
         float2 q2;
@@ -93,8 +102,8 @@ __device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB,
             q2 = sC[j];
         }
 #pragma unroll
-        for (int s = 0; s < NI; s++) {
-            const float dx = c.x - ox[s], dy = c.y - oy[s], dz = c.z - oz[s];
+        for (int k = 0; k < NI; k++) {
+            const float dx = c.x - ox[k], dy = c.y - oy[k], dz = c.z - oz[k];
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float rinv = rsqrtf(r2);
             const float rinv2 = rinv * rinv;
@@ -109,166 +118,234 @@ __device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB,
                 const float rinv5 = rinv2 * rinv2 * rinv;
                 const float t = dqd * rinv5;
                 const float f = fmaf(2.5f * t, rinv2, mr3);
-                pa[s][0] = fmaf(-qx, rinv5, fmaf(f, dx, pa[s][0]));
-                pa[s][1] = fmaf(-qy, rinv5, fmaf(f, dy, pa[s][1]));
-                pa[s][2] = fmaf(-qz, rinv5, fmaf(f, dz, pa[s][2]));
-                pa[s][3] = fmaf(0.5f, t, pa[s][3] + mr);
+                pa[k][0] = fmaf(-qx, rinv5, fmaf(f, dx, pa[k][0]));
+                pa[k][1] = fmaf(-qy, rinv5, fmaf(f, dy, pa[k][1]));
+                pa[k][2] = fmaf(-qz, rinv5, fmaf(f, dz, pa[k][2]));
+                pa[k][3] = fmaf(0.5f, t, pa[k][3] + mr);
             } else {
-                pa[s][0] = fmaf(mr3, dx, pa[s][0]);
-                pa[s][1] = fmaf(mr3, dy, pa[s][1]);
-                pa[s][2] = fmaf(mr3, dz, pa[s][2]);
-                pa[s][3] += mr;
+                pa[k][0] = fmaf(mr3, dx, pa[k][0]);
+                pa[k][1] = fmaf(mr3, dy, pa[k][1]);
+                pa[k][2] = fmaf(mr3, dz, pa[k][2]);
+                pa[k][3] += mr;
             }
         }
     }
 }
 
-template <int NI, bool NB>
+// PP tile.  Every lane runs the same number of iterations (the tile is
+// padded to a multiple of J with massless entries far away), so the warp can
+// vote per iteration: when no pair of the iteration lies within r_out (float
+// r^2 below r_out^2 (1 + 2^-10)), K = W = 0 exactly for all of them and the
+// plain Newtonian pair is evaluated; otherwise every lane takes the full
+// changeover path and neighbour candidates are confirmed in float64.
+template <int NI, int J, bool NB>
 __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, const float4 *sL,
-                                          int cnt, const ChgF &C, const float (&hx)[2],
-                                          const float (&hy)[2], const float (&hz)[2],
-                                          const float (&lx)[2], const float (&ly)[2],
-                                          const float (&lz)[2], const unsigned (&pid)[2],
-                                          const bool (&valid)[2], double rout2,
-                                          float (&pa)[2][4]) {
+                                          int s, int cnt, const ChgF &C, const float (&hx)[NI],
+                                          const float (&hy)[NI], const float (&hz)[NI],
+                                          const float (&lx)[NI], const float (&ly)[NI],
+                                          const float (&lz)[NI], const unsigned (&pid)[NI],
+                                          const bool (&valid)[NI], int nvalid, double rout2,
+                                          float (&pa)[NI][4], unsigned &n_full, unsigned &n_fast) {
+    const int iters = (cnt + J - 1) / J;
 #pragma unroll 2
-    for (int j = 0; j < cnt; j++) {
+    for (int it = 0; it < iters; it++) {
+        const int j = it * J + s;
         const float4 H = sH[j];
         const float4 L = sL[j];
+        float dx[NI], dy[NI], dz[NI], r2[NI];
+        bool near = false;
 #pragma unroll
-        for (int s = 0; s < NI; s++) {
-            const float dx = (H.x - hx[s]) + (L.x - lx[s]);
-            const float dy = (H.y - hy[s]) + (L.y - ly[s]);
-            const float dz = (H.z - hz[s]) + (L.z - lz[s]);
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (NB && r2 < C.rout2m) {
-                const unsigned pj = __float_as_uint(L.w);
-                if (valid[s] && pj != pid[s] && exact_r2(A.sp64[pid[s]], A.sp64[pj]) < rout2)
-                    emit_pair(A, pid[s], pj);
+        for (int k = 0; k < NI; k++) {
+            dx[k] = (H.x - hx[k]) + (L.x - lx[k]);
+            dy[k] = (H.y - hy[k]) + (L.y - ly[k]);
+            dz[k] = (H.z - hz[k]) + (L.z - lz[k]);
+            r2[k] = fmaf(dz[k], dz[k], fmaf(dy[k], dy[k], dx[k] * dx[k]));
+            near |= r2[k] < C.rout2m;
+        }
+        const unsigned real = (j < cnt) ? (unsigned)nvalid : 0u;
+        if (__any_sync(0xffffffffu, near)) {
+            n_full += real;
+#pragma unroll
+            for (int k = 0; k < NI; k++) {
+                if (NB && r2[k] < C.rout2m) {
+                    const unsigned pj = __float_as_uint(L.w);
+                    if (valid[k] && j < cnt && pj != pid[k] &&
+                        exact_r2(A.sp64[pid[k]], A.sp64[pj]) < rout2)
+                        emit_pair(A, pid[k], pj);
+                }
+                const float r2c = fmaxf(r2[k], C.tiny);
+                const float rinv = rsqrtf(r2c);
+                const float r = r2c * rinv;
+                const float xs = __saturatef(fmaf(r, C.invw, C.c0));
+                // K(xs) = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4)
+                const float t = xs - 1.0f;
+                const float t2 = t * t;
+                const float kq = fmaf(fmaf(fmaf(fmaf(C.c35l, xs, 20.0f), xs, 10.0f), xs, 4.0f), xs, 1.0f);
+                const float omk = fmaf(-t2 * t2, kq, 1.0f);          // 1 - K
+                // 1 - W = min(2r/(r_out+r_in) - Lambda xs^5 (14 - 28 xs + 20 xs^2 - 5 xs^3), 1),
+                // with Lambda folded into the cubic's coefficients
+                const float x2 = xs * xs;
+                const float x5 = x2 * x2 * xs;
+                const float wp = fmaf(fmaf(fmaf(C.w3, xs, C.w2), xs, C.w1), xs, C.w0);
+                const float omw = fminf(fmaf(-x5, wp, r * C.c2), 1.0f);
+                const float mr = H.w * rinv;
+                const float fk = (omk * mr) * (rinv * rinv);
+                pa[k][0] = fmaf(fk, dx[k], pa[k][0]);
+                pa[k][1] = fmaf(fk, dy[k], pa[k][1]);
+                pa[k][2] = fmaf(fk, dz[k], pa[k][2]);
+                pa[k][3] = fmaf(omw, mr, pa[k][3]);
             }
-            const float r2c = fmaxf(r2, C.tiny);
-            const float rinv = rsqrtf(r2c);
-            const float r = r2c * rinv;
-            const float xs = __saturatef(fmaf(r, C.invw, C.c0));
-            // K(xs) = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4)
-            const float t = xs - 1.0f;
-            const float t2 = t * t;
-            const float kq = fmaf(fmaf(fmaf(fmaf(C.c35l, xs, 20.0f), xs, 10.0f), xs, 4.0f), xs, 1.0f);
-            const float omk = fmaf(-t2 * t2, kq, 1.0f);          // 1 - K
-            // 1 - W = min(2r/(r_out+r_in) - Lambda xs^5 (14 - 28 xs + 20 xs^2 - 5 xs^3), 1)
-            const float x2 = xs * xs;
-            const float x5 = x2 * x2 * xs;
-            const float wp = fmaf(fmaf(fmaf(-5.0f, xs, 20.0f), xs, -28.0f), xs, 14.0f);
-            const float omw = fminf(fmaf(-C.lam * x5, wp, r * C.c2), 1.0f);
-            const float mr = H.w * rinv;
-            const float fk = (omk * mr) * (rinv * rinv);
-            pa[s][0] = fmaf(fk, dx, pa[s][0]);
-            pa[s][1] = fmaf(fk, dy, pa[s][1]);
-            pa[s][2] = fmaf(fk, dz, pa[s][2]);
-            pa[s][3] = fmaf(omw, mr, pa[s][3]);
+        } else {
+            n_fast += real;
+#pragma unroll
+            for (int k = 0; k < NI; k++) {
+                const float rinv = rsqrtf(r2[k]);
+                const float mr = H.w * rinv;
+                const float mr3 = mr * (rinv * rinv);
+                pa[k][0] = fmaf(mr3, dx[k], pa[k][0]);
+                pa[k][1] = fmaf(mr3, dy[k], pa[k][1]);
+                pa[k][2] = fmaf(mr3, dz[k], pa[k][2]);
+                pa[k][3] += mr;
+            }
         }
     }
 }
 
 template <int NI>
-__device__ __forceinline__ void fold(float (&pa)[2][4], float (&fh)[2][4], float (&fl)[2][4]) {
+__device__ __forceinline__ void fold(float (&pa)[NI][4], float (&fh)[NI][4], float (&fl)[NI][4]) {
 #pragma unroll
-    for (int s = 0; s < NI; s++)
+    for (int k = 0; k < NI; k++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            ff_add(fh[s][c], fl[s][c], pa[s][c]);
-            pa[s][c] = 0.0f;
+            ff_add(fh[k][c], fl[k][c], pa[k][c]);
+            pa[k][c] = 0.0f;
         }
 }
 
-template <int NI, int ORDER, bool NB>
+template <int NI, int J, int ORDER, bool NB>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                              const ChgF &C, double rout2, float4 (*sA)[kJ], float4 (*sB)[kJ],
-                             float2 (*sC)[kJ], double (*red)[kIB][4]) {
+                             float2 (*sC)[kJ], double (*red)[kSlotMax][4]) {
+    constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = lane / L, l = lane % L;
     const float4 Hg = A.spH[gr.x], Lg = A.spL[gr.x];
-    float hx[2], hy[2], hz[2], lx[2], ly[2], lz[2], ox[2], oy[2], oz[2];
-    unsigned pid[2];
-    bool valid[2];
+    unsigned pid[NI];
+    bool valid[NI];
 #pragma unroll
-    for (int s = 0; s < 2; s++) {
-        const unsigned idx = i0 + lane + 32 * s;
-        valid[s] = idx < gr.y;
-        pid[s] = gr.x + (valid[s] ? idx : 0u);
-        const float4 H = A.spH[pid[s]], L = A.spL[pid[s]];
-        hx[s] = H.x; hy[s] = H.y; hz[s] = H.z;
-        lx[s] = L.x; ly[s] = L.y; lz[s] = L.z;
-        ox[s] = (H.x - Hg.x) + (L.x - Lg.x);
-        oy[s] = (H.y - Hg.y) + (L.y - Lg.y);
-        oz[s] = (H.z - Hg.z) + (L.z - Lg.z);
+    for (int k = 0; k < NI; k++) {
+        const unsigned idx = i0 + l + L * k;
+        valid[k] = idx < gr.y;
+        pid[k] = gr.x + (valid[k] ? idx : 0u);
     }
-    float pa[2][4], fh[2][4], fl[2][4];
+    float pa[NI][4], fh[NI][4], fl[NI][4];
 #pragma unroll
-    for (int s = 0; s < 2; s++)
+    for (int k = 0; k < NI; k++)
 #pragma unroll
-        for (int c = 0; c < 4; c++) pa[s][c] = fh[s][c] = fl[s][c] = 0.0f;
-    // ---- cells
-    const unsigned nc = A.gr_nc[g];
-    const unsigned long long co = A.gr_co[g];
-    for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
-        const int cnt = (int)min((unsigned)kJ, nc - t);
+        for (int c = 0; c < 4; c++) pa[k][c] = fh[k][c] = fl[k][c] = 0.0f;
+    // ---- cells: float offsets from the group's first particle
+    {
+        float ox[NI], oy[NI], oz[NI];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int e = lane + 32 * h;
-            if (e < cnt) {
-                const unsigned v = A.cells[co + t + e];
-                const float4 f0 = A.nd_f[4 * v], f1 = A.nd_f[4 * v + 1];
-                sA[w][e] = make_float4((f0.x - Hg.x) + (f1.x - Lg.x), (f0.y - Hg.y) + (f1.y - Lg.y),
-                                       (f0.z - Hg.z) + (f1.z - Lg.z), f0.w);
-                if (ORDER == 2) {
-                    const float4 f2 = A.nd_f[4 * v + 2], f3 = A.nd_f[4 * v + 3];
-                    sB[w][e] = make_float4(f1.w, f2.x, f2.y, f2.z);
-                    sC[w][e] = make_float2(f2.w, f3.x);
+        for (int k = 0; k < NI; k++) {
+            const float4 H = A.spH[pid[k]], L4 = A.spL[pid[k]];
+            ox[k] = (H.x - Hg.x) + (L4.x - Lg.x);
+            oy[k] = (H.y - Hg.y) + (L4.y - Lg.y);
+            oz[k] = (H.z - Hg.z) + (L4.z - Lg.z);
+        }
+        const unsigned nc = A.gr_nc[g];
+        const unsigned long long co = A.gr_co[g];
+        for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
+            const int cnt = (int)min((unsigned)kJ, nc - t);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int e = lane + 32 * h;
+                if (e < cnt) {
+                    const unsigned v = A.cells[co + t + e];
+                    const float4 f0 = A.nd_f[4 * v], f1 = A.nd_f[4 * v + 1];
+                    sA[w][e] = make_float4((f0.x - Hg.x) + (f1.x - Lg.x), (f0.y - Hg.y) + (f1.y - Lg.y),
+                                           (f0.z - Hg.z) + (f1.z - Lg.z), f0.w);
+                    if (ORDER == 2) {
+                        const float4 f2 = A.nd_f[4 * v + 2], f3 = A.nd_f[4 * v + 3];
+                        sB[w][e] = make_float4(f1.w, f2.x, f2.y, f2.z);
+                        sC[w][e] = make_float2(f2.w, f3.x);
+                    }
                 }
             }
+            __syncwarp();
+            cells_tile_f<NI, J, ORDER>(sA[w], sB[w], sC[w], s, cnt, ox, oy, oz, pa);
+            __syncwarp();
+            fold<NI>(pa, fh, fl);
         }
-        __syncwarp();
-        cells_tile_f<NI, ORDER>(sA[w], sB[w], sC[w], cnt, ox, oy, oz, pa);
-        __syncwarp();
-        fold<NI>(pa, fh, fl);
     }
-    // ---- particle-particle
-    const unsigned np = A.gr_np[g];
-    const unsigned long long po = A.gr_po[g];
-    for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
-        const int cnt = (int)min((unsigned)kJ, np - t);
+    // ---- particle-particle: float-float differences
+    {
+        float hx[NI], hy[NI], hz[NI], lx[NI], ly[NI], lz[NI];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int e = lane + 32 * h;
-            if (e < cnt) {
-                const unsigned p = A.pp[po + t + e];
-                sA[w][e] = A.spH[p];
-                float4 L = A.spL[p];
-                L.w = __uint_as_float(p);
-                sB[w][e] = L;
+        for (int k = 0; k < NI; k++) {
+            const float4 H = A.spH[pid[k]], L4 = A.spL[pid[k]];
+            hx[k] = H.x; hy[k] = H.y; hz[k] = H.z;
+            lx[k] = L4.x; ly[k] = L4.y; lz[k] = L4.z;
+        }
+        int nvalid = 0;
+#pragma unroll
+        for (int k = 0; k < NI; k++) nvalid += valid[k] ? 1 : 0;
+        unsigned n_full = 0, n_fast = 0;
+        const unsigned np = A.gr_np[g];
+        const unsigned long long po = A.gr_po[g];
+        for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
+            const int cnt = (int)min((unsigned)kJ, np - t);
+            const int cntJ = (cnt + J - 1) / J * J;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int e = lane + 32 * h;
+                if (e < cnt) {
+                    const unsigned p = A.pp[po + t + e];
+                    sA[w][e] = A.spH[p];
+                    float4 L4 = A.spL[p];
+                    L4.w = __uint_as_float(p);
+                    sB[w][e] = L4;
+                } else if (e < cntJ) {                    // massless, far away
+                    sA[w][e] = make_float4(1e15f, 1e15f, 1e15f, 0.0f);
+                    sB[w][e] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(0xffffffffu));
+                }
             }
+            __syncwarp();
+            if (NB && A.want_nb)
+                pp_tile_f<NI, J, true>(A, sA[w], sB[w], s, cnt, C, hx, hy, hz, lx, ly, lz, pid, valid,
+                                       nvalid, rout2, pa, n_full, n_fast);
+            else
+                pp_tile_f<NI, J, false>(A, sA[w], sB[w], s, cnt, C, hx, hy, hz, lx, ly, lz, pid, valid,
+                                        nvalid, rout2, pa, n_full, n_fast);
+            __syncwarp();
+            fold<NI>(pa, fh, fl);
         }
-        __syncwarp();
-        if (NB && A.want_nb)
-            pp_tile_f<NI, true>(A, sA[w], sB[w], cnt, C, hx, hy, hz, lx, ly, lz, pid, valid, rout2, pa);
-        else
-            pp_tile_f<NI, false>(A, sA[w], sB[w], cnt, C, hx, hy, hz, lx, ly, lz, pid, valid, rout2, pa);
-        __syncwarp();
-        fold<NI>(pa, fh, fl);
+        n_full = warp_sum(n_full);
+        n_fast = warp_sum(n_fast);
+        if (lane == 0 && (n_full | n_fast)) {
+            atomicAdd(&A.st->pp_full, (unsigned long long)n_full);
+            atomicAdd(&A.st->pp_fast, (unsigned long long)n_fast);
+        }
     }
+    // ---- sum the J sub-streams of each target, then hand over to the block
 #pragma unroll
-    for (int s = 0; s < 2; s++)
+    for (int k = 0; k < NI; k++)
 #pragma unroll
-        for (int c = 0; c < 4; c++)
-            red[w][lane + 32 * s][c] = (s < NI) ? (double)fh[s][c] + (double)fl[s][c] : 0.0;
+        for (int c = 0; c < 4; c++) {
+            double v = (double)fh[k][c] + (double)fl[k][c];
+#pragma unroll
+            for (int o = L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (s == 0) red[w][l + L * k][c] = v;
+        }
 }
 
-// Final per-target sums (threads 0..kIB-1): fixed-order float64 reduction over
-// the warps, removal of the self entry, output in caller order.
+// Final per-target sums (threads 0..slots-1): fixed-order float64 reduction
+// over the warps, removal of the self entry, output in caller order.
 __device__ __forceinline__ void write_targets(const ForceArgs &A, const uint2 gr, unsigned i0,
-                                              double c2, double (*red)[kIB][4], double (&ep)[4]) {
+                                              unsigned slots, double c2, double (*red)[kSlotMax][4],
+                                              double (&ep)[4]) {
     const unsigned t = threadIdx.x;
-    if (t < kIB && i0 + t < gr.y) {
+    if (t < slots && i0 + t < gr.y) {
         double s[4] = {0, 0, 0, 0};
         for (int w = 0; w < kFWarps; w++)
             for (int c = 0; c < 4; c++) s[c] += red[w][t][c];
@@ -290,7 +367,6 @@ __device__ __forceinline__ void write_targets(const ForceArgs &A, const uint2 gr
 
 __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, double (&ep)[4],
                                                double (*ered)[4]) {
-    // threads 0..63 (warps 0 and 1) hold the partials
     const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < 4; c++) ep[c] = warp_sum(ep[c]);
@@ -298,18 +374,34 @@ __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, d
         for (int c = 0; c < 4; c++) ered[w][c] = ep[c];
     __syncthreads();
     if (threadIdx.x == 0) {
-        double e[4];
-        for (int c = 0; c < 4; c++) e[c] = ered[0][c] + ered[1][c];
+        double e[4] = {0, 0, 0, 0};
+        for (int k = 0; k < kFWarps; k++)
+            for (int c = 0; c < 4; c++) e[c] += ered[k][c];
         A.gpart[g] = make_double4(e[0], e[1], e[2], e[3]);
     }
 }
 
+// Pass configuration for `rem` remaining targets: returns the slot count and
+// runs the matching instantiation.
 template <int ORDER, bool NB>
-__global__ void __launch_bounds__(kFThreads) k_force_mixed(ForceArgs A) {
+__device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
+                               const ChgF &C, double rout2, float4 (*sA)[kJ], float4 (*sB)[kJ],
+                               float2 (*sC)[kJ], double (*red)[kSlotMax][4]) {
+    const unsigned rem = gr.y - i0;
+    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 24; }
+    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 32; }
+    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 48; }
+    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 64; }
+    group_pass_f<3, 1, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red);
+    return 96;
+}
+
+template <int ORDER, bool NB>
+__global__ void __launch_bounds__(kFThreads, 4) k_force_mixed(ForceArgs A) {
     __shared__ float4 sA[kFWarps][kJ];
     __shared__ float4 sB[kFWarps][kJ];
     __shared__ float2 sC[kFWarps][kJ];
-    __shared__ double red[kFWarps][kIB][4];
+    __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
     const unsigned ng = A.st->ngroups;
@@ -325,19 +417,20 @@ __global__ void __launch_bounds__(kFThreads) k_force_mixed(ForceArgs A) {
         C.invw = (float)C64.invw;
         C.c0 = (float)C64.c0;
         C.c2 = (float)C64.c2;
-        C.lam = (float)C64.lam;
         C.c35l = (float)(35.0 * C64.lam);
+        C.w0 = (float)(14.0 * C64.lam);
+        C.w1 = (float)(-28.0 * C64.lam);
+        C.w2 = (float)(20.0 * C64.lam);
+        C.w3 = (float)(-5.0 * C64.lam);
         C.tiny = fmaxf((float)C64.tiny, 1e-36f);
         C.rout2m = (float)(C64.rout2 * (1.0 + 1.0 / 1024.0));
         double ep[4] = {0, 0, 0, 0};
-        for (unsigned i0 = 0; i0 < gr.y; i0 += kIB) {
-            if (gr.y - i0 > 32)
-                group_pass_f<2, ORDER, NB>(A, g, gr, i0, C, C64.rout2, sA, sB, sC, red);
-            else
-                group_pass_f<1, ORDER, NB>(A, g, gr, i0, C, C64.rout2, sA, sB, sC, red);
+        for (unsigned i0 = 0; i0 < gr.y;) {
+            const unsigned slots = mixed_pass<ORDER, NB>(A, g, gr, i0, C, C64.rout2, sA, sB, sC, red);
             __syncthreads();
-            write_targets(A, gr, i0, C64.c2, red, ep);
+            write_targets(A, gr, i0, slots, C64.c2, red, ep);
             __syncthreads();
+            i0 += slots;
         }
         group_partials(A, g, ep, ered);
     }
@@ -430,7 +523,7 @@ __device__ __forceinline__ void pp_tile_d(const ForceArgs &A, const double4 *sP,
 template <int NI, int ORDER, bool NB>
 __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                              const Chg &C, double4 (*sA)[kJ], double4 (*sB)[kJ],
-                             double2 (*sC)[kJ], unsigned (*sI)[kJ], double (*red)[kIB][4]) {
+                             double2 (*sC)[kJ], unsigned (*sI)[kJ], double (*red)[kSlotMax][4]) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double xx[2], xy[2], xz[2];
     unsigned pid[2];
@@ -501,7 +594,7 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     __shared__ double4 sB[kFWarps][kJ];
     __shared__ double2 sC[kFWarps][kJ];
     __shared__ unsigned sI[kFWarps][kJ];
-    __shared__ double red[kFWarps][kIB][4];
+    __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
     const unsigned ng = A.st->ngroups;
@@ -520,7 +613,7 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
             else
                 group_pass_d<1, ORDER, NB>(A, g, gr, i0, C, sA, sB, sC, sI, red);
             __syncthreads();
-            write_targets(A, gr, i0, C.c2, red, ep);
+            write_targets(A, gr, i0, kIB, C.c2, red, ep);
             __syncthreads();
         }
         group_partials(A, g, ep, ered);

@@ -54,9 +54,12 @@ struct Status {
     unsigned nnodes;
     unsigned ngroups;
     unsigned max_level;
+    unsigned max_stack;              // deepest walk stack seen (entries per warp)
+    unsigned pad0;
     unsigned long long cell_total, pp_total;
     unsigned long long cell_inter, pp_inter;
     unsigned long long npairs;
+    unsigned long long pp_full, pp_fast;   // mixed PP pairs on the changeover / Newtonian path
     unsigned long long work[4];      // work counters for persistent kernels
     double energy, mom[3];
     unsigned lvl_begin[kLevels + 1];
@@ -142,9 +145,10 @@ int scan_exclusive(const unsigned *in, OutT *out, const unsigned *n_dev,
 struct SortTmp {
     unsigned long long *k2;  // n_max
     unsigned *v2;            // n_max
-    unsigned *counts;        // 256 * kSortBlocks
+    unsigned *counts;        // kSortCountsLen
 };
 constexpr int kSortBlocks = 304;
+constexpr int kSortCountsLen = 256 * kSortBlocks + 256;   // per-block digit counts + digit totals
 int radix_sort(const unsigned long long *keys_in, const unsigned *vals_in,
                 unsigned long long *keys_out, unsigned *vals_out,
                 const unsigned *n_dev, unsigned n_max, int bit0, int bit1,

@@ -6,7 +6,8 @@
 
 namespace pt {
 
-constexpr int kWalkStack = 2048;     // per-warp walk stack (shared memory)
+constexpr unsigned kWalkStackSmall = 2048;   // per-warp walk stack entries (shared memory)
+constexpr unsigned kWalkStackLarge = 12288;  // retry size after an overflow
 constexpr unsigned kWalkMaxIters = 1u << 24;   // safety cap on walk iterations per group
 
 struct BuildArgs {
@@ -53,6 +54,7 @@ struct WalkArgs {
     unsigned long long *gr_co, *gr_po;   // ngroups + 1
     unsigned *cells, *pp;
     unsigned long long cap_cells, cap_pp;
+    unsigned stack_cap;                  // stack entries per warp
     Status *st;
     ScanTmp scan_tmp;
 };
@@ -94,6 +96,22 @@ struct NbArgs {
     SortTmp sort_tmp;
 };
 
+// Per-set pointer table of a batch (device resident).
+struct BatchTab {
+    const double *pos, *mass;
+    double *acc, *pot;
+    long long *nb_off;
+    int *nb_idx;
+    unsigned long long nb_cap;
+};
+
+int batch_gather_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
+                        double *pos, double *mass, cudaStream_t st);
+int batch_scatter_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
+                         const double *acc, const double *pot, cudaStream_t st);
+int batch_nb_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
+                    const long long *off, const int *idx, long long *totals, bool split,
+                    cudaStream_t st);
 int build_launch(const BuildArgs &A, cudaStream_t st);   // returns kernels launched
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st);

@@ -29,7 +29,7 @@ constexpr size_t kOffVals = 0;                                               // 
 constexpr size_t kOffKeys2 = align_up(kOffVals + 4 * (size_t)kNoallocMaxN);  // u64 x max n
 constexpr size_t kOffVals2 = align_up(kOffKeys2 + 8 * (size_t)kNoallocMaxN); // u32 x max n
 constexpr size_t kOffCounts = align_up(kOffVals2 + 4 * (size_t)kNoallocMaxN);
-constexpr size_t kOffN = align_up(kOffCounts + 4 * 256 * (size_t)pt::kSortBlocks);
+constexpr size_t kOffN = align_up(kOffCounts + 4 * (size_t)pt::kSortCountsLen);
 constexpr size_t kNoallocBytes = align_up(kOffN + 16);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];

@@ -117,6 +117,7 @@ constexpr int kSortThreads = 256;               // 8 warps; one thread per digit
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortRounds = 4;                  // 32-item rounds per warp per tile
 constexpr int kSortTile = kSortThreads * kSortRounds;   // 1024 items
+constexpr int kSortScanThreads = 320;                   // >= kSortBlocks, multiple of 32
 
 template <bool SET_PASS>
 __device__ __forceinline__ unsigned digit_of(unsigned long long k, unsigned v, int shift,
@@ -144,20 +145,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const unsigned long 
     counts[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// One block: exclusive scan of the digit-major counts matrix (256 x nb).
-__global__ void __launch_bounds__(1024) k_sort_scan(unsigned *counts, int total) {
+// One block per digit: exclusive scan of that digit's per-block counts (in
+// place) and the digit's total in counts[256 * nb + digit].
+__global__ void __launch_bounds__(kSortScanThreads) k_sort_scan(unsigned *counts, int nb) {
     __shared__ unsigned long long sh[32];
-    const int per = (total + 1023) / 1024;
-    const int lo = threadIdx.x * per;
-    unsigned long long s = 0;
-    for (int i = lo; i < lo + per && i < total; i++) s += counts[i];
-    unsigned long long inc = block_incl_scan(s, sh);
-    unsigned long long run = inc - s;
-    for (int i = lo; i < lo + per && i < total; i++) {
-        unsigned c = counts[i];
-        counts[i] = (unsigned)run;
-        run += c;
-    }
+    const int d = blockIdx.x;
+    const unsigned v = (threadIdx.x < (unsigned)nb) ? counts[d * nb + threadIdx.x] : 0u;
+    const unsigned long long inc = block_incl_scan(v, sh);
+    if (threadIdx.x < (unsigned)nb) counts[d * nb + threadIdx.x] = (unsigned)(inc - v);
+    if (threadIdx.x == blockDim.x - 1) counts[256 * nb + d] = (unsigned)inc;
 }
 
 template <bool SET_PASS>
@@ -168,10 +164,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     __shared__ unsigned hist[kSortWarps][256];
     __shared__ unsigned off[kSortWarps][256];
     __shared__ unsigned run[256];
+    __shared__ unsigned long long scan_sh[32];
     const unsigned w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned lo, hi;
     chunk_of(*n_dev, blockIdx.x, gridDim.x, lo, hi);
-    run[threadIdx.x] = offsets[threadIdx.x * gridDim.x + blockIdx.x];
+    {   // start of this digit's bucket = sum of the smaller digits' totals
+        const unsigned tot = offsets[256 * gridDim.x + threadIdx.x];
+        const unsigned long long base = block_incl_scan(tot, scan_sh) - tot;
+        run[threadIdx.x] = (unsigned)base + offsets[threadIdx.x * gridDim.x + blockIdx.x];
+    }
     for (unsigned base = lo; base < hi; base += kSortTile) {
         for (int k = 0; k < kSortWarps; k++) hist[k][threadIdx.x] = 0;
         __syncthreads();
@@ -234,11 +235,11 @@ int radix_sort(const unsigned long long *keys_in, const unsigned *vals_in,
         unsigned *vd = to_out ? vals_out : tmp.v2;
         if (set_pass) {
             k_sort_hist<true><<<kSortBlocks, kSortThreads, 0, st>>>(ks, vs, n_dev, shift, set_of, tmp.counts);
-            k_sort_scan<<<1, 1024, 0, st>>>(tmp.counts, 256 * kSortBlocks);
+            k_sort_scan<<<256, kSortScanThreads, 0, st>>>(tmp.counts, kSortBlocks);
             k_sort_scatter<true><<<kSortBlocks, kSortThreads, 0, st>>>(ks, vs, kd, vd, n_dev, shift, set_of, tmp.counts);
         } else {
             k_sort_hist<false><<<kSortBlocks, kSortThreads, 0, st>>>(ks, vs, n_dev, shift, nullptr, tmp.counts);
-            k_sort_scan<<<1, 1024, 0, st>>>(tmp.counts, 256 * kSortBlocks);
+            k_sort_scan<<<256, kSortScanThreads, 0, st>>>(tmp.counts, kSortBlocks);
             k_sort_scatter<false><<<kSortBlocks, kSortThreads, 0, st>>>(ks, vs, kd, vd, n_dev, shift, nullptr, tmp.counts);
         }
         ks = kd;

@@ -18,7 +18,7 @@ constexpr int kWalkThreads = 32 * kWalkWarps;
 
 template <bool FILL>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
-    __shared__ unsigned stack[kWalkWarps][kWalkStack];
+    extern __shared__ unsigned stack_mem[];      // kWalkWarps x A.stack_cap entries
     __shared__ unsigned pfx[kWalkWarps][32];
     __shared__ unsigned pbeg[kWalkWarps][32];
     __shared__ long long ithr[kLevels];
@@ -26,7 +26,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     __syncthreads();
     const unsigned w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned ng = A.st->ngroups;
-    unsigned *stk = stack[w];
+    unsigned *stk = stack_mem + (size_t)w * A.stack_cap;
+    const int cap = (int)A.stack_cap;
+    int max_sp = 0;
     for (;;) {
         unsigned g = 0;
         if (lane == 0) g = atomicAdd(&A.st->work[FILL ? 1 : 0], 1ull);
@@ -128,15 +130,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
             // children of opened internal nodes
             const unsigned cincl = warp_incl_scan(nch);
             const unsigned ctot = __shfl_sync(0xffffffffu, cincl, 31);
-            if (sp + (int)ctot > kWalkStack) {
+            if (sp + (int)ctot > cap) {
                 overflow = true;
                 break;
             }
             for (unsigned j = 0; j < nch; j++) stk[sp + (cincl - nch) + j] = first + j;
             sp += (int)ctot;
+            max_sp = max(max_sp, sp);
             __syncwarp();
         }
         if (overflow && lane == 0) atomicOr(&A.st->flags, kErrStack);
+        if (!FILL && lane == 0) atomicMax(&A.st->max_stack, (unsigned)max_sp);
         if (!FILL && lane == 0) {
             A.gr_nc[g] = nc;
             A.gr_np[g] = np;
@@ -146,10 +150,15 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
 }
 
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
-    // work counters 0 and 1 are reset by the caller (part of the status block)
-    const int blocks = 152 * 4;
+    // work counters 0 and 1 are reset by the caller (part of the status block).
+    // The walk is latency bound: as many resident warps as the stack allows.
+    const size_t smem = (size_t)kWalkWarps * A.stack_cap * sizeof(unsigned);
+    int per_sm = (int)((200u * 1024u) / (smem + 2048));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
+    const int blocks = 152 * per_sm;
     if (phase == 0) {
-        k_walk<false><<<blocks, kWalkThreads, 0, st>>>(A);
+        cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_walk<false><<<blocks, kWalkThreads, smem, st>>>(A);
         int nk = 1;
         nk += scan_exclusive<unsigned long long>(A.gr_nc, A.gr_co, &A.st->ngroups, &A.st->cell_total,
                                                  nullptr, A.scan_tmp, st);
@@ -157,7 +166,8 @@ int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
                                                  nullptr, A.scan_tmp, st);
         return nk;
     }
-    k_walk<true><<<blocks, kWalkThreads, 0, st>>>(A);
+    cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_walk<true><<<blocks, kWalkThreads, smem, st>>>(A);
     return 1;
 }
 
