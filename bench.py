@@ -60,7 +60,7 @@ FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maxi
 # DRAM bytes per launch of the mixed force kernel from one ncu capture of the
 # same kernel build on this workload (profiles/force_mixed_plummer1m.md);
 # None when the kernel changed after the capture.
-FORCE_MIXED_DRAM_BYTES = None
+FORCE_MIXED_DRAM_BYTES = 1_357_447_000
 
 
 def workload_config(n):
@@ -173,6 +173,77 @@ def run_steps(ctx, tree_holder, pos, mass, prm, out, k, flush=None, timed=True):
     return times, stats
 
 
+def batch_leg(ctx, steps):
+    """Ensemble workload: 256 Kroupa Plummer clusters, N log-uniform in
+    1,024-65,536 (seed 4), theta 0.4, r_out from Eq. 42, r_in = r_out / 10,
+    FP32-mixed, neighbour lists on; n_leaf / n_group from the autotuner.
+    Times one batched pass (uncaptured and as a replayed CUDA graph) against
+    per-cluster calls of the same work."""
+    import torch
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+    ens = inputs.cluster_ensemble(256, 1024, 65536, seed=4)
+    sets = [{"pos": torch.from_numpy(c["pos"]).cuda(), "mass": torch.from_numpy(c["mass"]).cuda(),
+             "r_in": c["r_in"], "r_out": c["r_out"]} for c in ens]
+    ntot = sum(int(c["mass"].shape[0]) for c in ens)
+    bt = B.Batch(sets)
+    base = B.Params(theta=0.4, n_leaf=8, n_group=64, order=2, precision=B.PT_MIXED)
+    t0 = time.perf_counter()
+    tuned, tuned_ms = bt.autotune(ctx, base)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        out, st = [], None
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out, st
+
+    bt.run(ctx, tuned)
+    t_unc, st = timed(lambda: bt.run(ctx, tuned), steps)
+    bt.run(ctx, tuned, graph=True)          # sizes and captures
+    bt.run(ctx, tuned, graph=True)          # first replay
+    t_graph, stg = timed(lambda: bt.run(ctx, tuned, graph=True), steps)
+    # per-cluster calls, each set alone through pt_tree_build + pt_longrange_force
+    trees = [None] * len(sets)
+    prm = [B.Params(**{**tuned.__dict__, "r_in": s_["r_in"], "r_out": s_["r_out"]}) for s_ in sets]
+
+    def per_cluster():
+        tot = 0
+        for k, s_ in enumerate(sets):
+            if trees[k] is None:
+                trees[k] = B.Tree(ctx, s_["pos"], s_["mass"], prm[k])
+            else:
+                trees[k].rebuild(s_["pos"], s_["mass"], prm[k])
+            _, st1, _ = trees[k].force(bt.acc[k], bt.pot[k], bt.nb_off[k], bt.nb_idx[k], bt.descs[k].nb_capacity)
+            tot += st1.cell_interactions + st1.pp_interactions
+        return {"interactions": tot}
+    per_cluster()
+    t_per, stp = timed(per_cluster, max(2, steps // 2))
+    for tr in trees:
+        tr.free()
+    inter = st["cell_interactions"] + st["pp_interactions"]
+    return {
+        "workload": "256 Kroupa Plummer clusters, N log-uniform 1024-65536 (seed 4), theta 0.4, "
+                    "r_out = 0.2 N^-1/3, r_in = r_out/10, quadrupole, FP32-mixed, neighbour lists on",
+        "particles": ntot, "interactions_per_step": inter,
+        "autotuned": {"n_leaf": tuned.n_leaf, "n_group": tuned.n_group, "ms": tuned_ms,
+                      "tuning_s": tune_s},
+        "graph_ms_per_step": statistics.mean(t_graph),
+        "uncaptured_ms_per_step": statistics.mean(t_unc),
+        "per_cluster_ms_per_step": statistics.mean(t_per),
+        "graph_interactions_per_s": inter / (statistics.mean(t_graph) * 1e-3),
+        "per_cluster_interactions_per_s": stp["interactions"] / (statistics.mean(t_per) * 1e-3),
+        "speedup_graph_vs_per_cluster": statistics.mean(t_per) / statistics.mean(t_graph),
+        "launches_per_step": int(stg["launches_force"]),
+    }
+
+
 def cpu_oracle_sample(pos, mass, nsample, seed=11):
     """Oracle tree on the host cores: full build plus the tree force on
     nsample targets; returns the interactions/s it would sustain on the whole
@@ -230,7 +301,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only-mixed", action="store_true", help="skip the FP64 and e2e legs (profiling)")
+    ap.add_argument("--only-mixed", action="store_true", help="skip the FP64, e2e and batch legs (profiling)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-cluster batch leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -371,6 +443,8 @@ def main():
         tree_h.free()
     if holder[0] is not None:
         holder[0].free()
+    if not args.no_batch and not args.only_mixed:
+        line["batch"] = batch_leg(ctx, max(3, args.steps // 2))
     if rank == 0 and not args.no_cpu_baseline:
         v, secs, thr, si = cpu_oracle_sample(d["pos"], d["mass"], args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": thr, "kind": "oracle",

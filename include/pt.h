@@ -189,6 +189,22 @@ typedef struct {
 int pt_batch_longrange_force(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc,
                              const pt_params *params, int flags, pt_stats *stats);
 
+/* Autotuner: evaluates the batch `desc` (one set is a batch of one) with every
+ * (n_leaf, n_group) pair from the candidate lists, timing the device work of
+ * the tree build and the force call (best of `reps` runs after one sizing
+ * run), and writes the fastest parameters to *best (the other fields are
+ * copied from *base) and its time in ms to *best_ms (may be NULL).  NULL or
+ * empty lists select n_leaf in {4, 8, 16, 32} and n_group in
+ * {32, 48, 64, 96, 128}.  Results are cached in the context per (number of
+ * sets, power-of-two buckets of the total and mean set size, theta, order,
+ * precision); a cached entry is returned without timing.  The descriptors'
+ * outputs hold the last candidate's results.  The force kernel's lane layout
+ * (targets per lane and sub-streams per warp) is chosen per group at run
+ * time and needs no tuning. */
+int pt_autotune(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc, const pt_params *base,
+                const int *leaf_candidates, int n_leaf_candidates, const int *group_candidates,
+                int n_group_candidates, int reps, pt_params *best, double *best_ms);
+
 /* ---- introspection (copies to HOST buffers; for tests and tools) ---- */
 
 /* info[0..4] = n, nodes, groups, max level, clusters;

@@ -78,6 +78,8 @@ def lib():
                 "pt_tree_free": (I, [P]),
                 "pt_batch_longrange_force": (I, [P, I, C.POINTER(pt_cluster_desc), C.POINTER(pt_params), I,
                                                  C.POINTER(pt_stats)]),
+                "pt_autotune": (I, [P, I, C.POINTER(pt_cluster_desc), C.POINTER(pt_params), P, I, P, I, I,
+                                    C.POINTER(pt_params), C.POINTER(C.c_double)]),
                 "pt_tree_info": (I, [P, P, P]),
                 "pt_tree_keys": (I, [P, P, P]),
                 "pt_tree_nodes": (I, [P, P, P, P]),
@@ -134,6 +136,17 @@ def pt_batch_longrange_force(ctx, descs, params: pt_params, flags: int = 0):
     st = pt_stats()
     rc = lib().pt_batch_longrange_force(ctx, len(descs), arr, C.byref(params), flags, C.byref(st))
     return rc, arr, st
+
+
+def pt_autotune(ctx, descs, base: pt_params, leafs=None, groups=None, reps: int = 2):
+    arr = (pt_cluster_desc * len(descs))(*descs)
+    la = (C.c_int * len(leafs))(*leafs) if leafs else None
+    ga = (C.c_int * len(groups))(*groups) if groups else None
+    best = pt_params()
+    ms = C.c_double(0.0)
+    rc = lib().pt_autotune(ctx, len(descs), arr, C.byref(base), la, len(leafs) if leafs else 0,
+                           ga, len(groups) if groups else 0, reps, C.byref(best), C.byref(ms))
+    return rc, best, ms.value
 
 
 class PTError(RuntimeError):
@@ -289,6 +302,58 @@ class Tree:
             self.free()
         except Exception:
             pass
+
+
+class Batch:
+    """Device buffers and descriptors for pt_batch_longrange_force over many sets.
+
+    ``sets`` is a list of dicts with float64 CUDA tensors ``pos`` (n, 3) and
+    ``mass`` (n,) and floats ``r_in``, ``r_out``.  Outputs live in
+    ``self.acc[k]``, ``self.pot[k]``, ``self.nb_off[k]``, ``self.nb_idx[k]``.
+    """
+
+    def __init__(self, sets, neighbours: bool = True, nb_factor: int = 8):
+        import torch
+        self.sets = sets
+        self.acc, self.pot, self.nb_off, self.nb_idx, self.descs = [], [], [], [], []
+        for st in sets:
+            n = int(st["mass"].shape[0])
+            dev = st["pos"].device
+            self.acc.append(torch.empty((n, 3), dtype=torch.float64, device=dev))
+            self.pot.append(torch.empty((n,), dtype=torch.float64, device=dev))
+            cap = nb_factor * n + 64
+            self.nb_off.append(torch.empty((n + 1,), dtype=torch.int64, device=dev) if neighbours else None)
+            self.nb_idx.append(torch.empty((cap,), dtype=torch.int32, device=dev) if neighbours else None)
+            d = pt_cluster_desc()
+            d.n = n
+            d.pos, d.mass = _ptr(st["pos"]), _ptr(st["mass"])
+            d.r_in, d.r_out = float(st["r_in"]), float(st["r_out"])
+            d.acc, d.pot = _ptr(self.acc[-1]), _ptr(self.pot[-1])
+            d.nb_offsets = _ptr(self.nb_off[-1])
+            d.nb_idx = _ptr(self.nb_idx[-1])
+            d.nb_capacity = cap if neighbours else 0
+            self.descs.append(d)
+        self.arr = (pt_cluster_desc * len(self.descs))(*self.descs)
+
+    def run(self, ctx: Context, params: Params, graph: bool = False):
+        st = pt_stats()
+        rc = lib().pt_batch_longrange_force(ctx.h, len(self.descs), self.arr, C.byref(params.c()),
+                                            PT_BATCH_GRAPH if graph else 0, C.byref(st))
+        ctx.check(rc, "pt_batch_longrange_force")
+        return st.as_dict()
+
+    def autotune(self, ctx: Context, params: Params, leafs=None, groups=None, reps: int = 2):
+        la = (C.c_int * len(leafs))(*leafs) if leafs else None
+        ga = (C.c_int * len(groups))(*groups) if groups else None
+        best = pt_params()
+        ms = C.c_double(0.0)
+        rc = lib().pt_autotune(ctx.h, len(self.descs), self.arr, C.byref(params.c()), la,
+                               len(leafs) if leafs else 0, ga, len(groups) if groups else 0, reps,
+                               C.byref(best), C.byref(ms))
+        ctx.check(rc, "pt_autotune")
+        out = Params(**params.__dict__)
+        out.n_leaf, out.n_group = best.n_leaf, best.n_group
+        return out, ms.value
 
 
 def longrange_force(ctx: Context, pos, mass, params: Params, neighbours: bool = True,

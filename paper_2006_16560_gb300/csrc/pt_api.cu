@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -21,10 +22,18 @@ using namespace pt;
 struct pt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     char err[512] = {0};
     Status *h_status = nullptr;      // pinned
     cudaEvent_t ev[8] = {};
     pt_tree *batch_tree = nullptr;   // reused by pt_batch_longrange_force
+    struct TuneEntry {
+        int nsets, nbucket, mbucket, order, precision;
+        double theta;
+        int n_leaf, n_group;
+        double ms;
+    };
+    std::vector<TuneEntry> tune_cache;   // autotuner results of this context
 };
 
 namespace {
@@ -584,9 +593,8 @@ int batch_tables(pt_tree *t, int nsets) {
 
 // Everything a batch enqueues after the tables are filled, without any host
 // synchronisation (this is what a CUDA graph captures).
-int enqueue_batch(pt_tree *t, bool host_io, bool want_nb) {
+int enqueue_batch(pt_tree *t, cudaStream_t st, bool host_io, bool want_nb) {
     pt_ctx *ctx = t->ctx;
-    cudaStream_t st = ctx->stream;
     const unsigned n = t->n;
     const int C = t->nsets;
     Status *dS = t->status.as<Status>();
@@ -781,10 +789,18 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
             t->gexec = nullptr;
             const Status keep = t->h;
             cudaGraph_t g = nullptr;
-            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-            int rc = enqueue_batch(t, host_io, want_nb);
-            cudaError_t ec = cudaStreamEndCapture(st, &g);
-            if (rc != PT_OK) return rc;
+            // captured on the context's private stream (the caller's stream
+            // may be the legacy default stream, which cannot be captured); the
+            // graph is later launched on the caller's stream
+            cudaStream_t cs = ctx->cap_stream;
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_batch(t, cs, host_io, want_nb);
+            cudaError_t ec = cudaStreamEndCapture(cs, &g);
+            if (rc != PT_OK) {
+                if (g) cudaGraphDestroy(g);
+                (void)cudaGetLastError();
+                return rc;
+            }
             if (ec != cudaSuccess) return fail(ctx, PT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
             ec = cudaGraphInstantiate(&t->gexec, g, 0);
             cudaGraphDestroy(g);
@@ -844,6 +860,66 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
     return rc;
 }
 
+
+// ---------------------------------------------------------------------------
+// Autotuner: times every (n_leaf, n_group) candidate on the caller's batch
+// (device time of build + force, best of `reps`) and keeps the fastest; the
+// result is cached per (sets, size buckets, theta, order, precision).
+// ---------------------------------------------------------------------------
+
+int bucket_of(unsigned long long v) {
+    int b = 0;
+    while ((1ull << b) < v && b < 62) b++;
+    return b;
+}
+
+int autotune_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *base, const int *leafs,
+                  int nl, const int *groups, int ng, int reps, pt_params *best, double *best_ms) {
+    if (C < 1 || !d || !base || !best) return fail(ctx, PT_ERR_ARG, "autotune: bad arguments");
+    TRY(check_params(ctx, base));
+    static const int kLeafDefault[] = {4, 8, 16, 32};
+    static const int kGroupDefault[] = {32, 48, 64, 96, 128};
+    if (!leafs || nl <= 0) { leafs = kLeafDefault; nl = 4; }
+    if (!groups || ng <= 0) { groups = kGroupDefault; ng = 5; }
+    if (reps < 1) reps = 2;
+    unsigned long long ntot = 0;
+    for (int c = 0; c < C; c++) ntot += (unsigned long long)(d[c].n > 0 ? d[c].n : 0);
+    const int nb = bucket_of(ntot), mb = bucket_of(ntot / (unsigned long long)C);
+    for (const auto &e : ctx->tune_cache)
+        if (e.nsets == C && e.nbucket == nb && e.mbucket == mb && e.order == base->order &&
+            e.precision == base->precision && e.theta == base->theta) {
+            *best = *base;
+            best->n_leaf = e.n_leaf;
+            best->n_group = e.n_group;
+            if (best_ms) *best_ms = e.ms;
+            return PT_OK;
+        }
+    double bms = 1e300;
+    pt_params bp = *base;
+    for (int i = 0; i < nl; i++)
+        for (int j = 0; j < ng; j++) {
+            pt_params p = *base;
+            p.n_leaf = leafs[i];
+            p.n_group = groups[j];
+            double ms = 1e300;
+            for (int r = 0; r <= reps; r++) {        // first run sizes the buffers
+                pt_stats st{};
+                int rc = batch_impl(ctx, C, d, &p, 0, &st);
+                if (rc != PT_OK && rc != PT_ERR_CAPACITY) return rc;
+                if (r > 0) ms = std::min(ms, st.ms_build + st.ms_total);
+            }
+            if (ms < bms) {
+                bms = ms;
+                bp = p;
+            }
+        }
+    *best = bp;
+    if (best_ms) *best_ms = bms;
+    ctx->tune_cache.push_back({C, nb, mb, base->order, base->precision, base->theta, bp.n_leaf,
+                               bp.n_group, bms});
+    return PT_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -878,6 +954,12 @@ int pt_ctx_create(pt_ctx **out, int device, void *stream) {
         return PT_ERR_CUDA;
     }
     for (auto &e : ctx->ev) cudaEventCreate(&e);
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        walk_init() != 0) {
+        (void)cudaGetLastError();
+        pt_ctx_destroy(ctx);
+        return PT_ERR_CUDA;
+    }
     *out = ctx;
     return PT_OK;
 }
@@ -889,6 +971,7 @@ int pt_ctx_destroy(pt_ctx *ctx) {
     if (ctx->batch_tree) pt_tree_free(ctx->batch_tree);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
     return PT_OK;
@@ -1109,6 +1192,15 @@ int pt_batch_longrange_force(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc,
     if (!ctx) return PT_ERR_ARG;
     ctx->err[0] = 0;
     return batch_impl(ctx, n_clusters, desc, params, flags, stats);
+}
+
+int pt_autotune(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc, const pt_params *base,
+                const int *leaf_candidates, int n_leaf_candidates, const int *group_candidates,
+                int n_group_candidates, int reps, pt_params *best, double *best_ms) {
+    if (!ctx) return PT_ERR_ARG;
+    ctx->err[0] = 0;
+    return autotune_impl(ctx, n_clusters, desc, base, leaf_candidates, n_leaf_candidates,
+                         group_candidates, n_group_candidates, reps, best, best_ms);
 }
 
 }  // extern "C"

@@ -113,6 +113,7 @@ int batch_nb_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigne
                     const long long *off, const int *idx, long long *totals, bool split,
                     cudaStream_t st);
 int build_launch(const BuildArgs &A, cudaStream_t st);   // returns kernels launched
+int walk_init();   // once per context: kernel attributes of the walk
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st);
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st);

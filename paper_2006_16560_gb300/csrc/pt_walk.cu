@@ -149,6 +149,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     }
 }
 
+int walk_init() {
+    // the largest stack the walk may use, set once per context (kernel
+    // attributes are not stream work and stay out of captured graphs)
+    const int smem = (int)((size_t)kWalkWarps * kWalkStackLarge * sizeof(unsigned));
+    if (cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 1;
+    if (cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 1;
+    return 0;
+}
+
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
     // work counters 0 and 1 are reset by the caller (part of the status block).
     // The walk is latency bound: as many resident warps as the stack allows.
@@ -157,7 +168,6 @@ int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
     per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
     const int blocks = 152 * per_sm;
     if (phase == 0) {
-        cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_walk<false><<<blocks, kWalkThreads, smem, st>>>(A);
         int nk = 1;
         nk += scan_exclusive<unsigned long long>(A.gr_nc, A.gr_co, &A.st->ngroups, &A.st->cell_total,
@@ -166,7 +176,6 @@ int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
                                                  nullptr, A.scan_tmp, st);
         return nk;
     }
-    cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_walk<true><<<blocks, kWalkThreads, smem, st>>>(A);
     return 1;
 }
