@@ -244,6 +244,41 @@ def batch_leg(ctx, steps):
     }
 
 
+def serve_leg(ctx, duration_s):
+    """Serving workload: 64 resident Kroupa Plummer simulations, N log-uniform
+    in 2,000-2,000,000 (seed 5), theta 0.4, leaf 16, FP32-mixed, neighbour lists
+    on, HBM budget 150 GB; Poisson arrivals at 200 requests/s, each request a
+    drift + long-range force + kick of one simulation."""
+    import torch
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+    from paper_2006_16560_gb300.serve import Server, poisson_load
+    rng = inputs.rng_for(5)
+    sizes = np.exp(rng.uniform(math.log(2000), math.log(2_000_000), 64)).astype(np.int64)
+    seeds = rng.integers(1, 2 ** 31 - 1, 64)
+    prm = B.Params(theta=0.4, n_leaf=16, n_group=64, order=2, precision=B.PT_MIXED)
+    srv = Server(ctx, prm, hbm_budget_bytes=150e9, max_sims=64)
+    ids = []
+    t0 = time.perf_counter()
+    for n, sd in zip(sizes, seeds):
+        c = inputs.plummer(int(n), int(sd), masses="kroupa")
+        r_out = inputs.r_out_first_guess(int(n))
+        ids.append(srv.add_sim(c["pos"], c["vel"], c["mass"], 0.1 * r_out, r_out))
+    setup_s = time.perf_counter() - t0
+    # warm the pipeline's buffers with one request per simulation
+    for t in [srv.submit(i, 0.0, 0.0) for i in ids]:
+        srv.wait(t)
+    r = poisson_load(srv, ids, rate=200.0, duration_s=duration_s, seed=6, dt_drift=1e-5, dt_kick=1e-5)
+    st = srv.stats()
+    srv.close()
+    r.update({"workload": "64 resident Kroupa Plummer simulations, N log-uniform 2e3-2e6 (seed 5), "
+                          "theta 0.4, leaf 16, FP32-mixed, neighbour lists on, budget 150 GB, "
+                          "Poisson arrivals 200/s (seed 6)",
+              "resident_particles": int(sizes.sum()), "resident_bytes": st["resident_bytes"],
+              "max_batch_particles": st["max_batch_particles"], "setup_s": setup_s})
+    return r
+
+
 def cpu_oracle_sample(pos, mass, nsample, seed=11):
     """Oracle tree on the host cores: full build plus the tree force on
     nsample targets; returns the interactions/s it would sustain on the whole
@@ -303,6 +338,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="skip the FP64, e2e and batch legs (profiling)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-cluster batch leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -445,6 +482,8 @@ def main():
         holder[0].free()
     if not args.no_batch and not args.only_mixed:
         line["batch"] = batch_leg(ctx, max(3, args.steps // 2))
+    if not args.no_serve and not args.only_mixed and rank == 0:
+        line["serving"] = serve_leg(ctx, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         v, secs, thr, si = cpu_oracle_sample(d["pos"], d["mass"], args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": thr, "kind": "oracle",

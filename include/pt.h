@@ -205,6 +205,72 @@ int pt_autotune(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc, const pt_par
                 const int *leaf_candidates, int n_leaf_candidates, const int *group_candidates,
                 int n_group_candidates, int reps, pt_params *best, double *best_ms);
 
+/* ---- serving: long-range kick requests from many resident simulations ---- */
+
+/* A server keeps the particle state of many simulations resident on the
+ * device and serves "drift, long-range force, kick" requests for them with
+ * continuous batching: a worker thread takes the queued requests in arrival
+ * order (at most one per simulation, up to max_batch_particles particles) and
+ * evaluates them in one pass of the pipeline (pt_batch_longrange_force), so
+ * requests that arrive while a batch runs are served by the next batch.
+ * Admission is checked against hbm_budget_bytes: the resident state of every
+ * simulation (about 100 bytes plus neighbour capacity per particle) plus a
+ * workspace reserve of 1,536 bytes per batch particle must fit.
+ * A request on simulation s does x += v dt_drift (a free drift standing in for
+ * the short-range integrator, out of scope here), computes the long-range
+ * acceleration and potential (and neighbour lists if requested) of s, and
+ * then kicks v += a dt_kick (Sec. 6, Fig. 3, the P3T kick).  Its result is the
+ * same alone and batched with others. */
+typedef struct pt_server pt_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;      /* device memory the server may use          */
+    int64_t max_batch_particles;  /* particles per batch; 0 = from the budget  */
+    int max_sims;                 /* simulations that may be resident          */
+    int neighbours;               /* 1: keep r_out neighbour lists per sim     */
+    pt_params params;             /* theta, G, n_leaf, n_group, order,
+                                     precision (r_in / r_out come per sim)     */
+} pt_server_config;
+
+typedef struct {
+    int64_t ticket;
+    int sim;
+    int status;                   /* PT_OK or the batch's error code            */
+    double t_submit, t_start, t_done;   /* seconds on the server's clock        */
+    int batch_size;               /* requests served by the same batch          */
+    int64_t batch_particles;
+} pt_request_info;
+
+typedef struct {
+    int64_t batches, requests, particles, interactions;
+    double busy_s, uptime_s;      /* time with a batch on the device, lifetime */
+    int64_t resident_bytes, max_batch_particles, queued;
+} pt_server_stats_t;
+
+/* Starts a server (and its worker thread) on the calling thread's current
+ * device, with its own stream and context.  `ctx` must be a valid context (its
+ * device is used for checks only).  Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
+int pt_server_create(pt_ctx *ctx, const pt_server_config *cfg, pt_server **srv);
+/* Finishes the queued requests, stops the worker and frees all state. */
+int pt_server_destroy(pt_server *srv);
+/* Copies a simulation's n particles (pos, vel n x 3; mass n; host or device)
+ * into resident device memory; *sim_id receives its id.  PT_ERR_CAPACITY if
+ * the HBM budget, max_sims or max_batch_particles would be exceeded. */
+int pt_server_add_sim(pt_server *srv, int64_t n, const double *pos, const double *vel,
+                      const double *mass, double r_in, double r_out, int *sim_id);
+/* Waits for the simulation's requests, then frees its state. */
+int pt_server_remove_sim(pt_server *srv, int sim_id);
+/* Queues a request; *ticket identifies it for pt_server_wait.  Thread safe. */
+int pt_server_submit(pt_server *srv, int sim_id, double dt_drift, double dt_kick, int64_t *ticket);
+/* Waits for a request (timeout_s < 0: forever; PT_ERR_TIMEOUT when it runs
+ * out) and reports its timing; each ticket can be waited for once. */
+int pt_server_wait(pt_server *srv, int64_t ticket, double timeout_s, pt_request_info *info);
+/* Copies a simulation's current pos, vel, acc (n x 3) and pot (n) to the given
+ * buffers (host or device; NULL skips one) after its queued requests finish. */
+int pt_server_read_sim(pt_server *srv, int sim_id, double *pos, double *vel, double *acc, double *pot);
+/* Totals since the server started. */
+int pt_server_stats(pt_server *srv, pt_server_stats_t *stats);
+
 /* ---- introspection (copies to HOST buffers; for tests and tools) ---- */
 
 /* info[0..4] = n, nodes, groups, max level, clusters;
