@@ -46,10 +46,11 @@ def lib():
                 ("orc_f", _dbl, [_dbl, _dbl]),
                 ("orc_W", _dbl, [_dbl, _dbl]),
                 ("orc_K", _dbl, [_dbl, _dbl]),
-                ("orc_direct", None, [_i64, _p, _p, _dbl, _dbl, _dbl, _i64, _p, _p, _p, C.c_int]),
-                ("orc_neighbours_count", None, [_i64, _p, _dbl, _i64, _p, _p]),
-                ("orc_neighbours_fill", None, [_i64, _p, _dbl, _i64, _p, _p, _p]),
-                ("orc_tree_build", _p, [_i64, _p, _p, C.c_int, C.c_int]),
+                ("orc_direct", None, [_i64, _p, _p, _dbl, _dbl, _dbl, _i64, _p, _p, _p, C.c_int, _p]),
+                ("orc_neighbours_count", None, [_i64, _p, _dbl, _i64, _p, _p, _p]),
+                ("orc_neighbours_fill", None, [_i64, _p, _dbl, _i64, _p, _p, _p, _p]),
+                ("orc_radius_scale", None, [_i64, _p, _p]),
+                ("orc_tree_build", _p, [_i64, _p, _p, C.c_int, C.c_int, _p]),
                 ("orc_tree_free", None, [_p]),
                 ("orc_tree_info", None, [_p, _p, _p]),
                 ("orc_tree_keys", None, [_p, _p, _p, _p]),
@@ -87,45 +88,58 @@ def changeover_K(x: float, lam: float) -> float:
     return lib().orc_K(float(x), float(lam))
 
 
-def direct_force(pos, mass, r_in, r_out, G=1.0, targets=None, shortrange=False):
-    """Direct O(N^2) long-range (or short-range) acc (nt,3) and pot (nt,)."""
+def radius_scale(mass):
+    """Eq. 12 radius factors s_i = max(1, m_i/<m>)^(1/3)."""
+    mass = _f64(mass)
+    out = np.zeros(len(mass))
+    lib().orc_radius_scale(len(mass), _ptr(mass), _ptr(out))
+    return out
+
+
+def direct_force(pos, mass, r_in, r_out, G=1.0, targets=None, shortrange=False, scale=None):
+    """Direct O(N^2) long-range (or short-range) acc (nt,3) and pot (nt,);
+    ``scale`` gives per-particle radius factors (pair radii use the larger)."""
     pos = _f64(pos)
     mass = _f64(mass)
+    sc = None if scale is None else _f64(scale)
     n = len(mass)
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
     nt = n if tg is None else len(tg)
     acc = np.zeros((nt, 3))
     pot = np.zeros(nt)
     lib().orc_direct(n, _ptr(pos), _ptr(mass), G, r_in, r_out, nt, _ptr(tg),
-                     _ptr(acc), _ptr(pot), 1 if shortrange else 0)
+                     _ptr(acc), _ptr(pot), 1 if shortrange else 0, _ptr(sc))
     return acc, pot
 
 
-def neighbours(pos, r_out, targets=None):
+def neighbours(pos, r_out, targets=None, scale=None):
     """Brute-force r_out neighbour sets as CSR (offsets (nt+1,), idx)."""
     pos = _f64(pos)
+    sc = None if scale is None else _f64(scale)
     n = len(pos)
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
     nt = n if tg is None else len(tg)
     cnt = np.zeros(nt, dtype=np.int64)
-    lib().orc_neighbours_count(n, _ptr(pos), r_out, nt, _ptr(tg), _ptr(cnt))
+    lib().orc_neighbours_count(n, _ptr(pos), r_out, nt, _ptr(tg), _ptr(cnt), _ptr(sc))
     off = np.zeros(nt + 1, dtype=np.int64)
     np.cumsum(cnt, out=off[1:])
     idx = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
-    lib().orc_neighbours_fill(n, _ptr(pos), r_out, nt, _ptr(tg), _ptr(off), _ptr(idx))
+    lib().orc_neighbours_fill(n, _ptr(pos), r_out, nt, _ptr(tg), _ptr(off), _ptr(idx), _ptr(sc))
     return off, idx[: off[-1]]
 
 
 class Tree:
     """Oracle octree (keys, sort, nodes, moments, groups) over one particle set."""
 
-    def __init__(self, pos, mass, n_leaf: int, n_group: int):
+    def __init__(self, pos, mass, n_leaf: int, n_group: int, scale=None):
         self._pos = _f64(pos)
         self._mass = _f64(mass)
+        self._scale = None if scale is None else _f64(scale)
         self.n = len(self._mass)
         self.n_leaf = n_leaf
         self.n_group = n_group
-        self._h = lib().orc_tree_build(self.n, _ptr(self._pos), _ptr(self._mass), n_leaf, n_group)
+        self._h = lib().orc_tree_build(self.n, _ptr(self._pos), _ptr(self._mass), n_leaf, n_group,
+                                       _ptr(self._scale))
         info = np.zeros(4, dtype=np.int64)
         box = np.zeros(5)
         lib().orc_tree_info(self._h, _ptr(info), _ptr(box))

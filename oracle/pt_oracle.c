@@ -130,9 +130,30 @@ static void pair_shortrange(const double *xi, const double *xj, double mj,
 /* For each target t (original index targets[t], or t itself when targets is
  * NULL): a = G sum_{j != i} m_j (x_j - x_i)(1 - K)/r^3 and
  * phi = -G sum_{j != i} m_j (1 - W)/r, j in ascending order. */
+/* Mass-dependent changeover (Sec. 6.1, Eq. 12): particle i has radii
+ * s_i (r_in, r_out) and a pair uses the larger of the two (Eq. 16:
+ * r_in,ij = max(r_in,i, r_in,j), same for r_out).  scale == NULL means s = 1. */
+static double pair_scale(const double *scale, int64_t i, int64_t j)
+{
+    if (!scale) return 1.0;
+    return scale[i] > scale[j] ? scale[i] : scale[j];
+}
+
+/* Eq. 12: s_i = max(1, m_i / <m>)^(1/3), <m> the mean mass (summed in index order). */
+void orc_radius_scale(int64_t n, const double *mass, double *scale)
+{
+    double M = 0.0;
+    for (int64_t i = 0; i < n; i++) M += mass[i];
+    double mean = M / (double)n;
+    for (int64_t i = 0; i < n; i++) {
+        double q = mass[i] / mean;
+        scale[i] = cbrt(q > 1.0 ? q : 1.0);
+    }
+}
+
 void orc_direct(int64_t n, const double *pos, const double *mass, double G,
                 double r_in, double r_out, int64_t nt, const int64_t *targets,
-                double *acc, double *pot, int shortrange)
+                double *acc, double *pot, int shortrange, const double *scale)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; t++) {
@@ -140,10 +161,11 @@ void orc_direct(int64_t n, const double *pos, const double *mass, double G,
         double a[3] = {0.0, 0.0, 0.0}, p = 0.0;
         for (int64_t j = 0; j < n; j++) {
             if (j == i) continue;
+            double sij = pair_scale(scale, i, j);
             if (shortrange)
-                pair_shortrange(pos + 3 * i, pos + 3 * j, mass[j], r_in, r_out, a, &p);
+                pair_shortrange(pos + 3 * i, pos + 3 * j, mass[j], sij * r_in, sij * r_out, a, &p);
             else
-                pair_longrange(pos + 3 * i, pos + 3 * j, mass[j], r_in, r_out, a, &p);
+                pair_longrange(pos + 3 * i, pos + 3 * j, mass[j], sij * r_in, sij * r_out, a, &p);
         }
         acc[3 * t + 0] = G * a[0];
         acc[3 * t + 1] = G * a[1];
@@ -164,30 +186,37 @@ static int is_neighbour(const double *xi, const double *xj, double rout2)
     return r2 < rout2;
 }
 
+/* The pair's r_out squared: (s_ij r_out)^2 with s_ij = max(s_i, s_j). */
+static double pair_rout2(const double *scale, int64_t i, int64_t j, double r_out)
+{
+    double ro = r_out * pair_scale(scale, i, j);
+    return ro * ro;
+}
+
 /* counts[t] = number of neighbours of target t. */
 void orc_neighbours_count(int64_t n, const double *pos, double r_out, int64_t nt,
-                          const int64_t *targets, int64_t *counts)
+                          const int64_t *targets, int64_t *counts, const double *scale)
 {
-    double rout2 = r_out * r_out;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; t++) {
         int64_t i = targets ? targets[t] : t, c = 0;
         for (int64_t j = 0; j < n; j++)
-            if (j != i && is_neighbour(pos + 3 * i, pos + 3 * j, rout2)) c++;
+            if (j != i && is_neighbour(pos + 3 * i, pos + 3 * j, pair_rout2(scale, i, j, r_out))) c++;
         counts[t] = c;
     }
 }
 
 /* Fill idx[offsets[t] ..] with the neighbours of target t, ascending. */
 void orc_neighbours_fill(int64_t n, const double *pos, double r_out, int64_t nt,
-                         const int64_t *targets, const int64_t *offsets, int32_t *idx)
+                         const int64_t *targets, const int64_t *offsets, int32_t *idx,
+                         const double *scale)
 {
-    double rout2 = r_out * r_out;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; t++) {
         int64_t i = targets ? targets[t] : t, c = offsets[t];
         for (int64_t j = 0; j < n; j++)
-            if (j != i && is_neighbour(pos + 3 * i, pos + 3 * j, rout2)) idx[c++] = (int32_t)j;
+            if (j != i && is_neighbour(pos + 3 * i, pos + 3 * j, pair_rout2(scale, i, j, r_out)))
+                idx[c++] = (int32_t)j;
     }
 }
 
@@ -216,11 +245,13 @@ typedef struct {
     int nchild;
     uint32_t qmin[3], qmax[3];  /* tight box in grid cells (inclusive)      */
     double M, com[3], Q[6];     /* Q order: xx, yy, zz, xy, xz, yz          */
+    double smax;                /* largest radius scale of its particles    */
 } orc_node;
 
 typedef struct {
     int64_t begin, count;
     uint32_t qmin[3], qmax[3];
+    double smax;
 } orc_group;
 
 typedef struct {
@@ -230,6 +261,7 @@ typedef struct {
     uint32_t *q;                /* per original index, 3 each               */
     int64_t *perm;              /* sorted slot -> original index            */
     double *spos, *smass;       /* sorted copies                            */
+    double *sscale;             /* sorted radius scales (all 1 if none)     */
     uint32_t *sq;               /* sorted grid coordinates                  */
     uint64_t *skey;
     orc_node *node;
@@ -307,8 +339,10 @@ static void node_moments(orc_tree *t, orc_node *v)
 {
     double M = 0.0, s[3] = {0.0, 0.0, 0.0};
     for (int d = 0; d < 3; d++) { v->qmin[d] = ORC_GRID; v->qmax[d] = 0; }
+    v->smax = 0.0;
     for (int64_t p = v->begin; p < v->begin + v->count; p++) {
         double m = t->smass[p];
+        if (t->sscale[p] > v->smax) v->smax = t->sscale[p];
         M += m;
         for (int d = 0; d < 3; d++) {
             s[d] += m * t->spos[3 * p + d];
@@ -384,7 +418,7 @@ static void build_node(orc_tree *t, int64_t vi)
  * n_group particles is handled recursively, and consecutive smaller children
  * are packed greedily into groups of at most n_group particles. */
 static void group_emit(orc_tree *t, int64_t begin, int64_t count,
-                       const uint32_t *qmin, const uint32_t *qmax)
+                       const uint32_t *qmin, const uint32_t *qmax, double smax)
 {
     if (t->ngroups == t->gcap) {
         t->gcap = t->gcap * 2 + 16;
@@ -394,33 +428,37 @@ static void group_emit(orc_tree *t, int64_t begin, int64_t count,
     g->begin = begin;
     g->count = count;
     for (int d = 0; d < 3; d++) { g->qmin[d] = qmin[d]; g->qmax[d] = qmax[d]; }
+    g->smax = smax;
 }
 
 static void build_groups(orc_tree *t, int64_t vi)
 {
     const orc_node *v = &t->node[vi];
     if (v->count <= t->n_group || v->leaf) {
-        group_emit(t, v->begin, v->count, v->qmin, v->qmax);
+        group_emit(t, v->begin, v->count, v->qmin, v->qmax, v->smax);
         return;
     }
     int64_t pb = 0, pc = 0;
     uint32_t pmin[3], pmax[3];
+    double psmax = 0.0;
     for (int k = 0; k < v->nchild; k++) {
         const orc_node *c = &t->node[v->first_child + k];
         if (c->count > t->n_group) {
-            if (pc) group_emit(t, pb, pc, pmin, pmax);
+            if (pc) group_emit(t, pb, pc, pmin, pmax, psmax);
             pc = 0;
             build_groups(t, v->first_child + k);
             continue;
         }
         if (pc && pc + c->count > t->n_group) {
-            group_emit(t, pb, pc, pmin, pmax);
+            group_emit(t, pb, pc, pmin, pmax, psmax);
             pc = 0;
         }
         if (pc == 0) {
             pb = c->begin;
+            psmax = c->smax;
             for (int d = 0; d < 3; d++) { pmin[d] = c->qmin[d]; pmax[d] = c->qmax[d]; }
         } else {
+            if (c->smax > psmax) psmax = c->smax;
             for (int d = 0; d < 3; d++) {
                 if (c->qmin[d] < pmin[d]) pmin[d] = c->qmin[d];
                 if (c->qmax[d] > pmax[d]) pmax[d] = c->qmax[d];
@@ -428,7 +466,7 @@ static void build_groups(orc_tree *t, int64_t vi)
         }
         pc += c->count;
     }
-    if (pc) group_emit(t, pb, pc, pmin, pmax);
+    if (pc) group_emit(t, pb, pc, pmin, pmax, psmax);
 }
 
 static int cmp_group_begin(const void *a, const void *b)
@@ -438,7 +476,7 @@ static int cmp_group_begin(const void *a, const void *b)
 }
 
 orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass,
-                         int n_leaf, int n_group)
+                         int n_leaf, int n_group, const double *scale)
 {
     orc_tree *t = (orc_tree *)calloc(1, sizeof(orc_tree));
     t->n = n;
@@ -449,6 +487,7 @@ orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass,
     t->perm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
     t->spos = (double *)malloc((size_t)n * 3 * sizeof(double));
     t->smass = (double *)malloc((size_t)n * sizeof(double));
+    t->sscale = (double *)malloc((size_t)n * sizeof(double));
     t->sq = (uint32_t *)malloc((size_t)n * 3 * sizeof(uint32_t));
     t->skey = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
     compute_keys(t, pos);
@@ -462,6 +501,7 @@ orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass,
             t->sq[3 * s + d] = t->q[3 * i + d];
         }
         t->smass[s] = mass[i];
+        t->sscale[s] = scale ? scale[i] : 1.0;
         t->skey[s] = t->key[i];
     }
     int64_t root = node_alloc(t, 1);
@@ -479,7 +519,7 @@ orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass,
 void orc_tree_free(orc_tree *t)
 {
     if (!t) return;
-    free(t->key); free(t->q); free(t->perm); free(t->spos); free(t->smass);
+    free(t->key); free(t->q); free(t->perm); free(t->spos); free(t->smass); free(t->sscale);
     free(t->sq); free(t->skey); free(t->node); free(t->group);
     free(t);
 }
@@ -551,15 +591,20 @@ typedef struct {
     int64_t *pp, npp, pcap;
 } walk_out;
 
-static int64_t rout_threshold(const orc_tree *t, double r_out)
+/* Gap threshold for radius scale s: floor(((r_out s) scale)^2) + 2 whole
+ * grid cells squared.  The pair radius is the larger of the two scales, and
+ * the threshold grows with s, so a cell is tested against the larger of the
+ * group's and the cell's thresholds. */
+static int64_t rout_threshold(const orc_tree *t, double r_out, double s)
 {
-    double R = r_out * t->scale;
+    double R = (r_out * s) * t->scale;
     double R2 = R * R;
     if (R2 > 4.0e18) return (int64_t)4000000000000000000LL;  /* no gap that large */
     return (int64_t)floor(R2) + 2;
 }
 
-static int accept_cell(const orc_group *G, const orc_node *C, double theta2, int64_t r2thr)
+static int accept_cell(const orc_tree *t, const orc_group *G, const orc_node *C, double theta2,
+                       double r_out)
 {
     int sh = ORC_BITS - C->level;
     int64_t d2 = 0, gap2 = 0;
@@ -580,14 +625,15 @@ static int accept_cell(const orc_group *G, const orc_node *C, double theta2, int
     }
     double s = (double)((int64_t)1 << (ORC_BITS + 1 - C->level));  /* side, half cells */
     if (!(s * s < theta2 * (double)d2)) return 0;
-    return gap2 >= r2thr;
+    int64_t tg = rout_threshold(t, r_out, G->smax), tc = rout_threshold(t, r_out, C->smax);
+    return gap2 >= (tg > tc ? tg : tc);
 }
 
 static void walk_visit(const orc_tree *t, const orc_group *G, int64_t vi,
-                       double theta2, int64_t r2thr, walk_out *w)
+                       double theta2, double r_out, walk_out *w)
 {
     const orc_node *C = &t->node[vi];
-    if (accept_cell(G, C, theta2, r2thr)) {
+    if (accept_cell(t, G, C, theta2, r_out)) {
         if (w->cells && w->ncells < w->ccap) w->cells[w->ncells] = vi;
         w->ncells++;
         return;
@@ -600,7 +646,7 @@ static void walk_visit(const orc_tree *t, const orc_group *G, int64_t vi,
         return;
     }
     for (int k = 0; k < C->nchild; k++)
-        walk_visit(t, G, C->first_child + k, theta2, r2thr, w);
+        walk_visit(t, G, C->first_child + k, theta2, r_out, w);
 }
 
 /* Lists of group g: cells (node indices) and PP (sorted particle indices).
@@ -610,7 +656,7 @@ int orc_tree_walk(const orc_tree *t, int64_t g, double theta, double r_out,
                   int64_t *ncells, int64_t *npp)
 {
     walk_out w = {cells, 0, ccap, pp, 0, pcap};
-    walk_visit(t, &t->group[g], 0, theta * theta, rout_threshold(t, r_out), &w);
+    walk_visit(t, &t->group[g], 0, theta * theta, r_out, &w);
     *ncells = w.ncells;
     *npp = w.npp;
     return (w.ncells > ccap || w.npp > pcap) ? 1 : 0;
@@ -661,7 +707,8 @@ static void tree_force_one(const orc_tree *t, int64_t s, const walk_out *w,
     for (int64_t k = 0; k < w->npp; k++) {
         int64_t j = w->pp[k];
         if (j == s) continue;
-        pair_longrange(xi, t->spos + 3 * j, t->smass[j], r_in, r_out, a, &p);
+        double sij = t->sscale[s] > t->sscale[j] ? t->sscale[s] : t->sscale[j];
+        pair_longrange(xi, t->spos + 3 * j, t->smass[j], sij * r_in, sij * r_out, a, &p);
     }
     for (int k = 0; k < 3; k++) acc[k] = G * a[k];
     *pot = G * p;
@@ -681,12 +728,12 @@ static int64_t group_of(const orc_tree *t, int64_t s)
 static void walk_alloc(const orc_tree *t, int64_t g, double theta, double r_out, walk_out *w)
 {
     walk_out c = {NULL, 0, 0, NULL, 0, 0};
-    walk_visit(t, &t->group[g], 0, theta * theta, rout_threshold(t, r_out), &c);
+    walk_visit(t, &t->group[g], 0, theta * theta, r_out, &c);
     w->ccap = c.ncells; w->pcap = c.npp;
     w->cells = (int64_t *)malloc((size_t)(c.ncells + 1) * sizeof(int64_t));
     w->pp = (int64_t *)malloc((size_t)(c.npp + 1) * sizeof(int64_t));
     w->ncells = 0; w->npp = 0;
-    walk_visit(t, &t->group[g], 0, theta * theta, rout_threshold(t, r_out), w);
+    walk_visit(t, &t->group[g], 0, theta * theta, r_out, w);
 }
 
 /* Tree force.  With targets == NULL every particle is computed (one walk per

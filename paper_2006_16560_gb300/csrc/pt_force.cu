@@ -35,6 +35,9 @@ constexpr int kFThreads = 32 * kFWarps;
 constexpr int kJ = 64;        // list entries per warp tile
 constexpr int kIB = 64;       // targets per pass of the float64 kernel (two per lane)
 constexpr int kSlotMax = 96;  // largest pass of the mixed kernel
+#ifndef PT_FORCE_MIN_BLOCKS
+#define PT_FORCE_MIN_BLOCKS 4     // resident CTAs per SM the register budget is sized for
+#endif
 
 __device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
     const float s = __fadd_rn(hi, x);
@@ -397,7 +400,7 @@ __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, u
 }
 
 template <int ORDER, bool NB>
-__global__ void __launch_bounds__(kFThreads, 4) k_force_mixed(ForceArgs A) {
+__global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(ForceArgs A) {
     __shared__ float4 sA[kFWarps][kJ];
     __shared__ float4 sB[kFWarps][kJ];
     __shared__ float2 sC[kFWarps][kJ];
