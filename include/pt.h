@@ -101,7 +101,8 @@ typedef struct {
     int n_group;         /* max particles in a walk group                    */
     int order;           /* 0 = monopole, 2 = monopole + quadrupole          */
     int precision;       /* PT_FP64 or PT_MIXED                              */
-    int mass_dependent;  /* must be 0 (reserved for Eq. 12 radii)            */
+    int mass_dependent;  /* 1: per-particle radii s_i (r_in, r_out), a pair
+                            using the larger (Sec. 6.1, Eqs. 12 and 16)      */
 } pt_params;
 
 /* Counters and sums of one force evaluation. */
@@ -150,6 +151,18 @@ const char *pt_last_error(const pt_ctx *ctx);
 int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
                   const pt_params *params, pt_tree **tree);
 
+/* As pt_tree_build, with mass-dependent changeover radii (Sec. 6.1, Eq. 12):
+ * particle i has radii s_i (r_in, r_out) and a pair uses the larger pair
+ * (Eq. 16), so the changeover, the walk's r_out gap and the neighbour lists all
+ * use s_ij = max(s_i, s_j).  params->mass_dependent must be 1.  radius_scale
+ * (n doubles, host or device, each >= 1 in the paper's use) gives s_i; if it
+ * is NULL the library computes Eq. 12, s_i = max(1, m_i / <m>)^(1/3) with <m>
+ * the mean mass, on the device (CUDA cbrt: within 1 ulp of a host cbrt, so
+ * pass the factors explicitly when neighbour lists must match a host
+ * computation bit for bit). */
+int pt_tree_build_scaled(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                         const double *radius_scale, const pt_params *params, pt_tree **tree);
+
 /* Walks the tree, evaluates acc (n x 3) and pot (n), both in the caller's
  * particle order, and, if nb_offsets is not NULL, the r_out neighbour lists
  * as CSR: nb_offsets (n+1 int64) and nb_idx (nb_capacity int32 original
@@ -176,6 +189,7 @@ typedef struct {
     int32_t *nb_idx;         /* out: nb_capacity entries (cluster-local ids)  */
     int64_t nb_capacity;
     int64_t nb_total;        /* out: entries needed                           */
+    const double *radius_scale;  /* n radius factors (mass_dependent) or NULL */
 } pt_cluster_desc;
 
 /* Evaluates n_clusters independent sets in one pass of the pipeline: every

@@ -53,7 +53,7 @@ class pt_cluster_desc(C.Structure):
     _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("mass", C.c_void_p),
                 ("r_in", C.c_double), ("r_out", C.c_double), ("acc", C.c_void_p),
                 ("pot", C.c_void_p), ("nb_offsets", C.c_void_p), ("nb_idx", C.c_void_p),
-                ("nb_capacity", C.c_int64), ("nb_total", C.c_int64)]
+                ("nb_capacity", C.c_int64), ("nb_total", C.c_int64), ("radius_scale", C.c_void_p)]
 
 
 _lib = None
@@ -74,6 +74,7 @@ def lib():
                 "pt_ctx_destroy": (I, [P]),
                 "pt_last_error": (C.c_char_p, [P]),
                 "pt_tree_build": (I, [P, I64, P, P, C.POINTER(pt_params), C.POINTER(P)]),
+                "pt_tree_build_scaled": (I, [P, I64, P, P, P, C.POINTER(pt_params), C.POINTER(P)]),
                 "pt_longrange_force": (I, [P, P, P, P, P, P, I64, C.POINTER(I64), C.POINTER(pt_stats)]),
                 "pt_tree_free": (I, [P]),
                 "pt_batch_longrange_force": (I, [P, I, C.POINTER(pt_cluster_desc), C.POINTER(pt_params), I,
@@ -116,6 +117,12 @@ def pt_last_error(ctx) -> str:
 def pt_tree_build(ctx, n, pos_ptr, mass_ptr, params: pt_params, tree=None):
     h = tree if tree is not None else C.c_void_p()
     rc = lib().pt_tree_build(ctx, n, pos_ptr, mass_ptr, C.byref(params), C.byref(h))
+    return rc, h
+
+
+def pt_tree_build_scaled(ctx, n, pos_ptr, mass_ptr, scale_ptr, params: pt_params, tree=None):
+    h = tree if tree is not None else C.c_void_p()
+    rc = lib().pt_tree_build_scaled(ctx, n, pos_ptr, mass_ptr, scale_ptr, C.byref(params), C.byref(h))
     return rc, h
 
 
@@ -224,20 +231,23 @@ class Context:
 class Tree:
     """A built tree (pt_tree) over one particle set."""
 
-    def __init__(self, ctx: Context, pos, mass, params: Params):
+    def __init__(self, ctx: Context, pos, mass, params: Params, scale=None):
         self.ctx = ctx
         self.n = int(mass.shape[0])
         self.params = params
         self._cp = params.c()
-        rc, self.h = pt_tree_build(ctx.h, self.n, _ptr(pos), _ptr(mass), self._cp)
+        self._scale = scale
+        rc, self.h = pt_tree_build_scaled(ctx.h, self.n, _ptr(pos), _ptr(mass), _ptr(scale), self._cp)
         ctx.check(rc, "pt_tree_build")
 
-    def rebuild(self, pos, mass, params: Params | None = None):
+    def rebuild(self, pos, mass, params: Params | None = None, scale=None):
         if params is not None:
             self.params = params
             self._cp = params.c()
         self.n = int(mass.shape[0])
-        rc, self.h = pt_tree_build(self.ctx.h, self.n, _ptr(pos), _ptr(mass), self._cp, self.h)
+        self._scale = scale
+        rc, self.h = pt_tree_build_scaled(self.ctx.h, self.n, _ptr(pos), _ptr(mass), _ptr(scale),
+                                          self._cp, self.h)
         self.ctx.check(rc, "pt_tree_build")
 
     def force(self, acc, pot, nb_offsets=None, nb_idx=None, nb_capacity: int = 0,

@@ -124,6 +124,7 @@ struct pt_tree {
     Buf cells, pp;
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
+    Buf in_scale, scale_buf, set_mean, ssc, nd_thr, gr_thr;   // mass-dependent radii
     Buf out_acc, out_pot;                                  // staging for host outputs
     // batch state (the context's batch tree only)
     Buf d_tab, d_totals, d_acc, d_pot;
@@ -144,6 +145,7 @@ struct pt_tree {
     // last results
     Status h{};
     unsigned walk_stack = kWalkStackSmall;
+    const double *scale_in = nullptr;          // device radius factors of the current build
     bool built = false, lists_valid = false;
     float ms_build = 0.f;
     int launches_build = 0, launches_force = 0;
@@ -154,7 +156,8 @@ struct pt_tree {
                       &nd_c, &nd_q, &nd_t, &nd_f, &tmp_a, &tmp_b, &gflag, &gbegin, &gr_r, &gr_a,
                       &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
-                      &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot};
+                      &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
+                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr};
         for (Buf *b : all) b->release();
         d_tab.release(); d_totals.release(); d_acc.release(); d_pot.release();
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -180,7 +183,8 @@ int check_params(pt_ctx *ctx, const pt_params *p) {
     if (p->order != 0 && p->order != 2) return fail(ctx, PT_ERR_ARG, "order must be 0 or 2");
     if (p->precision != PT_FP64 && p->precision != PT_MIXED)
         return fail(ctx, PT_ERR_ARG, "precision must be PT_FP64 or PT_MIXED");
-    if (p->mass_dependent != 0) return fail(ctx, PT_ERR_ARG, "mass_dependent radii are not available");
+    if (p->mass_dependent != 0 && p->mass_dependent != 1)
+        return fail(ctx, PT_ERR_ARG, "mass_dependent must be 0 or 1");
     return PT_OK;
 }
 
@@ -260,6 +264,13 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->gr_co, (N + 1) * 8));
     TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
     TRY(ensure(ctx, t->gpart, N * 32));
+    TRY(ensure(ctx, t->ssc, N * 8));
+    TRY(ensure(ctx, t->set_mean, S * 8));
+    if (t->prm.mass_dependent) {
+        TRY(ensure(ctx, t->scale_buf, N * 8));
+        TRY(ensure(ctx, t->nd_thr, C * 8));
+        TRY(ensure(ctx, t->gr_thr, N * 8));
+    }
     TRY(ensure(ctx, t->scan_sums, (kScanBlocks + 1) * 8));
     TRY(ensure(ctx, t->sort_counts, (size_t)kSortCountsLen * 4));
     t->cap_sort = std::max<unsigned long long>(t->cap_sort, N);
@@ -307,6 +318,13 @@ BuildArgs build_args(pt_tree *t, const double *pos, const double *mass) {
     A.gr_b = t->gr_b.as<uint4>();
     A.n_leaf = t->prm.n_leaf;
     A.n_group = t->prm.n_group;
+    A.scale = t->scale_in;
+    A.massdep = t->prm.mass_dependent;
+    A.scale_buf = t->scale_buf.as<double>();
+    A.set_mean = t->set_mean.as<double>();
+    A.ssc = t->ssc.as<double>();
+    A.nd_thr = t->nd_thr.as<long long>();
+    A.gr_thr = t->gr_thr.as<long long>();
     A.status = t->status.as<Status>();
     A.scan_tmp = scan_tmp_of(t);
     A.sort_tmp = sort_tmp_of(t);
@@ -364,6 +382,9 @@ WalkArgs walk_args(pt_tree *t) {
     A.gr_a = t->gr_a.as<uint4>();
     A.gr_b = t->gr_b.as<uint4>();
     A.sets = t->sets.as<SetInfo>();
+    A.nd_thr = t->nd_thr.as<long long>();
+    A.gr_thr = t->gr_thr.as<long long>();
+    A.massdep = t->prm.mass_dependent;
     walk_thresholds(t->prm.theta, A.wp);
     A.gr_nc = t->gr_nc.as<unsigned>();
     A.gr_np = t->gr_np.as<unsigned>();
@@ -397,6 +418,8 @@ ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
     A.nd_f = t->nd_f.as<float4>();
     A.sets = t->sets.as<SetInfo>();
     A.perm = t->perm.as<unsigned>();
+    A.ssc = t->ssc.as<double>();
+    A.massdep = t->prm.mass_dependent;
     A.acc = acc;
     A.pot = pot;
     A.G = t->prm.G;
@@ -605,11 +628,13 @@ int enqueue_batch(pt_tree *t, cudaStream_t st, bool host_io, bool want_nb) {
     CK(cudaMemcpyAsync(dsets, t->h_sets_pin, C * sizeof(SetInfo), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(t->n_dev.p, t->h_n, 4, cudaMemcpyHostToDevice, st));
     int nk = 0;
+    double *isc = t->scale_in ? t->in_scale.as<double>() : nullptr;
     if (host_io) {
         CK(cudaMemcpyAsync(ip, t->h_io, (size_t)n * 24, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(im, t->h_io + 3ull * n, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+        if (isc) CK(cudaMemcpyAsync(isc, t->h_io + 4ull * n, (size_t)n * 8, cudaMemcpyHostToDevice, st));
     } else {
-        nk += batch_gather_launch(dtab, dsets, C, n, ip, im, st);
+        nk += batch_gather_launch(dtab, dsets, C, n, ip, im, isc, st);
     }
     CK(cudaMemsetAsync(dS, 0, sizeof(Status), st));
     nk += build_launch(build_args(t, ip, im), st);
@@ -654,8 +679,9 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
     if (C < 1 || !d) return fail(ctx, PT_ERR_ARG, "n_clusters must be >= 1");
     TRY(check_params(ctx, params));
     unsigned long long ntot = 0;
-    bool want_nb = false, any_dev = false, any_host = false;
+    bool want_nb = false, any_dev = false, any_host = false, any_scale = false;
     for (int c = 0; c < C; c++) {
+        if (d[c].radius_scale) any_scale = true;
         if (d[c].n < 1) return fail(ctx, PT_ERR_ARG, "cluster %d: n must be >= 1", c);
         if (!d[c].pos || !d[c].mass || !d[c].acc || !d[c].pot)
             return fail(ctx, PT_ERR_ARG, "cluster %d: NULL buffer", c);
@@ -669,6 +695,8 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
         (is_device_ptr(d[c].pos) ? any_dev : any_host) = true;
     }
     if (any_dev && any_host) return fail(ctx, PT_ERR_ARG, "mixing host and device buffers in one batch");
+    if (any_scale && !params->mass_dependent)
+        return fail(ctx, PT_ERR_ARG, "radius_scale needs params->mass_dependent = 1");
     if (ntot > 0x7fffffffull) return fail(ctx, PT_ERR_ARG, "batch holds more than 2^31 particles");
     const bool host_io = any_host;
     CK(cudaSetDevice(ctx->device));
@@ -703,12 +731,15 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
     TRY(ensure(ctx, t->in_pos, (size_t)n * 24));
     TRY(ensure(ctx, t->in_mass, (size_t)n * 8));
     TRY(ensure(ctx, t->nb_off, ((size_t)n + 1) * 8));
-    if (host_io) TRY(ensure_pinned(ctx, t->h_io, t->cap_h_io, 4ull * n));
+    if (any_scale) TRY(ensure(ctx, t->in_scale, (size_t)n * 8));
+    t->scale_in = any_scale ? t->in_scale.as<double>() : nullptr;
+    if (host_io) TRY(ensure_pinned(ctx, t->h_io, t->cap_h_io, (any_scale ? 5ull : 4ull) * n));
     // tables (pinned) and host inputs
     for (int c = 0; c < C; c++) {
         BatchTab e{};
         e.pos = d[c].pos;
         e.mass = d[c].mass;
+        e.scale = d[c].radius_scale;
         e.acc = d[c].acc;
         e.pot = d[c].pot;
         e.nb_off = (long long *)d[c].nb_offsets;
@@ -721,10 +752,15 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
             const size_t b = t->h_sets[c].begin, m = (size_t)d[c].n;
             std::memcpy(t->h_io + 3 * b, d[c].pos, m * 24);
             std::memcpy(t->h_io + 3ull * n + b, d[c].mass, m * 8);
+            if (any_scale) {
+                double *dst = t->h_io + 4ull * n + b;
+                if (d[c].radius_scale) std::memcpy(dst, d[c].radius_scale, m * 8);
+                else for (size_t k = 0; k < m; k++) dst[k] = 1.0;
+            }
         }
     }
     *t->h_n = n;
-    const int mode = (host_io ? 1 : 0) | (want_nb ? 2 : 0);
+    const int mode = (host_io ? 1 : 0) | (want_nb ? 2 : 0) | (any_scale ? 4 : 0);
     cudaStream_t st = ctx->stream;
     bool done = false;
     float ms[3] = {0, 0, 0};
@@ -749,12 +785,14 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
         // uncaptured path: sizes every buffer, then (optionally) captures a graph
         CK(cudaMemcpyAsync(t->d_tab.p, t->h_tab, C * sizeof(BatchTab), cudaMemcpyHostToDevice, st));
         double *ip = t->in_pos.as<double>(), *im = t->in_mass.as<double>();
+        double *isc = any_scale ? t->in_scale.as<double>() : nullptr;
         if (host_io) {
             CK(cudaMemcpyAsync(ip, t->h_io, (size_t)n * 24, cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(im, t->h_io + 3ull * n, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+            if (isc) CK(cudaMemcpyAsync(isc, t->h_io + 4ull * n, (size_t)n * 8, cudaMemcpyHostToDevice, st));
         } else {
             CK(cudaMemcpyAsync(t->sets.p, t->h_sets_pin, C * sizeof(SetInfo), cudaMemcpyHostToDevice, st));
-            batch_gather_launch(t->d_tab.as<BatchTab>(), t->sets.as<SetInfo>(), C, n, ip, im, st);
+            batch_gather_launch(t->d_tab.as<BatchTab>(), t->sets.as<SetInfo>(), C, n, ip, im, isc, st);
         }
         TRY(run_build(t, ip, im));
         TRY(run_force(t, t->d_acc.as<double>(), t->d_pot.as<double>(), want_nb, nb_hint, ms));
@@ -981,6 +1019,11 @@ const char *pt_last_error(const pt_ctx *ctx) { return ctx ? ctx->err : "no conte
 
 int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
                   const pt_params *params, pt_tree **tree) {
+    return pt_tree_build_scaled(ctx, n, pos, mass, nullptr, params, tree);
+}
+
+int pt_tree_build_scaled(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                         const double *radius_scale, const pt_params *params, pt_tree **tree) {
     if (!ctx) return PT_ERR_ARG;
     ctx->err[0] = 0;
     if (!tree) return fail(ctx, PT_ERR_ARG, "tree is NULL");
@@ -1005,7 +1048,20 @@ int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
     si.begin = 0;
     si.n = (unsigned)n;
     t->h_sets.assign(1, si);
+    if (radius_scale && !params->mass_dependent)
+        return fail(ctx, PT_ERR_ARG, "radius_scale needs params->mass_dependent = 1");
     const double *dpos = pos, *dmass = mass;
+    t->scale_in = nullptr;
+    if (radius_scale) {
+        if (is_device_ptr(radius_scale)) {
+            t->scale_in = radius_scale;
+        } else {
+            TRY(ensure(ctx, t->in_scale, (size_t)n * 8));
+            CK(cudaMemcpyAsync(t->in_scale.p, radius_scale, (size_t)n * 8, cudaMemcpyHostToDevice,
+                               ctx->stream));
+            t->scale_in = t->in_scale.as<double>();
+        }
+    }
     if (!is_device_ptr(pos)) {
         TRY(ensure(ctx, t->in_pos, (size_t)n * 24));
         CK(cudaMemcpyAsync(t->in_pos.p, pos, (size_t)n * 24, cudaMemcpyHostToDevice, ctx->stream));

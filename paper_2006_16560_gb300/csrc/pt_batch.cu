@@ -18,7 +18,7 @@ __device__ __forceinline__ int set_of_index(const SetInfo *sets, int nsets, unsi
 }
 
 __global__ void k_batch_gather(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
-                               double *pos, double *mass) {
+                               double *pos, double *mass, double *scale) {
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = set_of_index(sets, nsets, i);
         const unsigned k = i - sets[c].begin;
@@ -27,6 +27,7 @@ __global__ void k_batch_gather(const BatchTab *tab, const SetInfo *sets, int nse
         pos[3ull * i + 1] = p[3ull * k + 1];
         pos[3ull * i + 2] = p[3ull * k + 2];
         mass[i] = tab[c].mass[k];
+        if (scale) scale[i] = tab[c].scale ? tab[c].scale[k] : 1.0;
     }
 }
 
@@ -76,8 +77,8 @@ __global__ void k_batch_nb_split(const BatchTab *tab, const SetInfo *sets, int n
 }
 
 int batch_gather_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
-                        double *pos, double *mass, cudaStream_t st) {
-    k_batch_gather<<<152 * 8, 256, 0, st>>>(tab, sets, nsets, n, pos, mass);
+                        double *pos, double *mass, double *scale, cudaStream_t st) {
+    k_batch_gather<<<152 * 8, 256, 0, st>>>(tab, sets, nsets, n, pos, mass, scale);
     return 1;
 }
 

@@ -140,17 +140,55 @@ __global__ void __launch_bounds__(kT) k_keys(const double *pos, unsigned n, cons
 // position for the mixed-precision path, and grid coordinates.
 __global__ void __launch_bounds__(kT) k_gather(const double *pos, const double *mass, unsigned n,
                                                const unsigned *perm, const uint4 *qbuf,
+                                               const double *scale, double *ssc,
                                                double4 *sp64, float4 *spH, float4 *spL, uint4 *sq) {
     for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         unsigned i = perm[p];
+        const double sc = scale ? scale[i] : 1.0;
+        ssc[p] = sc;
         double x = pos[3ull * i], y = pos[3ull * i + 1], z = pos[3ull * i + 2], m = mass[i];
         sp64[p] = make_double4(x, y, z, m);
         float xh = __double2float_rn(x), yh = __double2float_rn(y), zh = __double2float_rn(z);
         spH[p] = make_float4(xh, yh, zh, __double2float_rn(m));
         spL[p] = make_float4(__double2float_rn(x - (double)xh), __double2float_rn(y - (double)yh),
-                             __double2float_rn(z - (double)zh), 0.0f);
+                             __double2float_rn(z - (double)zh), __double2float_rn(1.0 / sc));
         sq[p] = qbuf[i];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Mass-dependent radii (Sec. 6.1, Eq. 12): s_i = max(1, m_i/<m>)^(1/3), with
+// <m> the set's mean mass (one block per set, fixed summation order).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kT) k_set_mean_mass(const double *mass, const SetInfo *sets,
+                                                      double *mean) {
+    __shared__ double sh[kT];
+    const SetInfo S = sets[blockIdx.x];
+    double v = 0.0;
+    for (unsigned k = threadIdx.x; k < S.n; k += blockDim.x) v += mass[S.begin + k];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kT / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[blockIdx.x] = sh[0] / (double)S.n;
+}
+
+__global__ void __launch_bounds__(kT) k_eq12_scale(const double *mass, unsigned n, const unsigned *set_of,
+                                                   const double *mean, double *scale) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double q = mass[i] / mean[set_of ? set_of[i] : 0u];
+        scale[i] = cbrt(q > 1.0 ? q : 1.0);
+    }
+}
+
+// floor(((r_out s) scale)^2) + 2, the gap threshold of the walk (see pt.h).
+__device__ __forceinline__ long long gap_threshold(const SetInfo &S, double s) {
+    const double R = __dmul_rn(__dmul_rn(S.r_out, s), S.scale);
+    const double R2 = __dmul_rn(R, R);
+    return (R2 > 4.0e18) ? 4000000000000000000ll : (long long)floor(R2) + 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -285,14 +323,15 @@ __global__ void k_topo_finish(Status *st, unsigned cap) {
 __global__ void __launch_bounds__(kT) k_moments(int l, const double4 *sp64, const uint4 *sq,
                                                 uint4 *nd_a, uint4 *nd_b, const uint2 *nd_r,
                                                 double4 *nd_c, double4 *nd_q, double4 *nd_t,
-                                                float4 *nd_f, unsigned cap, const Status *st) {
+                                                float4 *nd_f, const double *ssc, const SetInfo *sets,
+                                                long long *nd_thr, unsigned cap, const Status *st) {
     unsigned b0, cnt;
     level_range(st, l, cap, b0, cnt);
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         unsigned v = b0 + k;
         uint4 a = nd_a[v], bb = nd_b[v];
         uint2 r = nd_r[v];
-        double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3];
+        double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3], smax = 0.0;
         unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
         if (meta_leaf(a.w)) {
             double4 p0 = sp64[r.x];
@@ -308,6 +347,7 @@ __global__ void __launch_bounds__(kT) k_moments(int l, const double4 *sp64, cons
                 s2[3] += m * d0 * d1; s2[4] += m * d0 * d2; s2[5] += m * d1 * d2;
                 qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
                 qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
+                smax = fmax(smax, ssc[p]);
             }
             if (M > 0.0) {
                 double dc[3] = {s1[0] / M, s1[1] / M, s1[2] / M};
@@ -333,6 +373,7 @@ __global__ void __launch_bounds__(kT) k_moments(int l, const double4 *sp64, cons
                 s1[1] += C.w * (C.y - x0[1]);
                 s1[2] += C.w * (C.z - x0[2]);
                 uint4 ca = nd_a[c], cb = nd_b[c];
+                smax = fmax(smax, nd_t[2 * c + 1].z);
                 qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
                 qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
             }
@@ -359,7 +400,8 @@ __global__ void __launch_bounds__(kT) k_moments(int l, const double4 *sp64, cons
         nd_q[2 * v] = make_double4(Q[0], Q[1], Q[2], Q[3]);
         nd_q[2 * v + 1] = make_double4(Q[4], Q[5], 0.0, 0.0);
         nd_t[2 * v] = make_double4(T[0], T[1], T[2], T[3]);
-        nd_t[2 * v + 1] = make_double4(T[4], T[5], 0.0, 0.0);
+        nd_t[2 * v + 1] = make_double4(T[4], T[5], smax, 0.0);
+        if (nd_thr) nd_thr[v] = gap_threshold(sets[sq[r.x].w], smax);
         a.x = qmn[0]; a.y = qmn[1]; a.z = qmn[2];
         bb.x = qmx[0]; bb.y = qmx[1]; bb.z = qmx[2];
         nd_a[v] = a;
@@ -421,7 +463,8 @@ __global__ void __launch_bounds__(kT) k_group_emit(const unsigned *gflag, const 
 // One warp per group: range, grid box, set, root node, reference point.
 __global__ void __launch_bounds__(kT) k_group_info(const unsigned *gbegin, unsigned n,
                                                    const uint4 *sq, uint2 *gr_r, uint4 *gr_a,
-                                                   uint4 *gr_b, const Status *st) {
+                                                   uint4 *gr_b, const double *ssc, const SetInfo *sets,
+                                                   long long *gr_thr, const Status *st) {
     const unsigned ng = st->ngroups;
     const unsigned lane = threadIdx.x & 31;
     for (unsigned g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng;
@@ -429,8 +472,10 @@ __global__ void __launch_bounds__(kT) k_group_info(const unsigned *gbegin, unsig
         unsigned b = gbegin[g];
         unsigned e = (g + 1 < ng) ? gbegin[g + 1] : n;
         unsigned mn[3] = {kGrid, kGrid, kGrid}, mx[3] = {0, 0, 0};
+        double smax = 0.0;
         for (unsigned p = b + lane; p < e; p += 32) {
             uint4 q = sq[p];
+            smax = fmax(smax, ssc[p]);
             mn[0] = min(mn[0], q.x); mn[1] = min(mn[1], q.y); mn[2] = min(mn[2], q.z);
             mx[0] = max(mx[0], q.x); mx[1] = max(mx[1], q.y); mx[2] = max(mx[2], q.z);
         }
@@ -438,8 +483,11 @@ __global__ void __launch_bounds__(kT) k_group_info(const unsigned *gbegin, unsig
             mn[d] = __reduce_min_sync(0xffffffffu, mn[d]);
             mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
         if (lane == 0) {
             unsigned set = sq[b].w;
+            if (gr_thr) gr_thr[g] = gap_threshold(sets[set], smax);
             gr_r[g] = make_uint2(b, e - b);
             gr_a[g] = make_uint4(mn[0], mn[1], mn[2], set);
             gr_b[g] = make_uint4(mx[0], mx[1], mx[2], set /* root node of the set */);
@@ -472,14 +520,21 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     k_box_finalize<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.bmin, A.bmax);
     k_keys<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, n, set_of, A.sets, A.keys_in, A.vals_in, A.qbuf);
     nk += 4;
+    const double *scale = A.scale;
+    if (A.massdep && !scale) {           // Eq. 12 factors from the masses
+        k_set_mean_mass<<<A.nsets, kT, 0, st>>>(A.mass, A.sets, A.set_mean);
+        k_eq12_scale<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.mass, n, set_of, A.set_mean, A.scale_buf);
+        scale = A.scale_buf;
+        nk += 2;
+    }
     int set_bits = 0;
     if (A.nsets > 1) {
         while ((1 << set_bits) < A.nsets) set_bits++;
     }
     nk += radix_sort(A.keys_in, A.vals_in, A.skey, A.perm, A.n_dev, n, 0, 3 * kBits, set_of,
                      set_bits, A.sort_tmp, st);
-    k_gather<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, A.mass, n, A.perm, A.qbuf, A.sp64, A.spH,
-                                                   A.spL, A.sq);
+    k_gather<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, A.mass, n, A.perm, A.qbuf, scale, A.ssc,
+                                                   A.sp64, A.spH, A.spL, A.sq);
     // topology
     k_topo_roots<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.nd_a, A.nd_b, A.nd_r, S);
     nk += 2;
@@ -497,7 +552,8 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     nk++;
     for (int l = kMaxLevel; l >= 0; l--) {
         k_moments<<<gmax, kT, 0, st>>>(l, A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q,
-                                       A.nd_t, A.nd_f, A.cap_nodes, S);
+                                       A.nd_t, A.nd_f, A.ssc, A.sets, A.massdep ? A.nd_thr : nullptr,
+                                       A.cap_nodes, S);
         nk++;
     }
     // groups
@@ -506,7 +562,8 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     nk++;
     nk += scan_exclusive<unsigned>(A.gflag, A.tmp_u32b, A.n_dev, nullptr, &S->ngroups, A.scan_tmp, st);
     k_group_emit<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.gflag, A.tmp_u32b, n, A.gbegin);
-    k_group_info<<<gmax, kT, 0, st>>>(A.gbegin, n, A.sq, A.gr_r, A.gr_a, A.gr_b, S);
+    k_group_info<<<gmax, kT, 0, st>>>(A.gbegin, n, A.sq, A.gr_r, A.gr_a, A.gr_b, A.ssc, A.sets,
+                                      A.massdep ? A.gr_thr : nullptr, S);
     nk += 2;
     return nk;
 }

@@ -141,21 +141,23 @@ __device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB,
 // r^2 below r_out^2 (1 + 2^-10)), K = W = 0 exactly for all of them and the
 // plain Newtonian pair is evaluated; otherwise every lane takes the full
 // changeover path and neighbour candidates are confirmed in float64.
-template <int NI, int J, bool NB>
+template <int NI, int J, bool NB, bool MD>
 __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, const float4 *sL,
-                                          int s, int cnt, const ChgF &C, const float (&hx)[NI],
-                                          const float (&hy)[NI], const float (&hz)[NI],
-                                          const float (&lx)[NI], const float (&ly)[NI],
-                                          const float (&lz)[NI], const unsigned (&pid)[NI],
+                                          const unsigned *sI, int s, int cnt, const ChgF &C,
+                                          const float (&hx)[NI], const float (&hy)[NI],
+                                          const float (&hz)[NI], const float (&lx)[NI],
+                                          const float (&ly)[NI], const float (&lz)[NI],
+                                          const float (&invs_t)[NI], const unsigned (&pid)[NI],
                                           const bool (&valid)[NI], int nvalid, double rout2,
-                                          float (&pa)[NI][4], unsigned &n_full, unsigned &n_fast) {
+                                          double rout, float (&pa)[NI][4], unsigned &n_full,
+                                          unsigned &n_fast) {
     const int iters = (cnt + J - 1) / J;
 #pragma unroll 2
     for (int it = 0; it < iters; it++) {
         const int j = it * J + s;
         const float4 H = sH[j];
         const float4 L = sL[j];
-        float dx[NI], dy[NI], dz[NI], r2[NI];
+        float dx[NI], dy[NI], dz[NI], r2[NI], q2[NI], invs[NI];
         bool near = false;
 #pragma unroll
         for (int k = 0; k < NI; k++) {
@@ -163,22 +165,33 @@ __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, 
             dy[k] = (H.y - hy[k]) + (L.y - ly[k]);
             dz[k] = (H.z - hz[k]) + (L.z - lz[k]);
             r2[k] = fmaf(dz[k], dz[k], fmaf(dy[k], dy[k], dx[k] * dx[k]));
-            near |= r2[k] < C.rout2m;
+            if (MD) {       // pair radii s_ij (r_in, r_out); 1/s_ij is the smaller inverse (L.w = 1/s_j)
+                invs[k] = fminf(invs_t[k], L.w);
+                q2[k] = r2[k] * (invs[k] * invs[k]);
+            } else {
+                invs[k] = 1.0f;
+                q2[k] = r2[k];
+            }
+            near |= q2[k] < C.rout2m;
         }
         const unsigned real = (j < cnt) ? (unsigned)nvalid : 0u;
         if (__any_sync(0xffffffffu, near)) {
             n_full += real;
 #pragma unroll
             for (int k = 0; k < NI; k++) {
-                if (NB && r2[k] < C.rout2m) {
-                    const unsigned pj = __float_as_uint(L.w);
-                    if (valid[k] && j < cnt && pj != pid[k] &&
-                        exact_r2(A.sp64[pid[k]], A.sp64[pj]) < rout2)
+                if (NB && q2[k] < C.rout2m && valid[k] && j < cnt) {
+                    const unsigned pj = sI[j];
+                    double ro2 = rout2;
+                    if (MD) {
+                        const double ro = __dmul_rn(rout, fmax(A.ssc[pid[k]], A.ssc[pj]));
+                        ro2 = __dmul_rn(ro, ro);
+                    }
+                    if (pj != pid[k] && exact_r2(A.sp64[pid[k]], A.sp64[pj]) < ro2)
                         emit_pair(A, pid[k], pj);
                 }
                 const float r2c = fmaxf(r2[k], C.tiny);
                 const float rinv = rsqrtf(r2c);
-                const float r = r2c * rinv;
+                const float r = MD ? (r2c * rinv) * invs[k] : r2c * rinv;    // r / s_ij
                 const float xs = __saturatef(fmaf(r, C.invw, C.c0));
                 // K(xs) = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4)
                 const float t = xs - 1.0f;
@@ -225,10 +238,11 @@ __device__ __forceinline__ void fold(float (&pa)[NI][4], float (&fh)[NI][4], flo
         }
 }
 
-template <int NI, int J, int ORDER, bool NB>
+template <int NI, int J, int ORDER, bool NB, bool MD>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                             const ChgF &C, double rout2, float4 (*sA)[kJ], float4 (*sB)[kJ],
-                             float2 (*sC)[kJ], double (*red)[kSlotMax][4]) {
+                             const ChgF &C, double rout2, double rout, float4 (*sA)[kJ],
+                             float4 (*sB)[kJ], float2 (*sC)[kJ], unsigned (*sI)[kJ],
+                             double (*red)[kSlotMax][4]) {
     constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = lane / L, l = lane % L;
@@ -283,12 +297,13 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
     }
     // ---- particle-particle: float-float differences
     {
-        float hx[NI], hy[NI], hz[NI], lx[NI], ly[NI], lz[NI];
+        float hx[NI], hy[NI], hz[NI], lx[NI], ly[NI], lz[NI], invs_t[NI];
 #pragma unroll
         for (int k = 0; k < NI; k++) {
             const float4 H = A.spH[pid[k]], L4 = A.spL[pid[k]];
             hx[k] = H.x; hy[k] = H.y; hz[k] = H.z;
             lx[k] = L4.x; ly[k] = L4.y; lz[k] = L4.z;
+            invs_t[k] = L4.w;                                    // 1 / s_i
         }
         int nvalid = 0;
 #pragma unroll
@@ -305,21 +320,21 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
                 if (e < cnt) {
                     const unsigned p = A.pp[po + t + e];
                     sA[w][e] = A.spH[p];
-                    float4 L4 = A.spL[p];
-                    L4.w = __uint_as_float(p);
-                    sB[w][e] = L4;
+                    sB[w][e] = A.spL[p];
+                    sI[w][e] = p;
                 } else if (e < cntJ) {                    // massless, far away
                     sA[w][e] = make_float4(1e15f, 1e15f, 1e15f, 0.0f);
-                    sB[w][e] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(0xffffffffu));
+                    sB[w][e] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+                    sI[w][e] = 0xffffffffu;
                 }
             }
             __syncwarp();
             if (NB && A.want_nb)
-                pp_tile_f<NI, J, true>(A, sA[w], sB[w], s, cnt, C, hx, hy, hz, lx, ly, lz, pid, valid,
-                                       nvalid, rout2, pa, n_full, n_fast);
+                pp_tile_f<NI, J, true, MD>(A, sA[w], sB[w], sI[w], s, cnt, C, hx, hy, hz, lx, ly, lz,
+                                           invs_t, pid, valid, nvalid, rout2, rout, pa, n_full, n_fast);
             else
-                pp_tile_f<NI, J, false>(A, sA[w], sB[w], s, cnt, C, hx, hy, hz, lx, ly, lz, pid, valid,
-                                        nvalid, rout2, pa, n_full, n_fast);
+                pp_tile_f<NI, J, false, MD>(A, sA[w], sB[w], sI[w], s, cnt, C, hx, hy, hz, lx, ly, lz,
+                                            invs_t, pid, valid, nvalid, rout2, rout, pa, n_full, n_fast);
             __syncwarp();
             fold<NI>(pa, fh, fl);
         }
@@ -354,7 +369,8 @@ __device__ __forceinline__ void write_targets(const ForceArgs &A, const uint2 gr
             for (int c = 0; c < 4; c++) s[c] += red[w][t][c];
         const unsigned p = gr.x + i0 + t;
         const double m = A.sp64[p].w;
-        const double P = s[3] - m * c2;              // remove the self entry
+        // remove the self entry m_i 2 / (s_i (r_out + r_in))
+        const double P = s[3] - (A.massdep ? m * c2 / A.ssc[p] : m * c2);
         const unsigned i = A.perm[p];
         const double ax = A.G * s[0], ay = A.G * s[1], az = A.G * s[2], phi = -A.G * P;
         A.acc[3ull * i] = ax;
@@ -386,24 +402,26 @@ __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, d
 
 // Pass configuration for `rem` remaining targets: returns the slot count and
 // runs the matching instantiation.
-template <int ORDER, bool NB>
+template <int ORDER, bool NB, bool MD>
 __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                               const ChgF &C, double rout2, float4 (*sA)[kJ], float4 (*sB)[kJ],
-                               float2 (*sC)[kJ], double (*red)[kSlotMax][4]) {
+                               const ChgF &C, double rout2, double rout, float4 (*sA)[kJ],
+                               float4 (*sB)[kJ], float2 (*sC)[kJ], unsigned (*sI)[kJ],
+                               double (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
-    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 24; }
-    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 32; }
-    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 48; }
-    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red); return 64; }
-    group_pass_f<3, 1, ORDER, NB>(A, g, gr, i0, C, rout2, sA, sB, sC, red);
+    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 24; }
+    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 32; }
+    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 48; }
+    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 64; }
+    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red);
     return 96;
 }
 
-template <int ORDER, bool NB>
+template <int ORDER, bool NB, bool MD>
 __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(ForceArgs A) {
     __shared__ float4 sA[kFWarps][kJ];
     __shared__ float4 sB[kFWarps][kJ];
     __shared__ float2 sC[kFWarps][kJ];
+    __shared__ unsigned sI[kFWarps][kJ];
     __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
@@ -429,7 +447,8 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         C.rout2m = (float)(C64.rout2 * (1.0 + 1.0 / 1024.0));
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y;) {
-            const unsigned slots = mixed_pass<ORDER, NB>(A, g, gr, i0, C, C64.rout2, sA, sB, sC, red);
+            const unsigned slots =
+                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sA, sB, sC, sI, red);
             __syncthreads();
             write_targets(A, gr, i0, slots, C64.c2, red, ep);
             __syncthreads();
@@ -485,10 +504,11 @@ __device__ __forceinline__ void cells_tile_d(const double4 *sA, const double4 *s
     }
 }
 
-template <int NI, bool NB>
+template <int NI, bool NB, bool MD>
 __device__ __forceinline__ void pp_tile_d(const ForceArgs &A, const double4 *sP, const unsigned *sI,
-                                          int cnt, const Chg &C, const double (&xx)[2],
-                                          const double (&xy)[2], const double (&xz)[2],
+                                          const double *sS, int cnt, const Chg &C,
+                                          const double (&xx)[2], const double (&xy)[2],
+                                          const double (&xz)[2], const double (&st)[2],
                                           const unsigned (&pid)[2], const bool (&valid)[2],
                                           double (&pa)[2][4]) {
     for (int j = 0; j < cnt; j++) {
@@ -497,13 +517,19 @@ __device__ __forceinline__ void pp_tile_d(const ForceArgs &A, const double4 *sP,
         for (int s = 0; s < NI; s++) {
             const double dx = __dsub_rn(P.x, xx[s]), dy = __dsub_rn(P.y, xy[s]), dz = __dsub_rn(P.z, xz[s]);
             const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            if (NB && r2 < C.rout2) {
+            double rout2 = C.rout2, sij = 1.0;
+            if (MD) {                       // pair radii s_ij (r_in, r_out), s_ij = max(s_i, s_j)
+                sij = fmax(st[s], sS[j]);
+                const double ro = __dmul_rn(C.ro, sij);
+                rout2 = __dmul_rn(ro, ro);
+            }
+            if (NB && r2 < rout2) {
                 const unsigned pj = sI[j];
                 if (valid[s] && pj != pid[s]) emit_pair(A, pid[s], pj);
             }
             const double r2c = fmax(r2, C.tiny);
             const double rinv = rsqrt(r2c);
-            const double r = r2c * rinv;
+            const double r = MD ? (r2c * rinv) / sij : r2c * rinv;     // r / s_ij
             const double xs = fmin(fmax(fma(r, C.invw, C.c0), 0.0), 1.0);
             const double t = xs - 1.0;
             const double t2 = t * t;
@@ -523,12 +549,13 @@ __device__ __forceinline__ void pp_tile_d(const ForceArgs &A, const double4 *sP,
     }
 }
 
-template <int NI, int ORDER, bool NB>
+template <int NI, int ORDER, bool NB, bool MD>
 __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                              const Chg &C, double4 (*sA)[kJ], double4 (*sB)[kJ],
-                             double2 (*sC)[kJ], unsigned (*sI)[kJ], double (*red)[kSlotMax][4]) {
+                             double2 (*sC)[kJ], unsigned (*sI)[kJ], double (*sS)[kJ],
+                             double (*red)[kSlotMax][4]) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double xx[2], xy[2], xz[2];
+    double xx[2], xy[2], xz[2], st[2];
     unsigned pid[2];
     bool valid[2];
 #pragma unroll
@@ -538,6 +565,7 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
         pid[s] = gr.x + (valid[s] ? idx : 0u);
         const double4 P = A.sp64[pid[s]];
         xx[s] = P.x; xy[s] = P.y; xz[s] = P.z;
+        st[s] = MD ? A.ssc[pid[s]] : 1.0;
     }
     double pa[2][4];
 #pragma unroll
@@ -576,13 +604,14 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
                 const unsigned p = A.pp[po + t + e];
                 sA[w][e] = A.sp64[p];
                 sI[w][e] = p;
+                if (MD) sS[w][e] = A.ssc[p];
             }
         }
         __syncwarp();
         if (NB && A.want_nb)
-            pp_tile_d<NI, true>(A, sA[w], sI[w], cnt, C, xx, xy, xz, pid, valid, pa);
+            pp_tile_d<NI, true, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
         else
-            pp_tile_d<NI, false>(A, sA[w], sI[w], cnt, C, xx, xy, xz, pid, valid, pa);
+            pp_tile_d<NI, false, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
         __syncwarp();
     }
 #pragma unroll
@@ -591,12 +620,13 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
         for (int c = 0; c < 4; c++) red[w][lane + 32 * s][c] = (s < NI) ? pa[s][c] : 0.0;
 }
 
-template <int ORDER, bool NB>
+template <int ORDER, bool NB, bool MD>
 __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     __shared__ double4 sA[kFWarps][kJ];
     __shared__ double4 sB[kFWarps][kJ];
     __shared__ double2 sC[kFWarps][kJ];
     __shared__ unsigned sI[kFWarps][kJ];
+    __shared__ double sS[kFWarps][MD ? kJ : 1];
     __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
@@ -612,9 +642,9 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y; i0 += kIB) {
             if (gr.y - i0 > 32)
-                group_pass_d<2, ORDER, NB>(A, g, gr, i0, C, sA, sB, sC, sI, red);
+                group_pass_d<2, ORDER, NB, MD>(A, g, gr, i0, C, sA, sB, sC, sI, (double (*)[kJ])sS, red);
             else
-                group_pass_d<1, ORDER, NB>(A, g, gr, i0, C, sA, sB, sC, sI, red);
+                group_pass_d<1, ORDER, NB, MD>(A, g, gr, i0, C, sA, sB, sC, sI, (double (*)[kJ])sS, red);
             __syncthreads();
             write_targets(A, gr, i0, kIB, C.c2, red, ep);
             __syncthreads();
@@ -666,12 +696,23 @@ __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, con
 
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
     const int blocks = 152 * 8;
+    const bool md = A.massdep != 0;
     if (precision == 1) {
-        if (A.order == 2) k_force_mixed<2, true><<<blocks, kFThreads, 0, st>>>(A);
-        else k_force_mixed<0, true><<<blocks, kFThreads, 0, st>>>(A);
+        if (A.order == 2) {
+            if (md) k_force_mixed<2, true, true><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_mixed<2, true, false><<<blocks, kFThreads, 0, st>>>(A);
+        } else {
+            if (md) k_force_mixed<0, true, true><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_mixed<0, true, false><<<blocks, kFThreads, 0, st>>>(A);
+        }
     } else {
-        if (A.order == 2) k_force_fp64<2, true><<<blocks, kFThreads, 0, st>>>(A);
-        else k_force_fp64<0, true><<<blocks, kFThreads, 0, st>>>(A);
+        if (A.order == 2) {
+            if (md) k_force_fp64<2, true, true><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_fp64<2, true, false><<<blocks, kFThreads, 0, st>>>(A);
+        } else {
+            if (md) k_force_fp64<0, true, true><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_fp64<0, true, false><<<blocks, kFThreads, 0, st>>>(A);
+        }
     }
     return 1;
 }

@@ -38,6 +38,14 @@ struct BuildArgs {
     uint2 *gr_r;
     uint4 *gr_a, *gr_b;
     int n_leaf, n_group;
+    // mass-dependent changeover radii (Eq. 12): per-particle factors in input
+    // order (NULL: computed from the masses when massdep, else all 1)
+    const double *scale;
+    int massdep;
+    double *scale_buf;               // n (device-computed factors)
+    double *set_mean;                // nsets
+    double *ssc;                     // n, sorted factors
+    long long *nd_thr, *gr_thr;      // gap thresholds per node / group
     Status *status;
     ScanTmp scan_tmp;
     SortTmp sort_tmp;
@@ -49,6 +57,8 @@ struct WalkArgs {
     const uint2 *gr_r;
     const uint4 *gr_a, *gr_b;
     const SetInfo *sets;
+    const long long *nd_thr, *gr_thr;    // per node / group gap thresholds (massdep)
+    int massdep;
     WalkParams wp;
     unsigned *gr_nc, *gr_np;
     unsigned long long *gr_co, *gr_po;   // ngroups + 1
@@ -71,6 +81,8 @@ struct ForceArgs {
     const float4 *nd_f;
     const SetInfo *sets;
     const unsigned *perm;
+    const double *ssc;               // sorted radius factors (massdep)
+    int massdep;
     double *acc, *pot;               // input (caller) order, device
     double G;
     int order;                       // 0 or 2
@@ -99,6 +111,7 @@ struct NbArgs {
 // Per-set pointer table of a batch (device resident).
 struct BatchTab {
     const double *pos, *mass;
+    const double *scale;             // radius factors or NULL
     double *acc, *pot;
     long long *nb_off;
     int *nb_idx;
@@ -106,7 +119,7 @@ struct BatchTab {
 };
 
 int batch_gather_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
-                        double *pos, double *mass, cudaStream_t st);
+                        double *pos, double *mass, double *scale, cudaStream_t st);
 int batch_scatter_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
                          const double *acc, const double *pot, cudaStream_t st);
 int batch_nb_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,

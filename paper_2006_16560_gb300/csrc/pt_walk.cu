@@ -16,7 +16,7 @@ namespace pt {
 constexpr int kWalkWarps = 4;
 constexpr int kWalkThreads = 32 * kWalkWarps;
 
-template <bool FILL>
+template <bool FILL, bool MD>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     extern __shared__ unsigned stack_mem[];      // kWalkWarps x A.stack_cap entries
     __shared__ unsigned pfx[kWalkWarps][32];
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ng) break;
         const uint4 ga = A.gr_a[g], gb = A.gr_b[g];
-        const long long r2thr = A.sets[ga.w].r2thr;
+        const long long r2thr = MD ? A.gr_thr[g] : A.sets[ga.w].r2thr;
         const int glo[3] = {2 * (int)ga.x, 2 * (int)ga.y, 2 * (int)ga.z};
         const int ghi[3] = {2 * (int)gb.x + 2, 2 * (int)gb.y + 2, 2 * (int)gb.z + 2};
         unsigned long long cbase = 0, pbase = 0;
@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
                     gg = max(gg, 0);
                     gap2 += (long long)gg * gg;
                 }
-                accept = (d2 >= ithr[level]) && (gap2 >= r2thr);
+                // mass-dependent radii: the larger of the group's and the cell's threshold
+                const long long thr = MD ? max(r2thr, A.nd_thr[v]) : r2thr;
+                accept = (d2 >= ithr[level]) && (gap2 >= thr);
                 leaf = meta_leaf(a.w);
                 if (!accept) {
                     if (leaf) {
@@ -153,9 +155,10 @@ int walk_init() {
     // the largest stack the walk may use, set once per context (kernel
     // attributes are not stream work and stay out of captured graphs)
     const int smem = (int)((size_t)kWalkWarps * kWalkStackLarge * sizeof(unsigned));
-    if (cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return 1;
-    if (cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_walk<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 1;
     return 0;
 }
@@ -168,7 +171,8 @@ int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
     per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
     const int blocks = 152 * per_sm;
     if (phase == 0) {
-        k_walk<false><<<blocks, kWalkThreads, smem, st>>>(A);
+        if (A.massdep) k_walk<false, true><<<blocks, kWalkThreads, smem, st>>>(A);
+        else k_walk<false, false><<<blocks, kWalkThreads, smem, st>>>(A);
         int nk = 1;
         nk += scan_exclusive<unsigned long long>(A.gr_nc, A.gr_co, &A.st->ngroups, &A.st->cell_total,
                                                  nullptr, A.scan_tmp, st);
@@ -176,7 +180,8 @@ int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
                                                  nullptr, A.scan_tmp, st);
         return nk;
     }
-    k_walk<true><<<blocks, kWalkThreads, smem, st>>>(A);
+    if (A.massdep) k_walk<true, true><<<blocks, kWalkThreads, smem, st>>>(A);
+    else k_walk<true, false><<<blocks, kWalkThreads, smem, st>>>(A);
     return 1;
 }
 
