@@ -32,7 +32,14 @@ namespace pt {
 
 constexpr int kFWarps = 4;
 constexpr int kFThreads = 32 * kFWarps;
-constexpr int kJ = 64;        // list entries per warp tile
+#ifndef PT_FORCE_TILE
+#define PT_FORCE_TILE 64
+#endif
+#ifndef PT_FORCE_UNROLL
+#define PT_FORCE_UNROLL 2
+#endif
+constexpr int kJ = PT_FORCE_TILE;   // list entries per warp tile
+constexpr int kUnroll = PT_FORCE_UNROLL;   // unroll of the inner list loops
 constexpr int kIB = 64;       // targets per pass of the float64 kernel (two per lane)
 constexpr int kSlotMax = 96;  // largest pass of the mixed kernel
 #ifndef PT_FORCE_MIN_BLOCKS
@@ -95,7 +102,7 @@ __device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB,
                                              int s, int cnt, const float (&ox)[NI],
                                              const float (&oy)[NI], const float (&oz)[NI],
                                              float (&pa)[NI][4]) {
-#pragma unroll 2
+#pragma unroll kUnroll
     for (int j = s; j < cnt; j += J) {
         const float4 c = sA[j];
         float4 q;
@@ -152,7 +159,7 @@ __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, 
                                           double rout, float (&pa)[NI][4], unsigned &n_full,
                                           unsigned &n_fast) {
     const int iters = (cnt + J - 1) / J;
-#pragma unroll 2
+#pragma unroll kUnroll
     for (int it = 0; it < iters; it++) {
         const int j = it * J + s;
         const float4 H = sH[j];
@@ -275,7 +282,7 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
             const int cnt = (int)min((unsigned)kJ, nc - t);
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
+            for (int h = 0; h < kJ / 32; h++) {
                 const int e = lane + 32 * h;
                 if (e < cnt) {
                     const unsigned v = A.cells[co + t + e];
@@ -315,7 +322,7 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
             const int cnt = (int)min((unsigned)kJ, np - t);
             const int cntJ = (cnt + J - 1) / J * J;
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
+            for (int h = 0; h < kJ / 32; h++) {
                 const int e = lane + 32 * h;
                 if (e < cnt) {
                     const unsigned p = A.pp[po + t + e];
@@ -577,7 +584,7 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
     for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
         const int cnt = (int)min((unsigned)kJ, nc - t);
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < kJ / 32; h++) {
             const int e = lane + 32 * h;
             if (e < cnt) {
                 const unsigned v = A.cells[co + t + e];
@@ -598,7 +605,7 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
     for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
         const int cnt = (int)min((unsigned)kJ, np - t);
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < kJ / 32; h++) {
             const int e = lane + 32 * h;
             if (e < cnt) {
                 const unsigned p = A.pp[po + t + e];

@@ -19,6 +19,11 @@ generators here reproduce that structure:
                       log-uniform semi-major axis in AU (1 AU = 3.726e-6 NB
                       for a 1 pc half-mass radius), thermal eccentricity,
                       uniform mean anomaly and random orientation.
+* ``kroupa95_binaries`` -- the paper's own binary population (Sec. 7.1.1,
+                      Eq. 39): every star in a binary, periods from the
+                      Kroupa (1995) distribution truncated to log10 P in
+                      [1, 8.43] days, thermal eccentricities, Kroupa masses
+                      0.08-40 Msun, Kepler's third law for the semi-major axes.
 * ``cluster_ensemble`` -- many independent clusters with log-uniform sizes.
 
 Every array is float64; positions are (n, 3) row-major.
@@ -164,6 +169,53 @@ def plummer_binaries(n_pairs: int, seed: int, amin_au: float = 0.005,
     vel = np.repeat(cen["vel"], 2, axis=0)
     return {"pos": np.ascontiguousarray(pos), "vel": vel, "mass": mass,
             "semi_major": a}
+
+
+KROUPA95_LOGP_MIN = 1.0      # log10 of the period in days (Sec. 7.1.1)
+KROUPA95_LOGP_MAX = 8.43
+
+
+def kroupa95_log_periods(n: int, rng: np.random.Generator) -> np.ndarray:
+    """log10 P [days] from Eq. 39, F(P) = 2.5 (lg P - 1) / (45 + (lg P - 1)^2),
+    truncated to [1, 8.43]: with x = lg P - 1 the cumulative distribution is
+    ln(1 + x^2/45) / ln(1 + x_max^2/45), inverted in closed form."""
+    xmax = KROUPA95_LOGP_MAX - KROUPA95_LOGP_MIN
+    u = rng.uniform(0.0, 1.0, n)
+    x = np.sqrt(45.0 * ((1.0 + xmax * xmax / 45.0) ** u - 1.0))
+    return KROUPA95_LOGP_MIN + x
+
+
+def kroupa95_binaries(n_pairs: int, seed: int, mmin: float = 0.08, mmax: float = 40.0) -> dict:
+    """Plummer cluster with 100% primordial binaries drawn like the paper's
+    N1kb..N1mkb models (Sec. 7.1.1): Kroupa IMF 0.08-40 Msun, periods from
+    Eq. 39, thermal eccentricity, half-mass radius 1 pc.  The pre-main-sequence
+    eigenevolution adjustment of tight orbits that the paper also applies is
+    not modelled.  Components of pair k are particles 2k and 2k+1."""
+    rng = rng_for(seed)
+    cen = plummer(n_pairs, seed, masses="equal", rng=rng)
+    m1 = kroupa_masses(n_pairs, rng, mmin=mmin, mmax=mmax)
+    m2 = kroupa_masses(n_pairs, rng, mmin=mmin, mmax=mmax)
+    lgp = kroupa95_log_periods(n_pairs, rng)
+    p_yr = 10.0 ** lgp / 365.25
+    a_au = ((m1 + m2) * p_yr * p_yr) ** (1.0 / 3.0)          # Kepler's third law, solar units
+    tot = m1.sum() + m2.sum()
+    a = a_au * AU_IN_NB
+    e = np.sqrt(rng.uniform(0.0, 1.0, n_pairs))
+    Manom = rng.uniform(0.0, 2.0 * math.pi, n_pairs)
+    E = _kepler_E(Manom, e)
+    rel = np.stack([a * (np.cos(E) - e), a * np.sqrt(1 - e * e) * np.sin(E),
+                    np.zeros(n_pairs)], axis=1)
+    rel = np.einsum("kij,kj->ki", _random_rotations(rng, n_pairs), rel)
+    mt = m1 + m2
+    pos = np.empty((2 * n_pairs, 3))
+    pos[0::2] = cen["pos"] - (m2 / mt)[:, None] * rel
+    pos[1::2] = cen["pos"] + (m1 / mt)[:, None] * rel
+    mass = np.empty(2 * n_pairs)
+    mass[0::2] = m1 / tot
+    mass[1::2] = m2 / tot
+    pos -= (mass[:, None] * pos).sum(0)
+    return {"pos": np.ascontiguousarray(pos), "vel": np.repeat(cen["vel"], 2, axis=0), "mass": mass,
+            "semi_major": a, "log_period_days": lgp, "ecc": e, "m1_msun": m1, "m2_msun": m2}
 
 
 def r_out_first_guess(n: int, total_mass: float = 1.0, sigma2: float = 1.0 / 6.0) -> float:

@@ -84,3 +84,20 @@ def test_binaries_1m(ctx):
 def test_kroupa_plummer_10m(ctx):
     d = inputs.plummer(10_000_000, 2, masses="kroupa")
     sampled_parity(ctx, d, c2_params(), 100, 9, check_mixed=False)
+
+
+def test_kroupa95_binaries_200k(ctx):
+    """The paper's own binary population (Eq. 39 periods, N100kb-like r_out of
+    Table 2): every companion closer than r_out is a neighbour."""
+    d = inputs.kroupa95_binaries(100_000, 12)
+    p = B.Params(theta=0.3, r_in=0.0004, r_out=0.004, n_leaf=16, n_group=64, order=2,
+                 precision=B.PT_FP64)
+    o = sampled_parity(ctx, d, p, 200, 13)
+    g = o["g64"]
+    n = len(d["mass"])
+    sep = np.linalg.norm(d["pos"][0::2] - d["pos"][1::2], axis=1)
+    close = np.nonzero(sep < p.r_out * 0.999)[0]
+    assert len(close) > 1000
+    rows = np.repeat(np.arange(n), np.diff(g["nb_off"]))
+    have = set((rows.astype(np.int64) * n + g["nb_idx"]).tolist())
+    assert all((2 * k) * n + 2 * k + 1 in have for k in close[::13])
