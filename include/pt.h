@@ -313,6 +313,46 @@ int pt_tree_lists(pt_tree *tree, int64_t *cell_off, uint32_t *cells,
 /* Version of this ABI (1). */
 int pt_abi_version(void);
 
+/* ---- tidal tensor of a binary's perturbation (Sec. 6.4.1, Eqs. 25-28) ----
+ *
+ * Outside its members' changeover radii, the long-range force on a binary is
+ * the centre-of-mass acceleration plus a tidal correction, expanded in
+ * r' = r - r_cm to first order (order 2: symmetric A_ij, 6 elements
+ * xx xy xz yy yz zz) or second order (order 3: those plus the fully
+ * symmetric A_ijk, 10 elements xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz, with
+ * the 1/2 of the Taylor term folded into A_ijk as in Table 1):
+ *     A'_i(r') = A_ij r'_j (+ A_ijk r'_j r'_k).
+ * The elements are measured with zero-mass points around r_cm at distance
+ * scale d_c (order 2: 4 tetrahedron corners; order 3: 8 corners; Table 1)
+ * whose accelerations come from the ordinary long-range force, and are
+ * solved by least squares from M T = A' (Eq. 28).
+ *
+ * All arrays are float64, row-major, host or device memory (host arrays are
+ * staged through temporary device buffers; device arrays must be on the
+ * context's device); the caller owns them.  The calls run on the context's
+ * stream and return when the results are in place.  Errors: PT_ERR_ARG for
+ * a NULL context or pointer with n > 0 or an order other than 2 or 3
+ * (message in pt_last_error), PT_ERR_OOM, PT_ERR_CUDA.  n = 0 is a no-op. */
+
+/* points (n x P x 3, P = 4 for order 2, 8 for order 3): measure points
+ * r_cm[b] + d_c[b] * (Table 1 unit point p) of each of n binaries. */
+int pt_tidal_points(pt_ctx *ctx, int order, int64_t n, const double *r_cm, const double *d_c,
+                    double *points);
+
+/* acc (n x (1 + P) x 3): per binary the long-range acceleration at r_cm
+ * followed by those at its P measure points (in pt_tidal_points order).
+ * T (n x E, E = 6 for order 2, 16 for order 3): the fitted elements, in the
+ * order listed above. */
+int pt_tidal_tensor(pt_ctx *ctx, int order, int64_t n, const double *acc, const double *d_c,
+                    double *T);
+
+/* acc_out (n_query x 3) = acc_cm[owner[q]] + the expansion of T[owner[q]] at
+ * rel[q] = r_q - r_cm (n_query x 3); owner (int64) indexes the n_binaries
+ * rows of T (n_binaries x E) and acc_cm (n_binaries x 3).  An owner outside
+ * [0, n_binaries) gives NaN for that query and touches nothing else. */
+int pt_tidal_eval(pt_ctx *ctx, int order, int64_t n_query, const int64_t *owner, const double *T,
+                  int64_t n_binaries, const double *acc_cm, const double *rel, double *acc_out);
+
 /* ---- allocation-free entry point ---- */
 
 /* Stable ascending sort of n 64-bit keys: keys_sorted[s] is the s-th

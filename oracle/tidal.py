@@ -71,9 +71,16 @@ def matrix(order: int, d_c: float = 1.0) -> np.ndarray:
 
 
 def fit(order: int, acc_cm, acc_pts, d_c: float) -> np.ndarray:
-    """T from the accelerations at the centre of mass and at the points."""
+    """T from the accelerations at the centre of mass and at the points.
+
+    As Table 1 writes it: the generalized inverse of M at unit distance,
+    applied to A', then divided by d_c for the rank-2 and by d_c^2 for the
+    rank-3 elements.  (The same T as pinv(M(d_c)) A' in exact arithmetic;
+    inverting M at scale d_c in floating point loses about log10(1/d_c)
+    digits, because its columns then differ in size by a factor 1/d_c.)"""
     Ap = (np.asarray(acc_pts, float) - np.asarray(acc_cm, float)[None, :]).reshape(-1)
-    return np.linalg.pinv(matrix(order, d_c)) @ Ap
+    k = np.array([len(e) - 1 for e in elements(order)], float)
+    return (np.linalg.pinv(matrix(order, 1.0)) @ Ap) / d_c ** k
 
 
 def evaluate(order: int, T, acc_cm, rel) -> np.ndarray:

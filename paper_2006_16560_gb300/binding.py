@@ -86,6 +86,9 @@ def lib():
                 "pt_tree_nodes": (I, [P, P, P, P]),
                 "pt_tree_groups": (I, [P, P]),
                 "pt_tree_lists": (I, [P, P, P, P, P]),
+                "pt_tidal_points": (I, [P, I, I64, P, P, P]),
+                "pt_tidal_tensor": (I, [P, I, I64, P, P, P]),
+                "pt_tidal_eval": (I, [P, I, I64, P, P, I64, P, P, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -154,6 +157,19 @@ def pt_autotune(ctx, descs, base: pt_params, leafs=None, groups=None, reps: int 
     rc = lib().pt_autotune(ctx, len(descs), arr, C.byref(base), la, len(leafs) if leafs else 0,
                            ga, len(groups) if groups else 0, reps, C.byref(best), C.byref(ms))
     return rc, best, ms.value
+
+
+def pt_tidal_points(ctx, order, n, r_cm_ptr, d_c_ptr, points_ptr) -> int:
+    return lib().pt_tidal_points(ctx, order, n, r_cm_ptr, d_c_ptr, points_ptr)
+
+
+def pt_tidal_tensor(ctx, order, n, acc_ptr, d_c_ptr, T_ptr) -> int:
+    return lib().pt_tidal_tensor(ctx, order, n, acc_ptr, d_c_ptr, T_ptr)
+
+
+def pt_tidal_eval(ctx, order, n_query, owner_ptr, T_ptr, n_binaries, acc_cm_ptr, rel_ptr, out_ptr) -> int:
+    return lib().pt_tidal_eval(ctx, order, n_query, owner_ptr, T_ptr, n_binaries, acc_cm_ptr, rel_ptr,
+                               out_ptr)
 
 
 class PTError(RuntimeError):
@@ -393,3 +409,42 @@ def longrange_force(ctx: Context, pos, mass, params: Params, neighbours: bool = 
     if neighbours:
         nb_idx = nb_idx[:total]
     return acc, pot, nb_off, nb_idx, st.as_dict()
+
+
+# ---- tidal tensor of a binary's perturbation (Sec. 6.4.1) -----------------
+
+TIDAL_POINTS = {2: 4, 3: 8}
+TIDAL_ELEMENTS = {2: 6, 3: 16}
+
+
+def _like(x, shape, dtype):
+    """Output array on the same side (CUDA tensor or numpy) as ``x``."""
+    if isinstance(x, np.ndarray):
+        return np.empty(shape, dtype=dtype)
+    import torch
+    return torch.empty(shape, dtype=getattr(torch, np.dtype(dtype).name), device=x.device)
+
+
+def tidal_points(ctx: Context, order: int, r_cm, d_c):
+    """(n, P, 3) measure points of n binaries (centres ``r_cm`` (n, 3), scales ``d_c`` (n,))."""
+    n = int(r_cm.shape[0])
+    out = _like(r_cm, (n, TIDAL_POINTS.get(order, 0), 3), np.float64)
+    ctx.check(pt_tidal_points(ctx.h, order, n, _ptr(r_cm), _ptr(d_c), _ptr(out)), "pt_tidal_points")
+    return out
+
+
+def tidal_tensor(ctx: Context, order: int, acc, d_c):
+    """(n, E) elements from ``acc`` (n, 1 + P, 3): centre of mass first, then the points."""
+    n = int(acc.shape[0])
+    out = _like(acc, (n, TIDAL_ELEMENTS.get(order, 0)), np.float64)
+    ctx.check(pt_tidal_tensor(ctx.h, order, n, _ptr(acc), _ptr(d_c), _ptr(out)), "pt_tidal_tensor")
+    return out
+
+
+def tidal_eval(ctx: Context, order: int, owner, T, acc_cm, rel):
+    """(n_query, 3) accelerations acc_cm[owner] + expansion of T[owner] at ``rel``."""
+    nq = int(owner.shape[0])
+    out = _like(rel, (nq, 3), np.float64)
+    ctx.check(pt_tidal_eval(ctx.h, order, nq, _ptr(owner), _ptr(T), int(T.shape[0]), _ptr(acc_cm),
+                            _ptr(rel), _ptr(out)), "pt_tidal_eval")
+    return out

@@ -1017,6 +1017,21 @@ int pt_ctx_destroy(pt_ctx *ctx) {
 
 const char *pt_last_error(const pt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
 
+}  // extern "C"
+
+namespace pt {
+cudaStream_t ctx_enter(pt_ctx *ctx) {
+    cudaSetDevice(ctx->device);
+    return ctx->stream;
+}
+int ctx_fail(pt_ctx *ctx, int code, const char *msg) {
+    snprintf(ctx->err, sizeof ctx->err, "%s", msg);
+    return code;
+}
+}  // namespace pt
+
+extern "C" {
+
 int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
                   const pt_params *params, pt_tree **tree) {
     return pt_tree_build_scaled(ctx, n, pos, mass, nullptr, params, tree);

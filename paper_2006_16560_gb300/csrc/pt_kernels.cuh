@@ -4,6 +4,8 @@
 
 #include "pt_internal.cuh"
 
+struct pt_ctx;
+
 namespace pt {
 
 constexpr unsigned kWalkStackSmall = 2048;   // per-warp walk stack entries (shared memory)
@@ -127,6 +129,10 @@ int batch_nb_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigne
                     cudaStream_t st);
 int build_launch(const BuildArgs &A, cudaStream_t st);   // returns kernels launched
 int walk_init();   // once per context: kernel attributes of the walk
+// Context access for the auxiliary entry points outside pt_api.cu: selects the
+// context's device and returns its stream; ctx_fail records a message.
+cudaStream_t ctx_enter(pt_ctx *ctx);
+int ctx_fail(pt_ctx *ctx, int code, const char *msg);
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st);
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st);
