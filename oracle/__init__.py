@@ -59,6 +59,12 @@ def lib():
                 ("orc_tree_walk", C.c_int, [_p, _i64, _dbl, _dbl, _p, _i64, _p, _i64, _p, _p]),
                 ("orc_cell_pull", None, [_p, _i64, _p, C.c_int, _p, _p]),
                 ("orc_tree_force", None, [_p, _dbl, _dbl, _dbl, _dbl, C.c_int, _i64, _p, _p, _p, _p]),
+                ("orc_pericentre", _dbl, [_p, _p, _dbl]),
+                ("orc_rnb", None, [_i64, _p, _p, _dbl, _dbl, _dbl, _p]),
+                ("orc_orbit_count", None, [_i64, _p, _p, _p, _p, _p, _dbl, _dbl, _dbl, C.c_int, _i64,
+                                           _p, _p, _p]),
+                ("orc_orbit_fill", None, [_i64, _p, _p, _p, _p, _p, _dbl, _dbl, _dbl, C.c_int, _i64,
+                                          _p, _p, _p]),
                 ("orc_abi_version", C.c_int, []),
             ]:
                 fn = getattr(L, name)
@@ -126,6 +132,51 @@ def neighbours(pos, r_out, targets=None, scale=None):
     idx = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
     lib().orc_neighbours_fill(n, _ptr(pos), r_out, nt, _ptr(tg), _ptr(off), _ptr(idx), _ptr(sc))
     return off, idx[: off[-1]]
+
+
+ORBIT_ROUT, ORBIT_RNB, ORBIT_CANDIDATES = 0, 1, 2
+
+
+def pericentre(dx, dv, mu) -> float:
+    """Kepler pericentre distance of the relative orbit (Sec. 6.3.1)."""
+    dx, dv = _f64(dx), _f64(dv)
+    return lib().orc_pericentre(_ptr(dx), _ptr(dv), float(mu))
+
+
+def neighbour_radius(vel, r_out, dt, C_r=3.0, scale=None):
+    """Eq. 24: r_nb,i = s_i r_out + C_r |v_i| dt."""
+    vel = _f64(vel)
+    sc = None if scale is None else _f64(scale)
+    out = np.zeros(len(vel))
+    lib().orc_rnb(len(vel), _ptr(vel), _ptr(sc), r_out, dt, C_r, _ptr(out))
+    return out
+
+
+def orbit_neighbours(pos, vel, mass, r_out, dt, C_r=3.0, C_v=1.5, G=1.0, mode=ORBIT_ROUT,
+                     scale=None, targets=None):
+    """Two-stage orbit-dependent neighbour sets (Sec. 6.3.1) as CSR
+    (offsets (nt+1,), idx) plus per-target stage-1 candidate counts.
+
+    mode ORBIT_ROUT keeps candidates with pericentre < C_v r_out,ij (the
+    reading used by the library), ORBIT_RNB the printed C_v r_nb,ij, and
+    ORBIT_CANDIDATES returns the stage-1 candidates themselves."""
+    pos, vel, mass = _f64(pos), _f64(vel), _f64(mass)
+    sc = None if scale is None else _f64(scale)
+    n = len(mass)
+    rnb = neighbour_radius(vel, r_out, dt, C_r, sc)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else len(tg)
+    cnt = np.zeros(nt, dtype=np.int64)
+    ncand = np.zeros(nt, dtype=np.int64)
+    L = lib()
+    L.orc_orbit_count(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(sc), _ptr(rnb), r_out, G, C_v, mode,
+                      nt, _ptr(tg), _ptr(cnt), _ptr(ncand))
+    off = np.zeros(nt + 1, dtype=np.int64)
+    np.cumsum(cnt, out=off[1:])
+    idx = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+    L.orc_orbit_fill(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(sc), _ptr(rnb), r_out, G, C_v, mode,
+                     nt, _ptr(tg), _ptr(off), _ptr(idx))
+    return off, idx[: off[-1]], ncand
 
 
 class Tree:

@@ -19,12 +19,15 @@
  *                      as a super-particle (centre of mass + multipoles)
  *   Sec. 6.4.2, Eqs. 30-31  quadrupole tensor and its traceless form
  *   Sec. 6 (Fig. 3 schedule, step 2)  tree neighbour search within r_out
+ *   Sec. 6.3.1, Eq. 24 orbit-dependent neighbour radius, pericentre stage
  *
  * Functions:
  *   orc_f / orc_W / orc_K      changeover functions exactly as printed
  *   orc_direct                 direct O(N^2) long-range acc and pot
  *   orc_direct_short           direct short-range part (split-identity pin)
  *   orc_neighbours_*           brute-force r_out neighbour sets
+ *   orc_pericentre, orc_rnb,   orbit-dependent neighbour radius (Eq. 24) and
+ *   orc_orbit_*                the two-stage pericentre selection (Sec. 6.3.1)
  *   orc_tree_*                 keys, stable sort, octree, moments, groups,
  *                              group-wise walk and tree force
  *
@@ -779,6 +782,116 @@ void orc_tree_force(orc_tree *t, double theta, double r_in, double r_out, double
         free(slot);
     }
     if (stats) { stats[0] = ci; stats[1] = pi; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Orbit-dependent neighbour criterion, Sec. 6.3.1, Eq. 24                   */
+/*                                                                          */
+/* Stage 1 (candidates): particle i searches within                         */
+/*     r_nb,i = r_out,i + C_r |v_i| dt_L        (Eq. 24; r_out,i = s_i r_out) */
+/* and j != i is a candidate of i when r_ij < r_nb,ij = max(r_nb,i, r_nb,j)  */
+/* (the larger radius, as for the pair radii of Eq. 12, so the relation is   */
+/* symmetric).  Stage 2 keeps candidate j when the pericentre distance of    */
+/* the two-body Kepler orbit of (i, j) is below C_v R_ij.  As printed,       */
+/* R_ij = r_nb,i; but a pericentre is never larger than the current         */
+/* separation, so with C_v >= 1 that test keeps every candidate.  The        */
+/* reading used by default is R_ij = r_out,ij = max(r_out,i, r_out,j): a     */
+/* candidate is kept if its orbit brings it (within the safety factor C_v)  */
+/* into the changeover region; mode 1 applies the printed R_ij = r_nb,ij.   */
+/* Every operation below is a single IEEE operation in the order written    */
+/* (no contraction), so each decision is reproducible bit for bit.          */
+/* ------------------------------------------------------------------------ */
+
+/* Pericentre of the relative Kepler orbit with separation dx, relative
+ * velocity dv and mu = G (m_i + m_j): with h = |dx x dv| and the
+ * eccentricity vector mu e = (v^2 - mu/r) dx - (dx . dv) dv, the pericentre
+ * is r_p = (h^2 / mu) / (1 + |e|).  (The eccentricity vector is used rather
+ * than e^2 = 1 + 2 E h^2 / mu^2, which cancels to half the digits for nearly
+ * circular orbits.)  Limits: dv = 0 gives r; mu = 0 (straight-line motion)
+ * gives the impact parameter h / |dv|; h = 0 with motion gives 0. */
+double orc_pericentre(const double *dx, const double *dv, double mu)
+{
+    double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    double v2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+    if (v2 == 0.0) return sqrt(r2);
+    double cx = dx[1] * dv[2] - dx[2] * dv[1];
+    double cy = dx[2] * dv[0] - dx[0] * dv[2];
+    double cz = dx[0] * dv[1] - dx[1] * dv[0];
+    double h2 = cx * cx + cy * cy + cz * cz;
+    if (mu == 0.0) return sqrt(h2 / v2);
+    double r = sqrt(r2);
+    double a = v2 - mu / r;
+    double b = dx[0] * dv[0] + dx[1] * dv[1] + dx[2] * dv[2];
+    double ex = a * dx[0] - b * dv[0];
+    double ey = a * dx[1] - b * dv[1];
+    double ez = a * dx[2] - b * dv[2];
+    double e = sqrt(ex * ex + ey * ey + ez * ez) / mu;
+    return (h2 / mu) / (1.0 + e);
+}
+
+/* Eq. 24 for every particle: r_nb[i] = s_i r_out + C_r (|v_i| dt). */
+void orc_rnb(int64_t n, const double *vel, const double *scale, double r_out, double dt,
+             double C_r, double *rnb)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const double *v = vel + 3 * i;
+        double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double ro = r_out * (scale ? scale[i] : 1.0);
+        rnb[i] = ro + C_r * (sp * dt);
+    }
+}
+
+/* 0: not a candidate, 1: candidate dropped by stage 2, 2: neighbour. */
+static int orbit_pair(const double *pos, const double *vel, const double *mass,
+                      const double *scale, const double *rnb, double r_out, double G,
+                      double C_v, int mode, int64_t i, int64_t j)
+{
+    double dx[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
+                    pos[3 * j + 2] - pos[3 * i + 2]};
+    double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    double R = rnb[i] > rnb[j] ? rnb[i] : rnb[j];
+    if (!(r2 < R * R)) return 0;
+    if (mode == 2) return 2;
+    double dv[3] = {vel[3 * j] - vel[3 * i], vel[3 * j + 1] - vel[3 * i + 1],
+                    vel[3 * j + 2] - vel[3 * i + 2]};
+    double rp = orc_pericentre(dx, dv, G * (mass[i] + mass[j]));
+    double Rs = mode == 1 ? R : r_out * pair_scale(scale, i, j);
+    return rp < C_v * Rs ? 2 : 1;
+}
+
+/* counts[t] (neighbours of target t after the chosen stage) and the number
+ * of stage-1 candidates in ncand[t]. */
+void orc_orbit_count(int64_t n, const double *pos, const double *vel, const double *mass,
+                     const double *scale, const double *rnb, double r_out, double G, double C_v,
+                     int mode, int64_t nt, const int64_t *targets, int64_t *counts, int64_t *ncand)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets ? targets[t] : t, c = 0, k = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            int s = orbit_pair(pos, vel, mass, scale, rnb, r_out, G, C_v, mode, i, j);
+            k += s > 0;
+            c += s == 2;
+        }
+        counts[t] = c;
+        if (ncand) ncand[t] = k;
+    }
+}
+
+/* Fill idx[offsets[t] ..] with the neighbours of target t, ascending. */
+void orc_orbit_fill(int64_t n, const double *pos, const double *vel, const double *mass,
+                    const double *scale, const double *rnb, double r_out, double G, double C_v,
+                    int mode, int64_t nt, const int64_t *targets, const int64_t *offsets,
+                    int32_t *idx)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets ? targets[t] : t, c = offsets[t];
+        for (int64_t j = 0; j < n; j++)
+            if (j != i && orbit_pair(pos, vel, mass, scale, rnb, r_out, G, C_v, mode, i, j) == 2)
+                idx[c++] = (int32_t)j;
+    }
 }
 
 int orc_abi_version(void) { return 1; }
