@@ -313,6 +313,50 @@ int pt_tree_lists(pt_tree *tree, int64_t *cell_off, uint32_t *cells,
 /* Version of this ABI (1). */
 int pt_abi_version(void);
 
+/* ---- orbit-dependent neighbour lists (Sec. 6.3.1, Eq. 24) ----
+ *
+ * Stage 1: particle i searches within r_nb,i = r_out,i + C_r |v_i| dt_L
+ * (Eq. 24; r_out,i = s_i r_out with the tree's radius factors when it was
+ * built mass-dependent, else r_out), and j != i is a candidate of i when
+ * r_ij < max(r_nb,i, r_nb,j) -- the larger radius, as for the pair radii of
+ * Eq. 12, so the relation is symmetric.  Stage 2 keeps a candidate when the
+ * pericentre of the pair's two-body Kepler orbit (mu = G (m_i + m_j); from
+ * the eccentricity vector, r_p = (h^2/mu) / (1 + e); the impact parameter
+ * when mu = 0; r_ij when the relative velocity is 0) is below C_v R_ij.  As
+ * printed, R_ij = r_nb; a pericentre never exceeds the current separation,
+ * so that form keeps every candidate when C_v >= 1.  PT_ORBIT_ROUT (the
+ * default reading) takes R_ij = r_out,ij = max(r_out,i, r_out,j): a
+ * candidate stays when its orbit reaches the changeover region within the
+ * safety factor C_v.  Every decision is made in float64, one IEEE operation
+ * at a time, so the lists equal a brute-force search bit for bit. */
+#define PT_ORBIT_ROUT 0         /* stage 2 with R_ij = r_out,ij */
+#define PT_ORBIT_RNB 1          /* stage 2 with R_ij = r_nb,ij (as printed) */
+#define PT_ORBIT_CANDIDATES 2   /* stage 1 only */
+
+typedef struct {
+    double dt;     /* dt_L, the long-range (tree) step, >= 0 */
+    double C_r;    /* Eq. 24 velocity coefficient (3.0 in the paper) */
+    double C_v;    /* pericentre safety factor (1.5 in the paper) */
+    int mode;      /* PT_ORBIT_* */
+} pt_orbit_params;
+
+/* On a tree built by pt_tree_build(_scaled) (its positions, masses, radius
+ * factors and G), with vel (n x 3 float64, input order, host or device):
+ * writes the CSR lists like pt_longrange_force (nb_offsets n + 1 int64,
+ * nb_idx int32 ascending within a row; NULL nb_offsets skips them), the
+ * number of stored pairs to *nb_total, the number of stage-1 candidate
+ * pairs (both directions) to *n_candidates, and Eq. 24's r_nb to r_nb
+ * (n float64, input order) when that is not NULL; outputs host or device.
+ * Too small a capacity returns PT_ERR_CAPACITY with *nb_total set.  The
+ * call reuses the tree's neighbour buffers (a later pt_longrange_force
+ * recomputes its own) and leaves the interaction lists untouched.
+ * Returns PT_OK, PT_ERR_ARG (unbuilt tree, NULL vel/params, negative or
+ * non-finite dt, C_r, C_v, unknown mode), PT_ERR_CAPACITY, PT_ERR_OOM,
+ * PT_ERR_CUDA, PT_ERR_INTERNAL. */
+int pt_orbit_neighbours(pt_tree *tree, const double *vel, const pt_orbit_params *params,
+                        int64_t *nb_offsets, int32_t *nb_idx, int64_t nb_capacity, int64_t *nb_total,
+                        int64_t *n_candidates, double *r_nb);
+
 /* ---- tidal tensor of a binary's perturbation (Sec. 6.4.1, Eqs. 25-28) ----
  *
  * Outside its members' changeover radii, the long-range force on a binary is

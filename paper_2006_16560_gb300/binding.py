@@ -56,6 +56,12 @@ class pt_cluster_desc(C.Structure):
                 ("nb_capacity", C.c_int64), ("nb_total", C.c_int64), ("radius_scale", C.c_void_p)]
 
 
+class pt_orbit_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("C_r", C.c_double), ("C_v", C.c_double), ("mode", C.c_int)]
+
+
+PT_ORBIT_ROUT, PT_ORBIT_RNB, PT_ORBIT_CANDIDATES = 0, 1, 2
+
 _lib = None
 _lock = threading.Lock()
 
@@ -86,6 +92,8 @@ def lib():
                 "pt_tree_nodes": (I, [P, P, P, P]),
                 "pt_tree_groups": (I, [P, P]),
                 "pt_tree_lists": (I, [P, P, P, P, P]),
+                "pt_orbit_neighbours": (I, [P, P, C.POINTER(pt_orbit_params), P, P, I64, C.POINTER(I64),
+                                            C.POINTER(I64), P]),
                 "pt_tidal_points": (I, [P, I, I64, P, P, P]),
                 "pt_tidal_tensor": (I, [P, I, I64, P, P, P]),
                 "pt_tidal_eval": (I, [P, I, I64, P, P, I64, P, P, P]),
@@ -157,6 +165,14 @@ def pt_autotune(ctx, descs, base: pt_params, leafs=None, groups=None, reps: int 
     rc = lib().pt_autotune(ctx, len(descs), arr, C.byref(base), la, len(leafs) if leafs else 0,
                            ga, len(groups) if groups else 0, reps, C.byref(best), C.byref(ms))
     return rc, best, ms.value
+
+
+def pt_orbit_neighbours(tree, vel_ptr, op: pt_orbit_params, nb_off_ptr, nb_idx_ptr, nb_capacity,
+                        rnb_ptr=None):
+    tot, cand = C.c_int64(0), C.c_int64(0)
+    rc = lib().pt_orbit_neighbours(tree, vel_ptr, C.byref(op), nb_off_ptr, nb_idx_ptr, nb_capacity,
+                                   C.byref(tot), C.byref(cand), rnb_ptr)
+    return rc, tot.value, cand.value
 
 
 def pt_tidal_points(ctx, order, n, r_cm_ptr, d_c_ptr, points_ptr) -> int:
@@ -274,6 +290,25 @@ class Tree:
             return total, st, rc
         self.ctx.check(rc, "pt_longrange_force")
         return total, st, rc
+
+    def orbit_neighbours(self, vel, dt: float, C_r: float = 3.0, C_v: float = 1.5,
+                         mode: int = PT_ORBIT_ROUT, nb_capacity: int | None = None, r_nb=None):
+        """Orbit-dependent neighbour lists (Sec. 6.3.1, Eq. 24) for velocities
+        ``vel`` (n, 3); returns (nb_offsets, nb_idx, n_candidates) on the side
+        (CUDA tensor or numpy) of ``vel``, growing the capacity as needed."""
+        op = pt_orbit_params(dt, C_r, C_v, mode)
+        cap = nb_capacity if nb_capacity is not None else max(8 * self.n, 1024)
+        for _ in range(2):
+            off = _empty_like(vel, (self.n + 1,), np.int64)
+            idx = _empty_like(vel, (max(cap, 1),), np.int32)
+            rc, total, cand = pt_orbit_neighbours(self.h, _ptr(vel), op, _ptr(off), _ptr(idx), cap,
+                                                  _ptr(r_nb))
+            if rc == PT_ERR_CAPACITY:
+                cap = total
+                continue
+            self.ctx.check(rc, "pt_orbit_neighbours")
+            return off, idx[:total], cand
+        self.ctx.check(rc, "pt_orbit_neighbours")
 
     # introspection (host numpy arrays)
     def info(self):
@@ -417,8 +452,8 @@ TIDAL_POINTS = {2: 4, 3: 8}
 TIDAL_ELEMENTS = {2: 6, 3: 16}
 
 
-def _like(x, shape, dtype):
-    """Output array on the same side (CUDA tensor or numpy) as ``x``."""
+def _empty_like(x, shape, dtype):
+    """Uninitialised array on the same side (CUDA tensor or numpy) as ``x``."""
     if isinstance(x, np.ndarray):
         return np.empty(shape, dtype=dtype)
     import torch
@@ -428,7 +463,7 @@ def _like(x, shape, dtype):
 def tidal_points(ctx: Context, order: int, r_cm, d_c):
     """(n, P, 3) measure points of n binaries (centres ``r_cm`` (n, 3), scales ``d_c`` (n,))."""
     n = int(r_cm.shape[0])
-    out = _like(r_cm, (n, TIDAL_POINTS.get(order, 0), 3), np.float64)
+    out = _empty_like(r_cm, (n, TIDAL_POINTS.get(order, 0), 3), np.float64)
     ctx.check(pt_tidal_points(ctx.h, order, n, _ptr(r_cm), _ptr(d_c), _ptr(out)), "pt_tidal_points")
     return out
 
@@ -436,7 +471,7 @@ def tidal_points(ctx: Context, order: int, r_cm, d_c):
 def tidal_tensor(ctx: Context, order: int, acc, d_c):
     """(n, E) elements from ``acc`` (n, 1 + P, 3): centre of mass first, then the points."""
     n = int(acc.shape[0])
-    out = _like(acc, (n, TIDAL_ELEMENTS.get(order, 0)), np.float64)
+    out = _empty_like(acc, (n, TIDAL_ELEMENTS.get(order, 0)), np.float64)
     ctx.check(pt_tidal_tensor(ctx.h, order, n, _ptr(acc), _ptr(d_c), _ptr(out)), "pt_tidal_tensor")
     return out
 
@@ -444,7 +479,7 @@ def tidal_tensor(ctx: Context, order: int, acc, d_c):
 def tidal_eval(ctx: Context, order: int, owner, T, acc_cm, rel):
     """(n_query, 3) accelerations acc_cm[owner] + expansion of T[owner] at ``rel``."""
     nq = int(owner.shape[0])
-    out = _like(rel, (nq, 3), np.float64)
+    out = _empty_like(rel, (nq, 3), np.float64)
     ctx.check(pt_tidal_eval(ctx.h, order, nq, _ptr(owner), _ptr(T), int(T.shape[0]), _ptr(acc_cm),
                             _ptr(rel), _ptr(out)), "pt_tidal_eval")
     return out

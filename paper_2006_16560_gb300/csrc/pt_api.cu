@@ -125,6 +125,7 @@ struct pt_tree {
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
     Buf in_scale, scale_buf, set_mean, ssc, nd_thr, gr_thr;   // mass-dependent radii
+    Buf orb_vel, orb_sv, orb_ndr, orb_ndthr, orb_grthr, orb_ctr, orb_rnb;   // orbit-dependent search
     Buf out_acc, out_pot;                                  // staging for host outputs
     // batch state (the context's batch tree only)
     Buf d_tab, d_totals, d_acc, d_pot;
@@ -157,7 +158,8 @@ struct pt_tree {
                       &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
-                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr};
+                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv,
+                      &orb_ndr, &orb_ndthr, &orb_grthr, &orb_ctr, &orb_rnb};
         for (Buf *b : all) b->release();
         d_tab.release(); d_totals.release(); d_acc.release(); d_pot.release();
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -1134,6 +1136,129 @@ int pt_longrange_force(pt_ctx *ctx, pt_tree *t, double *acc, double *pot, int64_
     }
     CK(cudaStreamSynchronize(st));
     fill_stats(t, stats, ms);
+    return rc;
+}
+
+int pt_orbit_neighbours(pt_tree *t, const double *vel, const pt_orbit_params *op, int64_t *nb_offsets,
+                        int32_t *nb_idx, int64_t nb_capacity, int64_t *nb_total, int64_t *n_candidates,
+                        double *r_nb) {
+    if (!t || !t->ctx) return PT_ERR_ARG;
+    pt_ctx *ctx = t->ctx;
+    ctx->err[0] = 0;
+    if (!t->built) return fail(ctx, PT_ERR_ARG, "tree is not built");
+    if (!vel || !op) return fail(ctx, PT_ERR_ARG, "vel and params must not be NULL");
+    if (!(op->dt >= 0.0) || !std::isfinite(op->dt) || !(op->C_r >= 0.0) || !std::isfinite(op->C_r) ||
+        !(op->C_v >= 0.0) || !std::isfinite(op->C_v))
+        return fail(ctx, PT_ERR_ARG, "need finite dt, C_r, C_v >= 0");
+    if (op->mode < PT_ORBIT_ROUT || op->mode > PT_ORBIT_CANDIDATES)
+        return fail(ctx, PT_ERR_ARG, "unknown orbit mode %d", op->mode);
+    if (nb_capacity < 0) return fail(ctx, PT_ERR_ARG, "nb_capacity < 0");
+    if (nb_offsets && !nb_idx && nb_capacity > 0) return fail(ctx, PT_ERR_ARG, "nb_idx is NULL");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t n = t->n;
+    const double *dvel = vel;
+    if (!is_device_ptr(vel)) {
+        TRY(ensure(ctx, t->orb_vel, n * 24));
+        CK(cudaMemcpyAsync(t->orb_vel.p, vel, n * 24, cudaMemcpyHostToDevice, st));
+        dvel = t->orb_vel.as<double>();
+    }
+    double *drnb = nullptr;
+    if (r_nb) {
+        if (is_device_ptr(r_nb)) {
+            drnb = r_nb;
+        } else {
+            TRY(ensure(ctx, t->orb_rnb, n * 8));
+            drnb = t->orb_rnb.as<double>();
+        }
+    }
+    TRY(ensure(ctx, t->orb_sv, n * 32));
+    TRY(ensure(ctx, t->orb_ndr, (size_t)t->cap_nodes * 8));
+    TRY(ensure(ctx, t->orb_ndthr, (size_t)t->cap_nodes * 8));
+    TRY(ensure(ctx, t->orb_grthr, n * 8));
+    TRY(ensure(ctx, t->orb_ctr, 16));
+    TRY(ensure(ctx, t->nb_off, (n + 1) * 8));
+    const bool want_nb = nb_offsets != nullptr;
+    TRY(alloc_pairs(t, std::max<unsigned long long>((unsigned long long)nb_capacity, 2ull * n)));
+    Status *dS = t->status.as<Status>();
+    unsigned stack = kWalkStackSmall;
+    unsigned long long ctr[2] = {0, 0};
+    for (int attempt = 0; attempt < 6; attempt++) {
+        CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));
+        CK(cudaMemsetAsync(&dS->npairs, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(t->orb_ctr.p, 0, 16, st));
+        OrbitArgs A{};
+        A.n = t->n;
+        A.perm = t->perm.as<unsigned>();
+        A.sp64 = t->sp64.as<double4>();
+        A.sq = t->sq.as<uint4>();
+        A.ssc = t->ssc.as<double>();
+        A.massdep = t->prm.mass_dependent;
+        A.sets = t->sets.as<SetInfo>();
+        A.nd_a = t->nd_a.as<uint4>();
+        A.nd_b = t->nd_b.as<uint4>();
+        A.nd_r = t->nd_r.as<uint2>();
+        A.gr_r = t->gr_r.as<uint2>();
+        A.gr_a = t->gr_a.as<uint4>();
+        A.gr_b = t->gr_b.as<uint4>();
+        A.vel = dvel;
+        A.dt = op->dt;
+        A.C_r = op->C_r;
+        A.C_v = op->C_v;
+        A.G = t->prm.G;
+        A.mode = op->mode;
+        A.sv = t->orb_sv.as<double4>();
+        A.nd_rnb = t->orb_ndr.as<double>();
+        A.nd_thr = t->orb_ndthr.as<long long>();
+        A.gr_thr = t->orb_grthr.as<long long>();
+        A.rnb_out = drnb;
+        A.pairs = t->pairs.as<uint2>();
+        A.pair_cap = t->cap_pairs;
+        A.ctr = t->orb_ctr.as<unsigned long long>();
+        A.stack_cap = stack;
+        A.cap_nodes = t->cap_nodes;
+        A.st = dS;
+        if (orbit_launch(A, st) < 0) return fail(ctx, PT_ERR_CUDA, "orbit search: kernel attribute refused");
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(ctx->h_status, t->orb_ctr.p, 16, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        memcpy(ctr, ctx->h_status, 16);
+        TRY(read_status(t));
+        if (t->h.flags & kErrStack) {
+            if (stack < kWalkStackLarge) {
+                stack = kWalkStackLarge;
+                continue;
+            }
+            return fail(ctx, PT_ERR_INTERNAL, "orbit search stack overflow (more than %u pending nodes)", stack);
+        }
+        if (want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= (unsigned long long)nb_capacity) {
+            TRY(alloc_pairs(t, t->h.npairs + t->h.npairs / 8));
+            continue;
+        }
+        break;
+    }
+    if (t->h.flags & kErrStack) return fail(ctx, PT_ERR_INTERNAL, "orbit search did not converge");
+    const unsigned long long npairs = t->h.npairs;
+    if (n_candidates) *n_candidates = (int64_t)ctr[1];
+    if (nb_total) *nb_total = (int64_t)npairs;
+    int rc = PT_OK;
+    if (drnb && drnb != r_nb) CK(cudaMemcpyAsync(r_nb, drnb, n * 8, cudaMemcpyDeviceToHost, st));
+    if (want_nb) {
+        if (npairs > (unsigned long long)nb_capacity || npairs > t->cap_pairs) {
+            rc = fail(ctx, PT_ERR_CAPACITY, "orbit neighbour lists need %llu entries, capacity %lld",
+                      npairs, (long long)nb_capacity);
+        } else {
+            nb_launch(nb_args(t), st);
+            CK(cudaGetLastError());
+            cudaMemcpyKind k1 = is_device_ptr(nb_offsets) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            CK(cudaMemcpyAsync(nb_offsets, t->nb_off.p, (n + 1) * 8, k1, st));
+            if (npairs) {
+                cudaMemcpyKind k2 = is_device_ptr(nb_idx) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+                CK(cudaMemcpyAsync(nb_idx, t->nb_idx.p, npairs * 4, k2, st));
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(st));
     return rc;
 }
 

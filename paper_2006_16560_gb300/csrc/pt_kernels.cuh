@@ -110,6 +110,35 @@ struct NbArgs {
     SortTmp sort_tmp;
 };
 
+// Orbit-dependent neighbour search (Sec. 6.3.1, Eq. 24) on a built tree.
+struct OrbitArgs {
+    unsigned n;
+    const unsigned *perm;
+    const double4 *sp64;
+    const uint4 *sq;
+    const double *ssc;
+    int massdep;
+    const SetInfo *sets;
+    const uint4 *nd_a, *nd_b;
+    const uint2 *nd_r;
+    const uint2 *gr_r;
+    const uint4 *gr_a, *gr_b;
+    const double *vel;                   // input order, n x 3 (device)
+    double dt, C_r, C_v, G;
+    int mode;                            // 0 r_out reference, 1 r_nb reference, 2 candidates
+    double4 *sv;                         // sorted (v, r_nb)
+    double *nd_rnb;                      // per node: largest r_nb
+    long long *nd_thr, *gr_thr;          // gap thresholds from r_nb
+    double *rnb_out;                     // optional: r_nb in input order
+    uint2 *pairs;
+    unsigned long long pair_cap;
+    unsigned long long *ctr;             // [0] work counter, [1] candidates
+    unsigned stack_cap;
+    unsigned cap_nodes;
+    Status *st;
+};
+int orbit_launch(const OrbitArgs &A, cudaStream_t st);
+
 // Per-set pointer table of a batch (device resident).
 struct BatchTab {
     const double *pos, *mass;
