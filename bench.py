@@ -279,6 +279,101 @@ def serve_leg(ctx, duration_s):
     return r
 
 
+def _device_ms(fn, k):
+    """Mean device time (ms) of fn() over k calls on the current stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out, res = [], None
+    for _ in range(k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.mean(out), res
+
+
+def orbit_leg(ctx, d, steps):
+    """Orbit-dependent neighbour lists (Sec. 6.3.1, Eq. 24) on the headline
+    workload: the mixed tree of the same 2^20 particles with their Plummer
+    velocities, dt_L = 0.3 r_out / sigma (sigma = 0.41), C_r = 3, C_v = 1.5."""
+    import torch
+    from paper_2006_16560_gb300 import binding as B
+    n = len(d["mass"])
+    r_out, sigma = 0.003, 0.41
+    dt = 0.3 * r_out / sigma
+    pos, mass = torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["mass"]).cuda()
+    vel = torch.from_numpy(d["vel"]).cuda()
+    t = B.Tree(ctx, pos, mass, params(B.PT_MIXED))
+    rnb = torch.empty(n, dtype=torch.float64, device="cuda")
+    cap = 16 * n
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    idx = torch.empty(cap, dtype=torch.int32, device="cuda")
+    op = B.pt_orbit_params(dt, 3.0, 1.5, B.PT_ORBIT_ROUT)
+
+    def call():
+        rc, tot, cand = B.pt_orbit_neighbours(t.h, B._ptr(vel), op, B._ptr(off), B._ptr(idx), cap,
+                                              B._ptr(rnb))
+        ctx.check(rc, "pt_orbit_neighbours")
+        return tot, cand
+    for _ in range(3):
+        call()
+    ms, (tot, cand) = _device_ms(call, max(3, steps))
+    r = (rnb / r_out).cpu().numpy()
+    t.free()
+    return {"workload": f"Plummer N={n} (seed {SEED}) with its velocities; dt_L = 0.3 r_out/0.41, "
+                        "C_r = 3, C_v = 1.5, reference radius r_out,ij",
+            "ms": ms, "candidate_pairs": int(cand), "neighbour_pairs": int(tot),
+            "r_nb_over_r_out": {"p50": float(np.percentile(r, 50)), "p99": float(np.percentile(r, 99))},
+            "particles_per_s": n / (ms * 1e-3)}
+
+
+def tidal_leg(ctx, d, steps, n_bin=65536, order=3):
+    """Tidal tensors (Sec. 6.4.1) of n_bin binaries on the headline workload:
+    measure points (order 3: 8 per binary, plus the centre of mass) appended
+    as zero-mass particles, one long-range step over the augmented set, then
+    the fit.  d_c = 1e-4; binaries at randomly chosen particles."""
+    import torch
+    from paper_2006_16560_gb300 import binding as B
+    n = len(d["mass"])
+    rng = np.random.default_rng(12)
+    cm = torch.from_numpy(d["pos"][rng.choice(n, n_bin, replace=False)]).cuda()
+    dc = torch.full((n_bin,), 1e-4, dtype=torch.float64, device="cuda")
+    P = B.TIDAL_POINTS[order]
+    pts = torch.empty((n_bin, P, 3), dtype=torch.float64, device="cuda")
+    T = torch.empty((n_bin, B.TIDAL_ELEMENTS[order]), dtype=torch.float64, device="cuda")
+    pos0, mass0 = torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["mass"]).cuda()
+    m_aug = torch.cat([mass0, torch.zeros(n_bin * (1 + P), dtype=torch.float64, device="cuda")])
+    na = n + n_bin * (1 + P)
+    acc = torch.empty((na, 3), dtype=torch.float64, device="cuda")
+    pot = torch.empty(na, dtype=torch.float64, device="cuda")
+    holder = [None]
+
+    def step():
+        ctx.check(B.pt_tidal_points(ctx.h, order, n_bin, B._ptr(cm), B._ptr(dc), B._ptr(pts)), "points")
+        meas = torch.cat([cm[:, None, :], pts], dim=1).reshape(-1, 3)
+        p_aug = torch.cat([pos0, meas]).contiguous()
+        if holder[0] is None:
+            holder[0] = B.Tree(ctx, p_aug, m_aug, params(B.PT_MIXED))
+        else:
+            holder[0].rebuild(p_aug, m_aug, params(B.PT_MIXED))
+        _, st, _ = holder[0].force(acc, pot)
+        a_meas = acc[n:].reshape(n_bin, 1 + P, 3)
+        ctx.check(B.pt_tidal_tensor(ctx.h, order, n_bin, B._ptr(a_meas), B._ptr(dc), B._ptr(T)), "fit")
+        return st.as_dict()
+    step()
+    ms, st = _device_ms(step, max(3, steps))
+    fit_ms, _ = _device_ms(lambda: B.pt_tidal_tensor(ctx.h, order, n_bin, B._ptr(acc[n:].reshape(n_bin, 1 + P, 3)),
+                                                     B._ptr(dc), B._ptr(T)), 5)
+    holder[0].free()
+    return {"workload": f"{n_bin} binaries at random particles of the headline set, order {order} "
+                        f"({P} points + centre each, d_c = 1e-4), FP32-mixed step over {na} particles",
+            "ms_per_step": ms, "fit_ms": fit_ms,
+            "interactions_per_step": st["cell_interactions"] + st["pp_interactions"],
+            "tensors_per_s": n_bin / (ms * 1e-3)}
+
+
 def cpu_oracle_sample(pos, mass, nsample, seed=11):
     """Oracle tree on the host cores: full build plus the tree force on
     nsample targets; returns the interactions/s it would sustain on the whole
@@ -340,6 +435,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-cluster batch leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--no-widened", action="store_true",
+                    help="skip the orbit-neighbour and tidal-tensor legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -484,6 +581,9 @@ def main():
         line["batch"] = batch_leg(ctx, max(3, args.steps // 2))
     if not args.no_serve and not args.only_mixed and rank == 0:
         line["serving"] = serve_leg(ctx, args.serve_seconds)
+    if not args.no_widened and not args.only_mixed:
+        line["orbit_neighbours"] = orbit_leg(ctx, d, args.steps)
+        line["tidal"] = tidal_leg(ctx, d, max(3, args.steps // 2))
     if rank == 0 and not args.no_cpu_baseline:
         v, secs, thr, si = cpu_oracle_sample(d["pos"], d["mass"], args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": thr, "kind": "oracle",

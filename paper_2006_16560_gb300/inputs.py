@@ -137,6 +137,30 @@ def _random_rotations(rng: np.random.Generator, n: int) -> np.ndarray:
     return R
 
 
+def _orbit_state(a, e, E, mu, R):
+    """Relative position and velocity of two-body orbits (semi-major axis a,
+    eccentricity e, eccentric anomaly E, mu = G (m1 + m2)), rotated by R."""
+    c, s = np.cos(E), np.sin(E)
+    q = np.sqrt(1.0 - e * e)
+    rel = np.stack([a * (c - e), a * q * s, np.zeros_like(a)], axis=1)
+    w = np.sqrt(mu / a) / (1.0 - e * c)              # mean motion * a / (r / a)
+    vrel = np.stack([-w * s, w * q * c, np.zeros_like(a)], axis=1)
+    return np.einsum("kij,kj->ki", R, rel), np.einsum("kij,kj->ki", R, vrel)
+
+
+def _members(cen, m1, m2, rel, vrel):
+    """Member positions / velocities (2k, 2k+1) about the pair centres."""
+    mt = m1 + m2
+    n = len(m1)
+    pos = np.empty((2 * n, 3))
+    vel = np.empty((2 * n, 3))
+    pos[0::2] = cen["pos"] - (m2 / mt)[:, None] * rel
+    pos[1::2] = cen["pos"] + (m1 / mt)[:, None] * rel
+    vel[0::2] = cen["vel"] - (m2 / mt)[:, None] * vrel
+    vel[1::2] = cen["vel"] + (m1 / mt)[:, None] * vrel
+    return pos, vel
+
+
 def plummer_binaries(n_pairs: int, seed: int, amin_au: float = 0.005,
                      amax_au: float = 50.0) -> dict:
     """Plummer cluster in which every star is in a binary (2*n_pairs stars).
@@ -155,19 +179,14 @@ def plummer_binaries(n_pairs: int, seed: int, amin_au: float = 0.005,
     e = np.sqrt(rng.uniform(0.0, 1.0, n_pairs))        # thermal: f(e) = 2e
     Manom = rng.uniform(0.0, 2.0 * math.pi, n_pairs)
     E = _kepler_E(Manom, e)
-    rel = np.stack([a * (np.cos(E) - e), a * np.sqrt(1 - e * e) * np.sin(E),
-                    np.zeros(n_pairs)], axis=1)
-    rel = np.einsum("kij,kj->ki", _random_rotations(rng, n_pairs), rel)
-    mt = m1 + m2
-    pos = np.empty((2 * n_pairs, 3))
-    pos[0::2] = cen["pos"] - (m2 / mt)[:, None] * rel
-    pos[1::2] = cen["pos"] + (m1 / mt)[:, None] * rel
+    rel, vrel = _orbit_state(a, e, E, m1 + m2, _random_rotations(rng, n_pairs))
+    pos, vel = _members(cen, m1, m2, rel, vrel)
     mass = np.empty(2 * n_pairs)
     mass[0::2] = m1
     mass[1::2] = m2
     pos -= (mass[:, None] * pos).sum(0)
-    vel = np.repeat(cen["vel"], 2, axis=0)
-    return {"pos": np.ascontiguousarray(pos), "vel": vel, "mass": mass,
+    vel -= (mass[:, None] * vel).sum(0)
+    return {"pos": np.ascontiguousarray(pos), "vel": np.ascontiguousarray(vel), "mass": mass,
             "semi_major": a}
 
 
@@ -203,18 +222,14 @@ def kroupa95_binaries(n_pairs: int, seed: int, mmin: float = 0.08, mmax: float =
     e = np.sqrt(rng.uniform(0.0, 1.0, n_pairs))
     Manom = rng.uniform(0.0, 2.0 * math.pi, n_pairs)
     E = _kepler_E(Manom, e)
-    rel = np.stack([a * (np.cos(E) - e), a * np.sqrt(1 - e * e) * np.sin(E),
-                    np.zeros(n_pairs)], axis=1)
-    rel = np.einsum("kij,kj->ki", _random_rotations(rng, n_pairs), rel)
-    mt = m1 + m2
-    pos = np.empty((2 * n_pairs, 3))
-    pos[0::2] = cen["pos"] - (m2 / mt)[:, None] * rel
-    pos[1::2] = cen["pos"] + (m1 / mt)[:, None] * rel
+    rel, vrel = _orbit_state(a, e, E, (m1 + m2) / tot, _random_rotations(rng, n_pairs))
+    pos, vel = _members(cen, m1, m2, rel, vrel)
     mass = np.empty(2 * n_pairs)
     mass[0::2] = m1 / tot
     mass[1::2] = m2 / tot
     pos -= (mass[:, None] * pos).sum(0)
-    return {"pos": np.ascontiguousarray(pos), "vel": np.repeat(cen["vel"], 2, axis=0), "mass": mass,
+    vel -= (mass[:, None] * vel).sum(0)
+    return {"pos": np.ascontiguousarray(pos), "vel": np.ascontiguousarray(vel), "mass": mass,
             "semi_major": a, "log_period_days": lgp, "ecc": e, "m1_msun": m1, "m2_msun": m2}
 
 

@@ -61,3 +61,22 @@ def test_kroupa95_binaries_kepler_and_thermal():
     assert np.all(sep <= 2.0 * d["semi_major"] * (1 + 1e-9))             # within apocentre
     assert d["mass"].sum() == pytest.approx(1.0)
     assert d["m1_msun"].max() <= 40.0
+
+
+def test_binary_members_move_on_their_orbits():
+    """Both binary generators give members the relative velocity of their
+    Kepler orbit: the pair's pericentre is a (1 - e) and the specific energy
+    is -mu / (2a)."""
+    import oracle
+    for gen in (inputs.kroupa95_binaries, inputs.plummer_binaries):
+        d = gen(500, 4)
+        i = np.arange(0, 1000, 2)
+        dx = d["pos"][i + 1] - d["pos"][i]
+        dv = d["vel"][i + 1] - d["vel"][i]
+        mu = d["mass"][i] + d["mass"][i + 1]
+        a = d["semi_major"]
+        eps = 0.5 * (dv * dv).sum(1) - mu / np.linalg.norm(dx, axis=1)
+        np.testing.assert_allclose(eps, -mu / (2 * a), rtol=1e-6)
+        if "ecc" in d:
+            rp = np.array([oracle.pericentre(dx[k], dv[k], mu[k]) for k in range(500)])
+            np.testing.assert_allclose(rp, a * (1 - d["ecc"]), rtol=1e-6)
