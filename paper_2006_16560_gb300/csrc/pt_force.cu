@@ -87,7 +87,7 @@ __device__ __forceinline__ Chg make_chg(const SetInfo &S) {
 // ===========================================================================
 
 struct ChgF {
-    float invw, c0, c2, c35l, w0, w1, w2, w3, tiny, rout2m;
+    float invw, c0, c2, k0, w0, w1, w2, w3, tiny, rout2m;
 };
 
 // Lane layout of one warp for a pass over up to NI * L targets: the warp's
@@ -200,15 +200,29 @@ __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, 
                 const float rinv = rsqrtf(r2c);
                 const float r = MD ? (r2c * rinv) * invs[k] : r2c * rinv;    // r / s_ij
                 const float xs = __saturatef(fmaf(r, C.invw, C.c0));
-                // K(xs) = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4)
+                // 1 - K(xs), K = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4).
+                // With k0 = 35 (1 - Lambda) = 70 r_in / (r_out + r_in):
+                //   K's quartic  = 1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 xs^4 - k0 xs^4,
+                //   1 - K        = xs^4 (k0 + xs (A(xs) - k0 B(xs))),
+                //   A = 56 - 140 xs + 120 xs^2 - 35 xs^3,  B = 4 - 6 xs + 4 xs^2 - xs^3.
+                // Subtracting K from 1 loses all relative accuracy as xs -> 0 (K -> 1),
+                // where a close companion's pull m (1 - K) / r^2 can still dominate the
+                // sum; the second form keeps it there but cancels near xs = 1, so each is
+                // used on its own half.  Only k0 is a per-set constant: the rest are
+                // immediates, which keeps the hot loop's register budget unchanged.
+                const float x2 = xs * xs;
+                const float x4 = x2 * x2;
                 const float t = xs - 1.0f;
                 const float t2 = t * t;
-                const float kq = fmaf(fmaf(fmaf(fmaf(C.c35l, xs, 20.0f), xs, 10.0f), xs, 4.0f), xs, 1.0f);
-                const float omk = fmaf(-t2 * t2, kq, 1.0f);          // 1 - K
+                const float kq = fmaf(-C.k0, x4, fmaf(fmaf(fmaf(fmaf(35.0f, xs, 20.0f), xs, 10.0f), xs, 4.0f), xs, 1.0f));
+                const float hi = fmaf(-t2 * t2, kq, 1.0f);
+                const float pa3 = fmaf(fmaf(fmaf(-35.0f, xs, 120.0f), xs, -140.0f), xs, 56.0f);
+                const float pb3 = fmaf(fmaf(fmaf(-1.0f, xs, 4.0f), xs, -6.0f), xs, 4.0f);
+                const float lo = x4 * fmaf(xs, fmaf(-C.k0, pb3, pa3), C.k0);
+                const float omk = xs < 0.5f ? lo : hi;
                 // 1 - W = min(2r/(r_out+r_in) - Lambda xs^5 (14 - 28 xs + 20 xs^2 - 5 xs^3), 1),
                 // with Lambda folded into the cubic's coefficients
-                const float x2 = xs * xs;
-                const float x5 = x2 * x2 * xs;
+                const float x5 = x4 * xs;
                 const float wp = fmaf(fmaf(fmaf(C.w3, xs, C.w2), xs, C.w1), xs, C.w0);
                 const float omw = fminf(fmaf(-x5, wp, r * C.c2), 1.0f);
                 const float mr = H.w * rinv;
@@ -445,7 +459,7 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         C.invw = (float)C64.invw;
         C.c0 = (float)C64.c0;
         C.c2 = (float)C64.c2;
-        C.c35l = (float)(35.0 * C64.lam);
+        C.k0 = (float)(70.0 * C64.ri / (C64.ro + C64.ri));   // 35 (1 - Lambda), no cancellation
         C.w0 = (float)(14.0 * C64.lam);
         C.w1 = (float)(-28.0 * C64.lam);
         C.w2 = (float)(20.0 * C64.lam);

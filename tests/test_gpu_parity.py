@@ -118,6 +118,32 @@ def test_plummer4096_mixed(ctx, order):
     assert np.array_equal(gmx["nb_idx"], g64["nb_idx"])
 
 
+def test_mixed_companions_across_the_changeover(ctx):
+    """Heavy companions at separations spread over r_in..r_out (x from 0 to
+    1, many just above r_in where K -> 1): the pull m (1 - K)/r^2 must keep
+    its relative accuracy on the mixed path, where subtracting K from 1
+    would not."""
+    n_pairs = 3000
+    d = inputs.plummer(n_pairs, 17)
+    rng = np.random.default_rng(17)
+    p = c1_params(order=2, precision=B.PT_FP64)
+    x = np.concatenate([rng.uniform(0.0, 0.05, n_pairs // 2), rng.uniform(0.0, 1.0, n_pairs - n_pairs // 2)])
+    r = p.r_in + x * (p.r_out - p.r_in)
+    u = rng.normal(size=(n_pairs, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    pos = np.empty((2 * n_pairs, 3))
+    pos[0::2] = d["pos"]
+    pos[1::2] = d["pos"] + r[:, None] * u
+    mass = np.repeat(d["mass"], 2) * 0.5
+    mass[1::2] *= 50.0                              # companions 50x heavier than their partners
+    mass /= mass.sum()
+    g64 = run_gpu(ctx, pos, mass, p)
+    gmx = run_gpu(ctx, pos, mass, c1_params(order=2, precision=B.PT_MIXED))
+    e = rel_err(gmx["acc"], g64["acc"])
+    assert np.percentile(e, 99) <= MIXED_P99
+    assert e.max() <= MIXED_MAX
+
+
 def test_theta0_equals_direct(ctx):
     d = inputs.plummer(1500, 5, masses="kroupa")
     p = c1_params(theta=0.0, order=2)
