@@ -125,7 +125,7 @@ struct pt_tree {
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
     Buf in_scale, scale_buf, set_mean, ssc, nd_thr, gr_thr;   // mass-dependent radii
-    Buf orb_vel, orb_sv, orb_ndr, orb_ndthr, orb_grthr, orb_ctr, orb_rnb;   // orbit-dependent search
+    Buf orb_vel, orb_sv, orb_rnbf, orb_ndr, orb_ndthr, orb_grthr, orb_ctr, orb_rnb;   // orbit-dependent search
     Buf out_acc, out_pot;                                  // staging for host outputs
     // batch state (the context's batch tree only)
     Buf d_tab, d_totals, d_acc, d_pot;
@@ -158,7 +158,7 @@ struct pt_tree {
                       &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
-                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv,
+                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv, &orb_rnbf,
                       &orb_ndr, &orb_ndthr, &orb_grthr, &orb_ctr, &orb_rnb};
         for (Buf *b : all) b->release();
         d_tab.release(); d_totals.release(); d_acc.release(); d_pot.release();
@@ -1173,6 +1173,7 @@ int pt_orbit_neighbours(pt_tree *t, const double *vel, const pt_orbit_params *op
         }
     }
     TRY(ensure(ctx, t->orb_sv, n * 32));
+    TRY(ensure(ctx, t->orb_rnbf, n * 4));
     TRY(ensure(ctx, t->orb_ndr, (size_t)t->cap_nodes * 8));
     TRY(ensure(ctx, t->orb_ndthr, (size_t)t->cap_nodes * 8));
     TRY(ensure(ctx, t->orb_grthr, n * 8));
@@ -1191,6 +1192,8 @@ int pt_orbit_neighbours(pt_tree *t, const double *vel, const pt_orbit_params *op
         A.n = t->n;
         A.perm = t->perm.as<unsigned>();
         A.sp64 = t->sp64.as<double4>();
+        A.spH = t->spH.as<float4>();
+        A.spL = t->spL.as<float4>();
         A.sq = t->sq.as<uint4>();
         A.ssc = t->ssc.as<double>();
         A.massdep = t->prm.mass_dependent;
@@ -1208,6 +1211,7 @@ int pt_orbit_neighbours(pt_tree *t, const double *vel, const pt_orbit_params *op
         A.G = t->prm.G;
         A.mode = op->mode;
         A.sv = t->orb_sv.as<double4>();
+        A.rnbf = t->orb_rnbf.as<float>();
         A.nd_rnb = t->orb_ndr.as<double>();
         A.nd_thr = t->orb_ndthr.as<long long>();
         A.gr_thr = t->orb_grthr.as<long long>();

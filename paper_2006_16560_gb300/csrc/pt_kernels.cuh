@@ -115,6 +115,7 @@ struct OrbitArgs {
     unsigned n;
     const unsigned *perm;
     const double4 *sp64;
+    const float4 *spH, *spL;             // float-float split of the sorted positions
     const uint4 *sq;
     const double *ssc;
     int massdep;
@@ -127,6 +128,7 @@ struct OrbitArgs {
     double dt, C_r, C_v, G;
     int mode;                            // 0 r_out reference, 1 r_nb reference, 2 candidates
     double4 *sv;                         // sorted (v, r_nb)
+    float *rnbf;                         // sorted r_nb as float (prefilter)
     double *nd_rnb;                      // per node: largest r_nb
     long long *nd_thr, *gr_thr;          // gap thresholds from r_nb
     double *rnb_out;                     // optional: r_nb in input order

@@ -39,6 +39,7 @@ __global__ void k_orbit_prep(OrbitArgs A) {
         const double ro = __dmul_rn(A.sets[A.sq[p].w].r_out, A.massdep ? A.ssc[p] : 1.0);
         const double rnb = __dadd_rn(ro, __dmul_rn(A.C_r, __dmul_rn(sp, A.dt)));
         A.sv[p] = make_double4(vx, vy, vz, rnb);
+        A.rnbf[p] = __double2float_rn(rnb);
         if (A.rnb_out) A.rnb_out[i] = rnb;
     }
 }
@@ -78,22 +79,26 @@ __global__ void k_orbit_groups(OrbitArgs A) {
 }
 
 // Kepler pericentre of the relative orbit (eccentricity-vector form; see pt.h).
-__device__ __forceinline__ double pericentre(const double dx[3], const double dv[3], double mu) {
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
-    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(dv[0], dv[0]), __dmul_rn(dv[1], dv[1])), __dmul_rn(dv[2], dv[2]));
+__device__ __forceinline__ double dot3(double ax, double ay, double az, double bx, double by, double bz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by)), __dmul_rn(az, bz));
+}
+__device__ __forceinline__ double pericentre(double dx, double dy, double dz, double vx, double vy,
+                                             double vz, double mu) {
+    const double r2 = dot3(dx, dy, dz, dx, dy, dz);
+    const double v2 = dot3(vx, vy, vz, vx, vy, vz);
     if (v2 == 0.0) return __dsqrt_rn(r2);
-    const double cx = __dsub_rn(__dmul_rn(dx[1], dv[2]), __dmul_rn(dx[2], dv[1]));
-    const double cy = __dsub_rn(__dmul_rn(dx[2], dv[0]), __dmul_rn(dx[0], dv[2]));
-    const double cz = __dsub_rn(__dmul_rn(dx[0], dv[1]), __dmul_rn(dx[1], dv[0]));
-    const double h2 = __dadd_rn(__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)), __dmul_rn(cz, cz));
+    const double cx = __dsub_rn(__dmul_rn(dy, vz), __dmul_rn(dz, vy));
+    const double cy = __dsub_rn(__dmul_rn(dz, vx), __dmul_rn(dx, vz));
+    const double cz = __dsub_rn(__dmul_rn(dx, vy), __dmul_rn(dy, vx));
+    const double h2 = dot3(cx, cy, cz, cx, cy, cz);
     if (mu == 0.0) return __dsqrt_rn(__ddiv_rn(h2, v2));
     const double r = __dsqrt_rn(r2);
     const double a = __dsub_rn(v2, __ddiv_rn(mu, r));
-    const double b = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dv[0]), __dmul_rn(dx[1], dv[1])), __dmul_rn(dx[2], dv[2]));
-    const double ex = __dsub_rn(__dmul_rn(a, dx[0]), __dmul_rn(b, dv[0]));
-    const double ey = __dsub_rn(__dmul_rn(a, dx[1]), __dmul_rn(b, dv[1]));
-    const double ez = __dsub_rn(__dmul_rn(a, dx[2]), __dmul_rn(b, dv[2]));
-    const double e = __ddiv_rn(__dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez))), mu);
+    const double b = dot3(dx, dy, dz, vx, vy, vz);
+    const double ex = __dsub_rn(__dmul_rn(a, dx), __dmul_rn(b, vx));
+    const double ey = __dsub_rn(__dmul_rn(a, dy), __dmul_rn(b, vy));
+    const double ez = __dsub_rn(__dmul_rn(a, dz), __dmul_rn(b, vz));
+    const double e = __ddiv_rn(__dsqrt_rn(dot3(ex, ey, ez, ex, ey, ez)), mu);
     return __ddiv_rn(__ddiv_rn(h2, mu), __dadd_rn(1.0, e));
 }
 
@@ -101,13 +106,13 @@ __device__ __forceinline__ double pericentre(const double dx[3], const double dv
 __device__ __forceinline__ int orbit_pair(const OrbitArgs &A, unsigned pi, unsigned pj) {
     const double4 xi = A.sp64[pi], xj = A.sp64[pj];
     const double4 vi = A.sv[pi], vj = A.sv[pj];
-    const double dx[3] = {__dsub_rn(xj.x, xi.x), __dsub_rn(xj.y, xi.y), __dsub_rn(xj.z, xi.z)};
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
+    const double dx = __dsub_rn(xj.x, xi.x), dy = __dsub_rn(xj.y, xi.y), dz = __dsub_rn(xj.z, xi.z);
+    const double r2 = dot3(dx, dy, dz, dx, dy, dz);
     const double R = fmax(vi.w, vj.w);
     if (!(r2 < __dmul_rn(R, R))) return 0;
     if (A.mode == 2) return 2;
-    const double dv[3] = {__dsub_rn(vj.x, vi.x), __dsub_rn(vj.y, vi.y), __dsub_rn(vj.z, vi.z)};
-    const double rp = pericentre(dx, dv, __dmul_rn(A.G, __dadd_rn(xi.w, xj.w)));
+    const double rp = pericentre(dx, dy, dz, __dsub_rn(vj.x, vi.x), __dsub_rn(vj.y, vi.y),
+                                 __dsub_rn(vj.z, vi.z), __dmul_rn(A.G, __dadd_rn(xi.w, xj.w)));
     double Rs = R;
     if (A.mode == 0) {
         const double s = A.massdep ? fmax(A.ssc[pi], A.ssc[pj]) : 1.0;
@@ -116,10 +121,52 @@ __device__ __forceinline__ int orbit_pair(const OrbitArgs &A, unsigned pi, unsig
     return rp < __dmul_rn(A.C_v, Rs) ? 2 : 1;
 }
 
+constexpr int kOrbChunk = 128;     // opened-leaf particles staged per warp
+
+// Candidate tests of the staged particles against every member of group g:
+// a float32 prefilter on float-float differences with a 2^-10 margin on
+// r_nb^2 (it can only let extra pairs through), then the exact float64 test
+// and the pericentre in orbit_pair.  Candidates are counted, kept pairs
+// appended to the pair buffer.
+__device__ __forceinline__ void orbit_chunk(const OrbitArgs &A, const uint2 gr, int fill,
+                                            const float4 *cH, const float4 *cL, const float *cR,
+                                            const unsigned *cI, unsigned long long &ncand) {
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned t0 = 0; t0 < gr.y; t0 += 32) {
+        const unsigned t = t0 + lane;
+        const bool valid = t < gr.y;
+        const unsigned pi = gr.x + (valid ? t : 0u);
+        const float4 Hi = A.spH[pi], Li = A.spL[pi];
+        const float ri = A.rnbf[pi];
+        for (int e = 0; e < fill; e++) {
+            const float4 Hj = cH[e], Lj = cL[e];
+            const float dx = (Hj.x - Hi.x) + (Lj.x - Li.x);
+            const float dy = (Hj.y - Hi.y) + (Lj.y - Li.y);
+            const float dz = (Hj.z - Hi.z) + (Lj.z - Li.z);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float R = fmaxf(ri, cR[e]);
+            if (valid && r2 < R * R * (1.0f + 1.0f / 1024.0f)) {
+                const unsigned pj = cI[e];
+                if (pj != pi) {
+                    const int state = orbit_pair(A, pi, pj);
+                    ncand += state > 0;
+                    if (state == 2) {
+                        const unsigned long long at = atomicAdd(&A.st->npairs, 1ull);
+                        if (at < A.pair_cap) A.pairs[at] = make_uint2(pi, pj);
+                    }
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kOrbThreads) k_orbit_search(OrbitArgs A) {
     extern __shared__ unsigned ostack[];
     __shared__ unsigned pfx[kOrbWarps][32];
     __shared__ unsigned pbeg[kOrbWarps][32];
+    __shared__ float4 cH[kOrbWarps][kOrbChunk], cL[kOrbWarps][kOrbChunk];
+    __shared__ float cR[kOrbWarps][kOrbChunk];
+    __shared__ unsigned cI[kOrbWarps][kOrbChunk];
     const unsigned w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned ng = A.st->ngroups;
     unsigned *stk = ostack + (size_t)w * A.stack_cap;
@@ -133,6 +180,7 @@ __global__ void __launch_bounds__(kOrbThreads) k_orbit_search(OrbitArgs A) {
         const uint2 gr = A.gr_r[g];
         const long long gthr = A.gr_thr[g];
         unsigned long long ncand = 0;
+        int fill = 0;
         if (lane == 0) stk[0] = gb.w;
         __syncwarp();
         int sp = 1;
@@ -173,42 +221,37 @@ __global__ void __launch_bounds__(kOrbThreads) k_orbit_search(OrbitArgs A) {
                     }
                 }
             }
-            // pairs (group member, particle of an opened leaf)
+            // stage the particles of the opened leaves, testing full chunks
             const unsigned pincl = warp_incl_scan(pcount);
             const unsigned ptot = __shfl_sync(0xffffffffu, pincl, 31);
             if (ptot) {
                 pfx[w][lane] = pincl - pcount;
                 pbeg[w][lane] = pbegin;
                 __syncwarp();
-                const unsigned long long total = (unsigned long long)ptot * gr.y;
-                for (unsigned long long e0 = 0; e0 < total; e0 += 32) {
-                    const unsigned long long e = e0 + lane;
-                    int state = 0;
-                    unsigned pi = 0, pj = 0;
-                    if (e < total) {
-                        const unsigned il = (unsigned)(e / ptot), jl = (unsigned)(e % ptot);
+                for (unsigned done = 0; done < ptot;) {
+                    const unsigned take = min(ptot - done, (unsigned)(kOrbChunk - fill));
+                    for (unsigned e = lane; e < take; e += 32) {
+                        const unsigned q = done + e;
                         int lo = 0, hi = 31;
                         while (lo < hi) {
                             const int mid = (lo + hi + 1) >> 1;
-                            if (pfx[w][mid] <= jl) lo = mid; else hi = mid - 1;
+                            if (pfx[w][mid] <= q) lo = mid; else hi = mid - 1;
                         }
-                        pi = gr.x + il;
-                        pj = pbeg[w][lo] + (jl - pfx[w][lo]);
-                        if (pi != pj) state = orbit_pair(A, pi, pj);
+                        const unsigned pj = pbeg[w][lo] + (q - pfx[w][lo]);
+                        cH[w][fill + e] = A.spH[pj];
+                        cL[w][fill + e] = A.spL[pj];
+                        cR[w][fill + e] = A.rnbf[pj];
+                        cI[w][fill + e] = pj;
                     }
-                    ncand += __popc(__ballot_sync(0xffffffffu, state > 0));
-                    const unsigned kmask = __ballot_sync(0xffffffffu, state == 2);
-                    if (kmask) {
-                        unsigned long long base = 0;
-                        if (lane == 0) base = atomicAdd(&A.st->npairs, (unsigned long long)__popc(kmask));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (state == 2) {
-                            const unsigned long long at = base + __popc(kmask & lanemask_lt());
-                            if (at < A.pair_cap) A.pairs[at] = make_uint2(pi, pj);
-                        }
+                    fill += (int)take;
+                    done += take;
+                    __syncwarp();
+                    if (fill == kOrbChunk) {
+                        orbit_chunk(A, gr, fill, cH[w], cL[w], cR[w], cI[w], ncand);
+                        fill = 0;
+                        __syncwarp();
                     }
                 }
-                __syncwarp();
             }
             // children of opened internal nodes
             const unsigned cincl = warp_incl_scan(nch);
@@ -221,6 +264,9 @@ __global__ void __launch_bounds__(kOrbThreads) k_orbit_search(OrbitArgs A) {
             sp += (int)ctot;
             __syncwarp();
         }
+        if (fill > 0 && !overflow) orbit_chunk(A, gr, fill, cH[w], cL[w], cR[w], cI[w], ncand);
+        __syncwarp();
+        ncand = warp_sum(ncand);
         if (lane == 0) {
             if (overflow) atomicOr(&A.st->flags, kErrStack);
             atomicAdd(&A.ctr[1], ncand);
@@ -237,7 +283,7 @@ int orbit_launch(const OrbitArgs &A, cudaStream_t st) {
     int nk = 1;
     for (int l = kLevels - 1; l >= 0; l--, nk++) k_orbit_nodes<<<152 * 4, 256, 0, st>>>(A, l);
     k_orbit_groups<<<152 * 4, 256, 0, st>>>(A);
-    int per_sm = (int)((200u * 1024u) / (smem + 2048));
+    int per_sm = (int)((200u * 1024u) / (smem + 24u * 1024u));
     per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
     k_orbit_search<<<152 * per_sm, kOrbThreads, smem, st>>>(A);
     return nk + 2;
