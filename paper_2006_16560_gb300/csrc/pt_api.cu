@@ -146,6 +146,10 @@ struct pt_tree {
     // last results
     Status h{};
     unsigned walk_stack = kWalkStackSmall;
+    // list sizes of the last successful walk of this tree: the one-pass walk
+    // sizes its arrays from them (0: no estimate yet, walk in two passes)
+    unsigned long long est_cells = 0, est_pp = 0;
+    unsigned long long chunk_cells = kWalkChunkEntries, chunk_pp = kWalkChunkEntries;
     const double *scale_in = nullptr;          // device radius factors of the current build
     bool built = false, lists_valid = false;
     float ms_build = 0.f;
@@ -396,6 +400,8 @@ WalkArgs walk_args(pt_tree *t) {
     A.pp = t->pp.as<unsigned>();
     A.cap_cells = t->cap_cells;
     A.cap_pp = t->cap_pp;
+    A.chunk_cells = t->chunk_cells;
+    A.chunk_pp = t->chunk_pp;
     A.stack_cap = t->walk_stack;
     A.st = t->status.as<Status>();
     A.scan_tmp = scan_tmp_of(t);
@@ -490,11 +496,69 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
     Status *dS = t->status.as<Status>();
     TRY(ensure(ctx, t->nb_off, ((size_t)t->n + 1) * 8));
     TRY(alloc_pairs(t, std::max<unsigned long long>(nb_cap_hint, 2ull * t->n)));
+    bool onepass = t->est_cells > 0 && t->est_pp > 0;
     for (int attempt = 0; attempt < 6; attempt++) {
         CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));
         CK(cudaMemsetAsync(&dS->max_stack, 0, sizeof(unsigned), st));
         CK(cudaMemsetAsync(&dS->work, 0, sizeof(dS->work), st));
         CK(cudaMemsetAsync(&dS->npairs, 0, 3 * sizeof(unsigned long long), st));   // npairs, pp_full, pp_fast
+        if (onepass) {
+            // chunks of about four groups' lists (about one move of a partial
+            // list per four groups); arrays for the estimate plus a quarter
+            // (the moves leave up to an eighth behind) and per active warp one
+            // and a half chunks left unused at the end
+            const unsigned long long ngr = std::max<unsigned long long>(t->h.ngroups, 1);
+            auto granule = [&](unsigned long long est) {
+                unsigned long long c = 4 * (est / ngr + 1);
+                return std::min<unsigned long long>(std::max<unsigned long long>(c, kWalkChunkEntries),
+                                                    1ull << 22);
+            };
+            t->chunk_cells = granule(t->est_cells);
+            t->chunk_pp = granule(t->est_pp);
+            const unsigned long long warps =
+                std::min<unsigned long long>((unsigned long long)walk_warps(t->walk_stack), ngr);
+            const unsigned long long need_c = t->est_cells + t->est_cells / 4 + warps * t->chunk_cells * 3 / 2;
+            const unsigned long long need_p = t->est_pp + t->est_pp / 4 + warps * t->chunk_pp * 3 / 2;
+            if (need_c > t->cap_cells || !t->cells.p) {
+                t->cap_cells = need_c;
+                TRY(ensure(ctx, t->cells, t->cap_cells * 4));
+            }
+            if (need_p > t->cap_pp || !t->pp.p) {
+                t->cap_pp = need_p;
+                TRY(ensure(ctx, t->pp, t->cap_pp * 4));
+            }
+            CK(cudaMemsetAsync(&dS->cell_total, 0, 2 * sizeof(unsigned long long), st));   // cell, pp totals
+            CK(cudaEventRecord(ctx->ev[2], st));
+            WalkArgs W = walk_args(t);
+            int nk = walk_launch(W, 2, st);
+            CK(cudaEventRecord(ctx->ev[3], st));
+            ForceArgs F = force_args(t, acc, pot, want_nb);
+            nk += force_launch(F, t->prm.precision, st);
+            CK(cudaEventRecord(ctx->ev[4], st));
+            nk += force_reduce_launch(F, st);
+            if (want_nb) nk += nb_launch(nb_args(t), st);
+            t->launches_force = nk;
+            CK(cudaGetLastError());
+            CK(cudaEventRecord(ctx->ev[5], st));
+            TRY(read_status(t));
+            const unsigned f = t->h.flags;
+            if (f & (kErrStack | kErrListCap)) {
+                if ((f & kErrStack) && t->walk_stack < kWalkStackLarge) t->walk_stack = kWalkStackLarge;
+                onepass = false;                         // size the lists exactly
+                continue;
+            }
+            if (want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= nb_cap_hint) {
+                TRY(alloc_pairs(t, t->h.npairs + t->h.npairs / 8));
+                continue;
+            }
+            cudaEventElapsedTime(&ms[0], ctx->ev[2], ctx->ev[3]);
+            cudaEventElapsedTime(&ms[1], ctx->ev[3], ctx->ev[4]);
+            cudaEventElapsedTime(&ms[2], ctx->ev[2], ctx->ev[5]);
+            t->est_cells = t->h.cell_total;
+            t->est_pp = t->h.pp_total;
+            t->lists_valid = true;
+            return PT_OK;
+        }
         CK(cudaEventRecord(ctx->ev[2], st));
         WalkArgs W = walk_args(t);
         int nk = walk_launch(W, 0, st);
@@ -539,6 +603,8 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         cudaEventElapsedTime(&ms[0], ctx->ev[2], ctx->ev[3]);
         cudaEventElapsedTime(&ms[1], ctx->ev[3], ctx->ev[4]);
         cudaEventElapsedTime(&ms[2], ctx->ev[2], ctx->ev[5]);
+        t->est_cells = t->h.cell_total;
+        t->est_pp = t->h.pp_total;
         t->lists_valid = true;
         return PT_OK;
     }
@@ -1366,24 +1432,44 @@ int pt_tree_groups(pt_tree *t, int64_t *g) {
     return PT_OK;
 }
 
-int pt_tree_lists(pt_tree *t, int64_t *cell_off, uint32_t *cells, int64_t *pp_off, uint32_t *pp) {
-    if (!t || !t->lists_valid) return PT_ERR_ARG;
+// Group-order CSR copy of one list kind; the device arrays hold each group's
+// entries contiguously at its offset (in group order after a two-pass walk,
+// in allocation order after a one-pass walk).
+static int lists_csr(pt_tree *t, const Buf &off_b, const Buf &cnt_b, const Buf &arr, int64_t *off_out,
+                     uint32_t *out) {
     pt_ctx *ctx = t->ctx;
     const size_t ng = t->h.ngroups;
-    std::vector<unsigned long long> co(ng), po(ng);
-    CK(cudaMemcpy(co.data(), t->gr_co.p, ng * 8, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(po.data(), t->gr_po.p, ng * 8, cudaMemcpyDeviceToHost));
-    if (cell_off) {
-        for (size_t k = 0; k < ng; k++) cell_off[k] = (int64_t)co[k];
-        cell_off[ng] = (int64_t)t->h.cell_total;
+    std::vector<unsigned long long> off(ng);
+    std::vector<unsigned> cnt(ng);
+    CK(cudaMemcpy(off.data(), off_b.p, ng * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt.data(), cnt_b.p, ng * 4, cudaMemcpyDeviceToHost));
+    unsigned long long extent = 0, total = 0;
+    for (size_t k = 0; k < ng; k++) {
+        extent = std::max(extent, off[k] + cnt[k]);
+        total += cnt[k];
     }
-    if (pp_off) {
-        for (size_t k = 0; k < ng; k++) pp_off[k] = (int64_t)po[k];
-        pp_off[ng] = (int64_t)t->h.pp_total;
+    if (off_out) {
+        int64_t acc = 0;
+        for (size_t k = 0; k < ng; k++) {
+            off_out[k] = acc;
+            acc += cnt[k];
+        }
+        off_out[ng] = acc;
     }
-    if (cells && t->h.cell_total)
-        CK(cudaMemcpy(cells, t->cells.p, t->h.cell_total * 4, cudaMemcpyDeviceToHost));
-    if (pp && t->h.pp_total) CK(cudaMemcpy(pp, t->pp.p, t->h.pp_total * 4, cudaMemcpyDeviceToHost));
+    if (out && total) {
+        std::vector<uint32_t> all(extent);
+        CK(cudaMemcpy(all.data(), arr.p, extent * 4, cudaMemcpyDeviceToHost));
+        size_t at = 0;
+        for (size_t k = 0; k < ng; k++)
+            for (unsigned e = 0; e < cnt[k]; e++) out[at++] = all[off[k] + e];
+    }
+    return PT_OK;
+}
+
+int pt_tree_lists(pt_tree *t, int64_t *cell_off, uint32_t *cells, int64_t *pp_off, uint32_t *pp) {
+    if (!t || !t->lists_valid) return PT_ERR_ARG;
+    TRY(lists_csr(t, t->gr_co, t->gr_nc, t->cells, cell_off, cells));
+    TRY(lists_csr(t, t->gr_po, t->gr_np, t->pp, pp_off, pp));
     return PT_OK;
 }
 

@@ -446,6 +446,9 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
     __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
+    // lists left unusable by the walk (one-pass arrays exhausted, stack
+    // overflow): do nothing, the host re-runs the walk and the force
+    if (A.st->flags & (kErrListCap | kErrStack)) return;
     const unsigned ng = A.st->ngroups;
     for (;;) {
         __syncthreads();
@@ -651,6 +654,9 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
+    // lists left unusable by the walk (one-pass arrays exhausted, stack
+    // overflow): do nothing, the host re-runs the walk and the force
+    if (A.st->flags & (kErrListCap | kErrStack)) return;
     const unsigned ng = A.st->ngroups;
     for (;;) {
         __syncthreads();

@@ -11,6 +11,7 @@ namespace pt {
 constexpr unsigned kWalkStackSmall = 2048;   // per-warp walk stack entries (shared memory)
 constexpr unsigned kWalkStackLarge = 12288;  // retry size after an overflow
 constexpr unsigned kWalkMaxIters = 1u << 24;   // safety cap on walk iterations per group
+constexpr unsigned long long kWalkChunkEntries = 8192;   // one-pass list allocation granule
 
 struct BuildArgs {
     unsigned n;                      // particles (all sets)
@@ -66,6 +67,7 @@ struct WalkArgs {
     unsigned long long *gr_co, *gr_po;   // ngroups + 1
     unsigned *cells, *pp;
     unsigned long long cap_cells, cap_pp;
+    unsigned long long chunk_cells, chunk_pp;   // one-pass allocation granules (entries)
     unsigned stack_cap;                  // stack entries per warp
     Status *st;
     ScanTmp scan_tmp;
@@ -164,7 +166,8 @@ int walk_init();   // once per context: kernel attributes of the walk
 // context's device and returns its stream; ctx_fail records a message.
 cudaStream_t ctx_enter(pt_ctx *ctx);
 int ctx_fail(pt_ctx *ctx, int code, const char *msg);
-int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill
+int walk_warps(unsigned stack_cap);   // warps of a walk launch with this stack size
+int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill, 2 one pass
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st);
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st);
 int nb_launch(const NbArgs &A, cudaStream_t st);

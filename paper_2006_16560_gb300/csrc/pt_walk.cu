@@ -5,9 +5,17 @@
 // stack, tests them in parallel and emits accepted cells, opened leaves'
 // particles and opened internal nodes' children with warp prefix sums.  All
 // tests are exact integer arithmetic on the grid boxes (see pt.h), so the
-// lists are identical to the CPU oracle's.  The walk runs twice: a counting
-// pass sizes every group's lists, an exclusive scan places them, and a
-// filling pass writes them; both passes visit nodes in the same order.
+// lists are identical to the CPU oracle's.  Two ways to place the lists:
+// - two passes: a counting pass sizes every group's lists, an exclusive scan
+//   places them, and a filling pass writes them (both visit nodes in the
+//   same order); used when no size estimate exists, and by batches;
+// - one pass: each warp takes chunks of the list arrays from a bump
+//   allocator and writes a group's lists contiguously into its chunk,
+//   moving the group's entries so far to a fresh, larger chunk when the
+//   current one fills.  Offsets are then in allocation order rather than
+//   group order.  The arrays are sized from the previous walk of the tree;
+//   if they run out, the kernel flags it and the host falls back to two
+//   passes.
 // Warps take groups from an atomic work counter (persistent grid).
 #include "pt_kernels.cuh"
 
@@ -16,7 +24,33 @@ namespace pt {
 constexpr int kWalkWarps = 4;
 constexpr int kWalkThreads = 32 * kWalkWarps;
 
-template <bool FILL, bool MD>
+
+// Makes room for `need` entries of the current group in the one-pass list
+// array: the group's entries so far ([g0, g0 + have)) move to a new chunk of
+// max(chunk, 2 need) entries.  Returns false (and flags) when the array is full.
+__device__ __forceinline__ bool grow_list(unsigned *arr, unsigned long long cap,
+                                          unsigned long long *cursor, unsigned long long &g0,
+                                          unsigned long long &end, unsigned have, unsigned long long need,
+                                          unsigned long long chunk, unsigned *flags) {
+    const unsigned lane = threadIdx.x & 31;
+    unsigned long long size = 2 * need;
+    if (size < chunk) size = chunk;
+    unsigned long long nb = 0;
+    if (lane == 0) nb = atomicAdd(cursor, size);
+    nb = __shfl_sync(0xffffffffu, nb, 0);
+    if (nb + size > cap) {
+        if (lane == 0) atomicOr(flags, kErrListCap);
+        return false;
+    }
+    __syncwarp();
+    for (unsigned e = lane; e < have; e += 32) arr[nb + e] = arr[g0 + e];
+    __syncwarp();
+    g0 = nb;
+    end = nb + size;
+    return true;
+}
+
+template <bool FILL, bool MD, bool ONEPASS>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     extern __shared__ unsigned stack_mem[];      // kWalkWarps x A.stack_cap entries
     __shared__ unsigned pfx[kWalkWarps][32];
@@ -29,6 +63,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     unsigned *stk = stack_mem + (size_t)w * A.stack_cap;
     const int cap = (int)A.stack_cap;
     int max_sp = 0;
+    // one pass: the warp's current chunks [.., c_end) and [.., p_end) and their
+    // first free entries (uniform across the warp)
+    unsigned long long c_free = 0, c_end = 0, p_free = 0, p_end = 0;
+    bool dead = false;          // list array exhausted: keep walking, write nothing
     for (;;) {
         unsigned g = 0;
         if (lane == 0) g = atomicAdd(&A.st->work[FILL ? 1 : 0], 1ull);
@@ -39,7 +77,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
         const int glo[3] = {2 * (int)ga.x, 2 * (int)ga.y, 2 * (int)ga.z};
         const int ghi[3] = {2 * (int)gb.x + 2, 2 * (int)gb.y + 2, 2 * (int)gb.z + 2};
         unsigned long long cbase = 0, pbase = 0;
-        if (FILL) {
+        if (ONEPASS) {
+            cbase = c_free;
+            pbase = p_free;
+        } else if (FILL) {
             cbase = A.gr_co[g];
             pbase = A.gr_po[g];
         }
@@ -99,7 +140,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
             }
             // accepted cells
             const unsigned amask = __ballot_sync(0xffffffffu, accept);
-            if (FILL && accept) {
+            if (ONEPASS && amask && !dead && cbase + nc + __popc(amask) > c_end)
+                dead = !grow_list(A.cells, A.cap_cells, &A.st->work[0], cbase, c_end, nc,
+                                  nc + __popc(amask), A.chunk_cells, &A.st->flags);
+            if (FILL && accept && !dead) {
                 unsigned long long pos = cbase + nc + __popc(amask & lanemask_lt());
                 if (pos < A.cap_cells) A.cells[pos] = v;
                 else atomicOr(&A.st->flags, kErrListCap);
@@ -108,7 +152,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
             // particles of opened leaves
             const unsigned pincl = warp_incl_scan(pcount);
             const unsigned ptot = __shfl_sync(0xffffffffu, pincl, 31);
-            if (FILL && ptot) {
+            if (ONEPASS && ptot && !dead && pbase + np + ptot > p_end)
+                dead = !grow_list(A.pp, A.cap_pp, &A.st->work[3], pbase, p_end, np, np + ptot,
+                                  A.chunk_pp, &A.st->flags);
+            if (FILL && ptot && !dead) {
                 pfx[w][lane] = pincl - pcount;
                 pbeg[w][lane] = pbegin;
                 __syncwarp();
@@ -142,10 +189,20 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
             __syncwarp();
         }
         if (overflow && lane == 0) atomicOr(&A.st->flags, kErrStack);
-        if (!FILL && lane == 0) atomicMax(&A.st->max_stack, (unsigned)max_sp);
-        if (!FILL && lane == 0) {
+        if ((!FILL || ONEPASS) && lane == 0) atomicMax(&A.st->max_stack, (unsigned)max_sp);
+        if ((!FILL || ONEPASS) && lane == 0) {
             A.gr_nc[g] = nc;
             A.gr_np[g] = np;
+        }
+        if (ONEPASS) {
+            if (lane == 0) {
+                A.gr_co[g] = cbase;
+                A.gr_po[g] = pbase;
+                atomicAdd(&A.st->cell_total, (unsigned long long)nc);
+                atomicAdd(&A.st->pp_total, (unsigned long long)np);
+            }
+            c_free = cbase + nc;
+            p_free = pbase + np;
         }
         __syncwarp();
     }
@@ -155,24 +212,38 @@ int walk_init() {
     // the largest stack the walk may use, set once per context (kernel
     // attributes are not stream work and stay out of captured graphs)
     const int smem = (int)((size_t)kWalkWarps * kWalkStackLarge * sizeof(unsigned));
-    if (cudaFuncSetAttribute(k_walk<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_walk<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_walk<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_walk<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_walk<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_walk<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 1;
     return 0;
 }
 
-int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
-    // work counters 0 and 1 are reset by the caller (part of the status block).
-    // The walk is latency bound: as many resident warps as the stack allows.
-    const size_t smem = (size_t)kWalkWarps * A.stack_cap * sizeof(unsigned);
+// The walk is latency bound: as many resident blocks as the stack allows.
+static int walk_blocks(unsigned stack_cap) {
+    const size_t smem = (size_t)kWalkWarps * stack_cap * sizeof(unsigned);
     int per_sm = (int)((200u * 1024u) / (smem + 2048));
     per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
-    const int blocks = 152 * per_sm;
+    return 152 * per_sm;
+}
+
+int walk_warps(unsigned stack_cap) { return walk_blocks(stack_cap) * kWalkWarps; }
+
+int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
+    // work counters are reset by the caller (part of the status block)
+    const size_t smem = (size_t)kWalkWarps * A.stack_cap * sizeof(unsigned);
+    const int blocks = walk_blocks(A.stack_cap);
+    if (phase == 2) {       // one pass (work[0] / work[3] are the list cursors)
+        if (A.massdep) k_walk<true, true, true><<<blocks, kWalkThreads, smem, st>>>(A);
+        else k_walk<true, false, true><<<blocks, kWalkThreads, smem, st>>>(A);
+        return 1;
+    }
     if (phase == 0) {
-        if (A.massdep) k_walk<false, true><<<blocks, kWalkThreads, smem, st>>>(A);
-        else k_walk<false, false><<<blocks, kWalkThreads, smem, st>>>(A);
+        if (A.massdep) k_walk<false, true, false><<<blocks, kWalkThreads, smem, st>>>(A);
+        else k_walk<false, false, false><<<blocks, kWalkThreads, smem, st>>>(A);
         int nk = 1;
         nk += scan_exclusive<unsigned long long>(A.gr_nc, A.gr_co, &A.st->ngroups, &A.st->cell_total,
                                                  nullptr, A.scan_tmp, st);
@@ -180,8 +251,8 @@ int walk_launch(const WalkArgs &A, int phase, cudaStream_t st) {
                                                  nullptr, A.scan_tmp, st);
         return nk;
     }
-    if (A.massdep) k_walk<true, true><<<blocks, kWalkThreads, smem, st>>>(A);
-    else k_walk<true, false><<<blocks, kWalkThreads, smem, st>>>(A);
+    if (A.massdep) k_walk<true, true, false><<<blocks, kWalkThreads, smem, st>>>(A);
+    else k_walk<true, false, false><<<blocks, kWalkThreads, smem, st>>>(A);
     return 1;
 }
 

@@ -234,3 +234,49 @@ def test_errors(ctx):
     T = oracle.Tree(d["pos"], d["mass"], 8, 64)
     a, _, _ = T.force(0.5, 0.02, 0.2, order=0)
     assert rel_err(acc, a).max() <= FP64_TOL
+
+
+@pytest.mark.parametrize("precision", [B.PT_FP64, B.PT_MIXED])
+def test_one_pass_walk_matches_two_pass(ctx, precision):
+    """A tree's first force call walks in two passes (count, scan, fill); later
+    calls walk once into arrays sized from the previous walk.  Same lists in
+    the same order, so bit-identical forces, potentials and neighbours; a
+    rebuild over many more particles exhausts the arrays and falls back."""
+    import torch
+    d = inputs.plummer(20000, 23, masses="kroupa")
+    p = c1_params(order=2, precision=precision)
+    p.r_out, p.r_in = 0.01, 0.001
+    pos, mass = torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["mass"]).cuda()
+    t = B.Tree(ctx, pos, mass, p)
+    outs, lists = [], []
+    for _ in range(3):
+        acc = torch.empty((20000, 3), dtype=torch.float64, device="cuda")
+        pot = torch.empty(20000, dtype=torch.float64, device="cuda")
+        off = torch.empty(20001, dtype=torch.int64, device="cuda")
+        idx = torch.empty(400000, dtype=torch.int32, device="cuda")
+        total, st, _ = t.force(acc, pot, off, idx, 400000)
+        outs.append((acc.cpu().numpy(), pot.cpu().numpy(), off.cpu().numpy(), idx[:total].cpu().numpy(),
+                     st.as_dict()))
+        lists.append(t.lists(st.cell_list_total, st.pp_list_total))
+        t.rebuild(pos, mass, p)
+    for o, l in zip(outs[1:], lists[1:]):
+        for a, b in zip(o[:4], outs[0][:4]):
+            assert np.array_equal(a, b)
+        for a, b in zip(l, lists[0]):
+            assert np.array_equal(a, b)
+        for k in ("cell_interactions", "pp_interactions", "cell_list_total", "pp_list_total", "neighbours"):
+            assert o[4][k] == outs[0][4][k]
+        assert o[4]["launches_force"] < outs[0][4]["launches_force"]   # one pass, no count/scan
+    # stale size estimate: theta = 0 puts every particle in every group's PP
+    # list (8e6 entries against arrays sized for theta = 0.5) -> fall back
+    p0 = c1_params(order=2, precision=precision, theta=0.0)
+    p0.r_out, p0.r_in = 0.01, 0.001
+    t.rebuild(pos, mass, p0)
+    acc = torch.empty((20000, 3), dtype=torch.float64, device="cuda")
+    pot = torch.empty(20000, dtype=torch.float64, device="cuda")
+    _, st, _ = t.force(acc, pot)
+    ref = run_gpu(ctx, d["pos"], d["mass"], p0, neighbours=False)
+    assert st.pp_list_total == ref["stats"]["pp_list_total"]
+    assert st.launches_force == ref["stats"]["launches_force"]      # the two-pass sequence ran
+    assert np.array_equal(acc.cpu().numpy(), ref["acc"])
+    assert np.array_equal(pot.cpu().numpy(), ref["pot"])
