@@ -40,6 +40,10 @@ constexpr int kFThreads = 32 * kFWarps;
 #endif
 constexpr int kJ = PT_FORCE_TILE;   // list entries per warp tile
 constexpr int kUnroll = PT_FORCE_UNROLL;   // unroll of the inner list loops
+#ifndef PT_FORCE_UNROLL_PAIRS
+#define PT_FORCE_UNROLL_PAIRS 2
+#endif
+constexpr int kUnrollPairs = PT_FORCE_UNROLL_PAIRS;   // unroll of the packed cell-pair loop
 constexpr int kIB = 64;       // targets per pass of the float64 kernel (two per lane)
 constexpr int kSlotMax = 96;  // largest pass of the mixed kernel
 #ifndef PT_FORCE_MIN_BLOCKS
@@ -52,6 +56,41 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
     const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
     hi = s;
     lo = __fadd_rn(lo, e);
+}
+
+// Packed float32 pairs: one f32x2 instruction does the same operation on two
+// values (two cells of a tile at once), halving the issue slots the float32
+// arithmetic takes; the FP32 pipe's throughput is the same as for scalars.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(f2x v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x r;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+    f2x r;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+    f2x r;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x r;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 __device__ __forceinline__ double exact_r2(double4 a, double4 b) {
@@ -97,6 +136,57 @@ struct ChgF {
 // broadcast).  The configuration is picked per pass as the smallest slot
 // count NI * L that covers the remaining targets, which keeps most lanes busy
 // for the uneven group sizes a tree produces.
+// Cell tile in pair layout: pair P holds two cells (a, b) as five float4
+// rows (xa, xb, ya, yb), (za, zb, ma, mb), (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz),
+// each 64-bit half a packed (a, b) operand.  Sub-stream s takes pairs
+// s, s + J, ..; npairs is a multiple of J (the tile is padded with massless
+// cells far away).
+template <int NI, int J, int ORDER>
+__device__ __forceinline__ void cells_tile_f2(const ulonglong2 (*sP)[kJ / 2], int s, int npairs,
+                                              const f2x (&OX)[NI], const f2x (&OY)[NI],
+                                              const f2x (&OZ)[NI], f2x (&PA)[NI][4]) {
+    const f2x m25 = pk2(-2.5f, -2.5f), mhalf = pk2(-0.5f, -0.5f), mone = pk2(-1.0f, -1.0f);
+#pragma unroll kUnrollPairs
+    for (int P = s; P < npairs; P += J) {
+        const ulonglong2 xy = sP[0][P], zm = sP[1][P];
+        ulonglong2 qa, qb, qc;
+        if (ORDER == 2) {
+            qa = sP[2][P];
+            qb = sP[3][P];
+            qc = sP[4][P];
+        }
+#pragma unroll
+        for (int k = 0; k < NI; k++) {
+            const f2x dx = sub2(xy.x, OX[k]), dy = sub2(xy.y, OY[k]), dz = sub2(zm.x, OZ[k]);
+            const float2 r2 = up2(fma2(dz, dz, fma2(dy, dy, mul2(dx, dx))));
+            const f2x rinv = pk2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const f2x rinv2 = mul2(rinv, rinv);
+            const f2x mr = mul2(zm.y, rinv);
+            const f2x mr3 = mul2(mr, rinv2);
+            if (ORDER == 2) {
+                // qa = (Qxx, Qyy), qb = (Qzz, Qxy), qc = (Qxz, Qyz)
+                const f2x qx = fma2(qc.x, dz, fma2(qb.y, dy, mul2(qa.x, dx)));
+                const f2x qy = fma2(qc.y, dz, fma2(qa.y, dy, mul2(qb.y, dx)));
+                const f2x qz = fma2(qb.x, dz, fma2(qc.y, dy, mul2(qc.x, dx)));
+                const f2x dqd = fma2(dz, qz, fma2(dy, qy, mul2(dx, qx)));
+                const f2x nrinv5 = mul2(mul2(mul2(rinv2, rinv2), rinv), mone);   // -1/r^5
+                const f2x nt = mul2(dqd, nrinv5);                   // -t, t = (d.Q.d) / r^5
+                // f = mr3 + 2.5 t / r^2;  a += f d - Q d / r^5;  P += mr + t / 2
+                const f2x f = fma2(mul2(nt, m25), rinv2, mr3);
+                PA[k][0] = fma2(qx, nrinv5, fma2(f, dx, PA[k][0]));
+                PA[k][1] = fma2(qy, nrinv5, fma2(f, dy, PA[k][1]));
+                PA[k][2] = fma2(qz, nrinv5, fma2(f, dz, PA[k][2]));
+                PA[k][3] = fma2(nt, mhalf, add2(PA[k][3], mr));
+            } else {
+                PA[k][0] = fma2(mr3, dx, PA[k][0]);
+                PA[k][1] = fma2(mr3, dy, PA[k][1]);
+                PA[k][2] = fma2(mr3, dz, PA[k][2]);
+                PA[k][3] = add2(PA[k][3], mr);
+            }
+        }
+    }
+}
+
 template <int NI, int J, int ORDER>
 __device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB, const float2 *sC,
                                              int s, int cnt, const float (&ox)[NI],
@@ -248,22 +338,26 @@ __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, 
     }
 }
 
+// Per-lane float-float accumulators live in shared memory (touched once per
+// tile), which keeps their 8 NI registers free for the inner loops.
 template <int NI>
-__device__ __forceinline__ void fold(float (&pa)[NI][4], float (&fh)[NI][4], float (&fl)[NI][4]) {
+__device__ __forceinline__ void fold(float (&pa)[NI][4], float2 (*acc)[4][32]) {
+    const unsigned lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NI; k++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            ff_add(fh[k][c], fl[k][c], pa[k][c]);
+            float2 v = acc[k][c][lane];
+            ff_add(v.x, v.y, pa[k][c]);
+            acc[k][c][lane] = v;
             pa[k][c] = 0.0f;
         }
 }
-
 template <int NI, int J, int ORDER, bool NB, bool MD>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                              const ChgF &C, double rout2, double rout, float4 (*sA)[kJ],
-                             float4 (*sB)[kJ], float2 (*sC)[kJ], unsigned (*sI)[kJ],
-                             double (*red)[kSlotMax][4]) {
+                             float4 (*sB)[kJ], ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ],
+                             float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = lane / L, l = lane % L;
@@ -276,44 +370,88 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         valid[k] = idx < gr.y;
         pid[k] = gr.x + (valid[k] ? idx : 0u);
     }
-    float pa[NI][4], fh[NI][4], fl[NI][4];
+    float pa[NI][4];
+    float2 (*acc)[4][32] = sF[w];
 #pragma unroll
     for (int k = 0; k < NI; k++)
 #pragma unroll
-        for (int c = 0; c < 4; c++) pa[k][c] = fh[k][c] = fl[k][c] = 0.0f;
-    // ---- cells: float offsets from the group's first particle
+        for (int c = 0; c < 4; c++) {
+            pa[k][c] = 0.0f;
+            acc[k][c][lane] = make_float2(0.0f, 0.0f);
+        }
+    // ---- cells: float offsets from the group's first particle; the tile is
+    // stored in pair layout and evaluated two cells per f32x2 operation
     {
-        float ox[NI], oy[NI], oz[NI];
+        f2x OX[NI], OY[NI], OZ[NI], PA[NI][4];
 #pragma unroll
         for (int k = 0; k < NI; k++) {
             const float4 H = A.spH[pid[k]], L4 = A.spL[pid[k]];
-            ox[k] = (H.x - Hg.x) + (L4.x - Lg.x);
-            oy[k] = (H.y - Hg.y) + (L4.y - Lg.y);
-            oz[k] = (H.z - Hg.z) + (L4.z - Lg.z);
+            const float ox = (H.x - Hg.x) + (L4.x - Lg.x);
+            const float oy = (H.y - Hg.y) + (L4.y - Lg.y);
+            const float oz = (H.z - Hg.z) + (L4.z - Lg.z);
+            OX[k] = pk2(ox, ox);
+            OY[k] = pk2(oy, oy);
+            OZ[k] = pk2(oz, oz);
+#pragma unroll
+            for (int c = 0; c < 4; c++) PA[k][c] = 0ull;
         }
         const unsigned nc = A.gr_nc[g];
         const unsigned long long co = A.gr_co[g];
+        constexpr int R = 4 * (kJ / 2);                 // floats per row of the pair layout
+        float *rows = reinterpret_cast<float *>(sP[w]);
         for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
             const int cnt = (int)min((unsigned)kJ, nc - t);
+            const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
 #pragma unroll
             for (int h = 0; h < kJ / 32; h++) {
                 const int e = lane + 32 * h;
-                if (e < cnt) {
-                    const unsigned v = A.cells[co + t + e];
-                    const float4 f0 = A.nd_f[4 * v], f1 = A.nd_f[4 * v + 1];
-                    sA[w][e] = make_float4((f0.x - Hg.x) + (f1.x - Lg.x), (f0.y - Hg.y) + (f1.y - Lg.y),
-                                           (f0.z - Hg.z) + (f1.z - Lg.z), f0.w);
-                    if (ORDER == 2) {
-                        const float4 f2 = A.nd_f[4 * v + 2], f3 = A.nd_f[4 * v + 3];
-                        sB[w][e] = make_float4(f1.w, f2.x, f2.y, f2.z);
-                        sC[w][e] = make_float2(f2.w, f3.x);
+                if (e < cnt2) {
+                    // entry e -> pair P = (e / 2J) J + (e mod J), half (e mod 2J) / J
+                    const int m = e / (2 * J), r = e - m * 2 * J;
+                    const int half = r >= J ? 1 : 0;
+                    const int P = m * J + r - half * J;
+                    float x = 1e15f, y = 1e15f, z = 1e15f, ms = 0.0f;   // padding: massless, far away
+                    float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f, q4 = 0.0f, q5 = 0.0f;
+                    if (e < cnt) {
+                        const unsigned v = A.cells[co + t + e];
+                        const float4 f0 = A.nd_f[4 * v], f1 = A.nd_f[4 * v + 1];
+                        x = (f0.x - Hg.x) + (f1.x - Lg.x);
+                        y = (f0.y - Hg.y) + (f1.y - Lg.y);
+                        z = (f0.z - Hg.z) + (f1.z - Lg.z);
+                        ms = f0.w;
+                        if (ORDER == 2) {
+                            const float4 f2 = A.nd_f[4 * v + 2], f3 = A.nd_f[4 * v + 3];
+                            q0 = f1.w; q1 = f2.x; q2 = f2.y; q3 = f2.z; q4 = f2.w; q5 = f3.x;
+                        }
+                    }
+                    float *b = rows + 4 * P + half;
+                    b[0] = x;
+                    b[2] = y;
+                    b[R] = z;
+                    b[R + 2] = ms;
+                    if (ORDER == 2) {        // (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz)
+                        b[2 * R] = q0;
+                        b[2 * R + 2] = q1;
+                        b[3 * R] = q2;
+                        b[3 * R + 2] = q3;
+                        b[4 * R] = q4;
+                        b[4 * R + 2] = q5;
                     }
                 }
             }
             __syncwarp();
-            cells_tile_f<NI, J, ORDER>(sA[w], sB[w], sC[w], s, cnt, ox, oy, oz, pa);
+            cells_tile_f2<NI, J, ORDER>(sP[w], s, cnt2 / 2, OX, OY, OZ, PA);
             __syncwarp();
-            fold<NI>(pa, fh, fl);
+#pragma unroll
+            for (int k = 0; k < NI; k++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float2 v = up2(PA[k][c]);
+                    float2 a = acc[k][c][lane];
+                    ff_add(a.x, a.y, v.x + v.y);
+                    acc[k][c][lane] = a;
+                    PA[k][c] = 0ull;
+                }
         }
     }
     // ---- particle-particle: float-float differences
@@ -357,7 +495,7 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
                 pp_tile_f<NI, J, false, MD>(A, sA[w], sB[w], sI[w], s, cnt, C, hx, hy, hz, lx, ly, lz,
                                             invs_t, pid, valid, nvalid, rout2, rout, pa, n_full, n_fast);
             __syncwarp();
-            fold<NI>(pa, fh, fl);
+            fold<NI>(pa, acc);
         }
         n_full = warp_sum(n_full);
         n_fast = warp_sum(n_fast);
@@ -371,7 +509,8 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
     for (int k = 0; k < NI; k++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            double v = (double)fh[k][c] + (double)fl[k][c];
+            const float2 a = acc[k][c][lane];
+            double v = (double)a.x + (double)a.y;
 #pragma unroll
             for (int o = L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (s == 0) red[w][l + L * k][c] = v;
@@ -426,14 +565,14 @@ __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, d
 template <int ORDER, bool NB, bool MD>
 __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                                const ChgF &C, double rout2, double rout, float4 (*sA)[kJ],
-                               float4 (*sB)[kJ], float2 (*sC)[kJ], unsigned (*sI)[kJ],
-                               double (*red)[kSlotMax][4]) {
+                               float4 (*sB)[kJ], ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ],
+                               float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
-    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 24; }
-    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 32; }
-    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 48; }
-    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red); return 64; }
-    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sC, sI, red);
+    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 24; }
+    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 32; }
+    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 48; }
+    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 64; }
+    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red);
     return 96;
 }
 
@@ -441,7 +580,8 @@ template <int ORDER, bool NB, bool MD>
 __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(ForceArgs A) {
     __shared__ float4 sA[kFWarps][kJ];
     __shared__ float4 sB[kFWarps][kJ];
-    __shared__ float2 sC[kFWarps][kJ];
+    __shared__ ulonglong2 sP[kFWarps][5][kJ / 2];
+    __shared__ float2 sF[kFWarps][3][4][32];
     __shared__ unsigned sI[kFWarps][kJ];
     __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
@@ -472,7 +612,7 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y;) {
             const unsigned slots =
-                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sA, sB, sC, sI, red);
+                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sA, sB, sP, sI, sF, red);
             __syncthreads();
             write_targets(A, gr, i0, slots, C64.c2, red, ep);
             __syncthreads();
