@@ -44,6 +44,10 @@ constexpr int kUnroll = PT_FORCE_UNROLL;   // unroll of the inner list loops
 #define PT_FORCE_UNROLL_PAIRS 2
 #endif
 constexpr int kUnrollPairs = PT_FORCE_UNROLL_PAIRS;   // unroll of the packed cell-pair loop
+#ifndef PT_FORCE_UNROLL_PP
+#define PT_FORCE_UNROLL_PP 1
+#endif
+constexpr int kUnrollPP = PT_FORCE_UNROLL_PP;   // unroll of the packed PP-pair loop
 constexpr int kIB = 64;       // targets per pass of the float64 kernel (two per lane)
 constexpr int kSlotMax = 96;  // largest pass of the mixed kernel
 #ifndef PT_FORCE_MIN_BLOCKS
@@ -187,152 +191,137 @@ __device__ __forceinline__ void cells_tile_f2(const ulonglong2 (*sP)[kJ / 2], in
     }
 }
 
-template <int NI, int J, int ORDER>
-__device__ __forceinline__ void cells_tile_f(const float4 *sA, const float4 *sB, const float2 *sC,
-                                             int s, int cnt, const float (&ox)[NI],
-                                             const float (&oy)[NI], const float (&oz)[NI],
-                                             float (&pa)[NI][4]) {
-#pragma unroll kUnroll
-    for (int j = s; j < cnt; j += J) {
-        const float4 c = sA[j];
-        float4 q;
-        float2 q2;
-        if (ORDER == 2) {
-            q = sB[j];
-            q2 = sC[j];
-        }
-#pragma unroll
-        for (int k = 0; k < NI; k++) {
-            const float dx = c.x - ox[k], dy = c.y - oy[k], dz = c.z - oz[k];
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float rinv = rsqrtf(r2);
-            const float rinv2 = rinv * rinv;
-            const float mr = c.w * rinv;
-            const float mr3 = mr * rinv2;
-            if (ORDER == 2) {
-                // q = (Qxx, Qyy, Qzz, Qxy), q2 = (Qxz, Qyz)
-                const float qx = fmaf(q2.x, dz, fmaf(q.w, dy, q.x * dx));
-                const float qy = fmaf(q2.y, dz, fmaf(q.y, dy, q.w * dx));
-                const float qz = fmaf(q.z, dz, fmaf(q2.y, dy, q2.x * dx));
-                const float dqd = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
-                const float rinv5 = rinv2 * rinv2 * rinv;
-                const float t = dqd * rinv5;
-                const float f = fmaf(2.5f * t, rinv2, mr3);
-                pa[k][0] = fmaf(-qx, rinv5, fmaf(f, dx, pa[k][0]));
-                pa[k][1] = fmaf(-qy, rinv5, fmaf(f, dy, pa[k][1]));
-                pa[k][2] = fmaf(-qz, rinv5, fmaf(f, dz, pa[k][2]));
-                pa[k][3] = fmaf(0.5f, t, pa[k][3] + mr);
-            } else {
-                pa[k][0] = fmaf(mr3, dx, pa[k][0]);
-                pa[k][1] = fmaf(mr3, dy, pa[k][1]);
-                pa[k][2] = fmaf(mr3, dz, pa[k][2]);
-                pa[k][3] += mr;
-            }
-        }
+// Changeover pair (one list entry H, L against target k): the full 1 - K,
+// 1 - W path, and the float64 confirmation of a neighbour candidate.
+template <int NI, bool NB, bool MD>
+__device__ __forceinline__ void pp_changeover_f(const ForceArgs &A, const float4 &H, const float4 &L,
+                                                unsigned pj, bool real, const ChgF &C, int k,
+                                                float hx, float hy, float hz, float lx, float ly, float lz,
+                                                float invs_t, unsigned pid, bool valid, double rout2,
+                                                double rout, float (&pa)[NI][4]) {
+    const float dx = (H.x - hx) + (L.x - lx);
+    const float dy = (H.y - hy) + (L.y - ly);
+    const float dz = (H.z - hz) + (L.z - lz);
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float invs = 1.0f, q2 = r2;
+    if (MD) {       // pair radii s_ij (r_in, r_out); 1/s_ij is the smaller inverse (L.w = 1/s_j)
+        invs = fminf(invs_t, L.w);
+        q2 = r2 * (invs * invs);
     }
+    if (NB && q2 < C.rout2m && valid && real) {
+        double ro2 = rout2;
+        if (MD) {
+            const double ro = __dmul_rn(rout, fmax(A.ssc[pid], A.ssc[pj]));
+            ro2 = __dmul_rn(ro, ro);
+        }
+        if (pj != pid && exact_r2(A.sp64[pid], A.sp64[pj]) < ro2) emit_pair(A, pid, pj);
+    }
+    const float r2c = fmaxf(r2, C.tiny);
+    const float rinv = rsqrtf(r2c);
+    const float r = MD ? (r2c * rinv) * invs : r2c * rinv;    // r / s_ij
+    const float xs = __saturatef(fmaf(r, C.invw, C.c0));
+    // 1 - K(xs), K = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4).
+    // With k0 = 35 (1 - Lambda) = 70 r_in / (r_out + r_in):
+    //   K's quartic  = 1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 xs^4 - k0 xs^4,
+    //   1 - K        = xs^4 (k0 + xs (A(xs) - k0 B(xs))),
+    //   A = 56 - 140 xs + 120 xs^2 - 35 xs^3,  B = 4 - 6 xs + 4 xs^2 - xs^3.
+    // Subtracting K from 1 loses all relative accuracy as xs -> 0 (K -> 1),
+    // where a close companion's pull m (1 - K) / r^2 can still dominate the
+    // sum; the second form keeps it there but cancels near xs = 1, so each is
+    // used on its own half.  Only k0 is a per-set constant: the rest are
+    // immediates, which keeps the register budget unchanged.
+    const float x2 = xs * xs;
+    const float x4 = x2 * x2;
+    const float t = xs - 1.0f;
+    const float t2 = t * t;
+    const float kq = fmaf(-C.k0, x4, fmaf(fmaf(fmaf(fmaf(35.0f, xs, 20.0f), xs, 10.0f), xs, 4.0f), xs, 1.0f));
+    const float hi = fmaf(-t2 * t2, kq, 1.0f);
+    const float pa3 = fmaf(fmaf(fmaf(-35.0f, xs, 120.0f), xs, -140.0f), xs, 56.0f);
+    const float pb3 = fmaf(fmaf(fmaf(-1.0f, xs, 4.0f), xs, -6.0f), xs, 4.0f);
+    const float lo = x4 * fmaf(xs, fmaf(-C.k0, pb3, pa3), C.k0);
+    const float omk = xs < 0.5f ? lo : hi;
+    // 1 - W = min(2r/(r_out+r_in) - Lambda xs^5 (14 - 28 xs + 20 xs^2 - 5 xs^3), 1),
+    // with Lambda folded into the cubic's coefficients
+    const float x5 = x4 * xs;
+    const float wp = fmaf(fmaf(fmaf(C.w3, xs, C.w2), xs, C.w1), xs, C.w0);
+    const float omw = fminf(fmaf(-x5, wp, r * C.c2), 1.0f);
+    const float mr = H.w * rinv;
+    const float fk = (omk * mr) * (rinv * rinv);
+    pa[k][0] = fmaf(fk, dx, pa[k][0]);
+    pa[k][1] = fmaf(fk, dy, pa[k][1]);
+    pa[k][2] = fmaf(fk, dz, pa[k][2]);
+    pa[k][3] = fmaf(omw, mr, pa[k][3]);
 }
 
-// PP tile.  Every lane runs the same number of iterations (the tile is
-// padded to a multiple of J with massless entries far away), so the warp can
-// vote per iteration: when no pair of the iteration lies within r_out (float
-// r^2 below r_out^2 (1 + 2^-10)), K = W = 0 exactly for all of them and the
-// plain Newtonian pair is evaluated; otherwise every lane takes the full
-// changeover path and neighbour candidates are confirmed in float64.
+// PP tile in pair layout: pair P holds list entries (a, b) as four float4
+// rows (Hx, Hy), (Hz, m), (Lx, Ly), (Lz, 1/s) of packed (a, b) halves, and
+// their particle ids in sI[2P], sI[2P + 1].  Every lane runs the same number
+// of iterations (the tile is padded to a multiple of 2J with massless
+// entries far away), so the warp can vote per iteration: when neither entry
+// of any lane lies within r_out (float r^2 below r_out^2 (1 + 2^-10)),
+// K = W = 0 exactly and both plain Newtonian pairs are evaluated with packed
+// f32x2 arithmetic; otherwise every lane takes the full changeover path for
+// both entries, with neighbour candidates confirmed in float64.
 template <int NI, int J, bool NB, bool MD>
-__device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, const float4 *sL,
-                                          const unsigned *sI, int s, int cnt, const ChgF &C,
-                                          const float (&hx)[NI], const float (&hy)[NI],
-                                          const float (&hz)[NI], const float (&lx)[NI],
-                                          const float (&ly)[NI], const float (&lz)[NI],
-                                          const float (&invs_t)[NI], const unsigned (&pid)[NI],
-                                          const bool (&valid)[NI], int nvalid, double rout2,
-                                          double rout, float (&pa)[NI][4], unsigned &n_full,
-                                          unsigned &n_fast) {
-    const int iters = (cnt + J - 1) / J;
-#pragma unroll kUnroll
-    for (int it = 0; it < iters; it++) {
-        const int j = it * J + s;
-        const float4 H = sH[j];
-        const float4 L = sL[j];
-        float dx[NI], dy[NI], dz[NI], r2[NI], q2[NI], invs[NI];
+__device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 (*sQ)[kJ / 2],
+                                           const unsigned *sI, int s, int npairs, int cnt, const ChgF &C,
+                                           const f2x (&HX)[NI], const f2x (&HY)[NI], const f2x (&HZ)[NI],
+                                           const f2x (&LX)[NI], const f2x (&LY)[NI], const f2x (&LZ)[NI],
+                                           const float (&invs_t)[NI], const unsigned (&pid)[NI],
+                                           const bool (&valid)[NI], int nvalid, double rout2, double rout,
+                                           f2x (&PA)[NI][4], float (&pa)[NI][4], unsigned &n_full,
+                                           unsigned &n_fast) {
+#pragma unroll kUnrollPP
+    for (int P = s; P < npairs; P += J) {
+        const ulonglong2 q0 = sQ[0][P], q1 = sQ[1][P], q2 = sQ[2][P], q3 = sQ[3][P];
+        // list positions of the two entries (for the padding test)
+        const int ea = (P / J) * 2 * J + (P % J), eb = ea + J;
+        f2x dx[NI], dy[NI], dz[NI];
+        float2 r2[NI];
         bool near = false;
 #pragma unroll
         for (int k = 0; k < NI; k++) {
-            dx[k] = (H.x - hx[k]) + (L.x - lx[k]);
-            dy[k] = (H.y - hy[k]) + (L.y - ly[k]);
-            dz[k] = (H.z - hz[k]) + (L.z - lz[k]);
-            r2[k] = fmaf(dz[k], dz[k], fmaf(dy[k], dy[k], dx[k] * dx[k]));
-            if (MD) {       // pair radii s_ij (r_in, r_out); 1/s_ij is the smaller inverse (L.w = 1/s_j)
-                invs[k] = fminf(invs_t[k], L.w);
-                q2[k] = r2[k] * (invs[k] * invs[k]);
-            } else {
-                invs[k] = 1.0f;
-                q2[k] = r2[k];
+            dx[k] = add2(sub2(q0.x, HX[k]), sub2(q2.x, LX[k]));
+            dy[k] = add2(sub2(q0.y, HY[k]), sub2(q2.y, LY[k]));
+            dz[k] = add2(sub2(q1.x, HZ[k]), sub2(q3.x, LZ[k]));
+            r2[k] = up2(fma2(dz[k], dz[k], fma2(dy[k], dy[k], mul2(dx[k], dx[k]))));
+            float qa = r2[k].x, qb = r2[k].y;
+            if (MD) {
+                const float2 w = up2(q3.y);
+                const float ia = fminf(invs_t[k], w.x), ib = fminf(invs_t[k], w.y);
+                qa *= ia * ia;
+                qb *= ib * ib;
             }
-            near |= q2[k] < C.rout2m;
+            near |= (qa < C.rout2m) | (qb < C.rout2m);
         }
-        const unsigned real = (j < cnt) ? (unsigned)nvalid : 0u;
+        const unsigned real = (ea < cnt ? (unsigned)nvalid : 0u) + (eb < cnt ? (unsigned)nvalid : 0u);
         if (__any_sync(0xffffffffu, near)) {
             n_full += real;
+            const float2 hxy = up2(q0.x), hyy = up2(q0.y), hzz = up2(q1.x), mm = up2(q1.y);
+            const float2 lxx = up2(q2.x), lyy = up2(q2.y), lzz = up2(q3.x), ww = up2(q3.y);
+            const float4 Ha = make_float4(hxy.x, hyy.x, hzz.x, mm.x), Hb = make_float4(hxy.y, hyy.y, hzz.y, mm.y);
+            const float4 La = make_float4(lxx.x, lyy.x, lzz.x, ww.x), Lb = make_float4(lxx.y, lyy.y, lzz.y, ww.y);
+            const unsigned pa_id = sI[2 * P], pb_id = sI[2 * P + 1];
 #pragma unroll
             for (int k = 0; k < NI; k++) {
-                if (NB && q2[k] < C.rout2m && valid[k] && j < cnt) {
-                    const unsigned pj = sI[j];
-                    double ro2 = rout2;
-                    if (MD) {
-                        const double ro = __dmul_rn(rout, fmax(A.ssc[pid[k]], A.ssc[pj]));
-                        ro2 = __dmul_rn(ro, ro);
-                    }
-                    if (pj != pid[k] && exact_r2(A.sp64[pid[k]], A.sp64[pj]) < ro2)
-                        emit_pair(A, pid[k], pj);
-                }
-                const float r2c = fmaxf(r2[k], C.tiny);
-                const float rinv = rsqrtf(r2c);
-                const float r = MD ? (r2c * rinv) * invs[k] : r2c * rinv;    // r / s_ij
-                const float xs = __saturatef(fmaf(r, C.invw, C.c0));
-                // 1 - K(xs), K = (xs - 1)^4 (1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 Lambda xs^4).
-                // With k0 = 35 (1 - Lambda) = 70 r_in / (r_out + r_in):
-                //   K's quartic  = 1 + 4 xs + 10 xs^2 + 20 xs^3 + 35 xs^4 - k0 xs^4,
-                //   1 - K        = xs^4 (k0 + xs (A(xs) - k0 B(xs))),
-                //   A = 56 - 140 xs + 120 xs^2 - 35 xs^3,  B = 4 - 6 xs + 4 xs^2 - xs^3.
-                // Subtracting K from 1 loses all relative accuracy as xs -> 0 (K -> 1),
-                // where a close companion's pull m (1 - K) / r^2 can still dominate the
-                // sum; the second form keeps it there but cancels near xs = 1, so each is
-                // used on its own half.  Only k0 is a per-set constant: the rest are
-                // immediates, which keeps the hot loop's register budget unchanged.
-                const float x2 = xs * xs;
-                const float x4 = x2 * x2;
-                const float t = xs - 1.0f;
-                const float t2 = t * t;
-                const float kq = fmaf(-C.k0, x4, fmaf(fmaf(fmaf(fmaf(35.0f, xs, 20.0f), xs, 10.0f), xs, 4.0f), xs, 1.0f));
-                const float hi = fmaf(-t2 * t2, kq, 1.0f);
-                const float pa3 = fmaf(fmaf(fmaf(-35.0f, xs, 120.0f), xs, -140.0f), xs, 56.0f);
-                const float pb3 = fmaf(fmaf(fmaf(-1.0f, xs, 4.0f), xs, -6.0f), xs, 4.0f);
-                const float lo = x4 * fmaf(xs, fmaf(-C.k0, pb3, pa3), C.k0);
-                const float omk = xs < 0.5f ? lo : hi;
-                // 1 - W = min(2r/(r_out+r_in) - Lambda xs^5 (14 - 28 xs + 20 xs^2 - 5 xs^3), 1),
-                // with Lambda folded into the cubic's coefficients
-                const float x5 = x4 * xs;
-                const float wp = fmaf(fmaf(fmaf(C.w3, xs, C.w2), xs, C.w1), xs, C.w0);
-                const float omw = fminf(fmaf(-x5, wp, r * C.c2), 1.0f);
-                const float mr = H.w * rinv;
-                const float fk = (omk * mr) * (rinv * rinv);
-                pa[k][0] = fmaf(fk, dx[k], pa[k][0]);
-                pa[k][1] = fmaf(fk, dy[k], pa[k][1]);
-                pa[k][2] = fmaf(fk, dz[k], pa[k][2]);
-                pa[k][3] = fmaf(omw, mr, pa[k][3]);
+                const float2 hx = up2(HX[k]), hy = up2(HY[k]), hz = up2(HZ[k]);
+                const float2 lx = up2(LX[k]), ly = up2(LY[k]), lz = up2(LZ[k]);
+                pp_changeover_f<NI, NB, MD>(A, Ha, La, pa_id, ea < cnt, C, k, hx.x, hy.x, hz.x, lx.x, ly.x,
+                                            lz.x, invs_t[k], pid[k], valid[k], rout2, rout, pa);
+                pp_changeover_f<NI, NB, MD>(A, Hb, Lb, pb_id, eb < cnt, C, k, hx.x, hy.x, hz.x, lx.x, ly.x,
+                                            lz.x, invs_t[k], pid[k], valid[k], rout2, rout, pa);
             }
         } else {
             n_fast += real;
 #pragma unroll
             for (int k = 0; k < NI; k++) {
-                const float rinv = rsqrtf(r2[k]);
-                const float mr = H.w * rinv;
-                const float mr3 = mr * (rinv * rinv);
-                pa[k][0] = fmaf(mr3, dx[k], pa[k][0]);
-                pa[k][1] = fmaf(mr3, dy[k], pa[k][1]);
-                pa[k][2] = fmaf(mr3, dz[k], pa[k][2]);
-                pa[k][3] += mr;
+                const f2x rinv = pk2(rsqrtf(r2[k].x), rsqrtf(r2[k].y));
+                const f2x mr = mul2(q1.y, rinv);
+                const f2x mr3 = mul2(mr, mul2(rinv, rinv));
+                PA[k][0] = fma2(mr3, dx[k], PA[k][0]);
+                PA[k][1] = fma2(mr3, dy[k], PA[k][1]);
+                PA[k][2] = fma2(mr3, dz[k], PA[k][2]);
+                PA[k][3] = add2(PA[k][3], mr);
             }
         }
     }
@@ -340,24 +329,11 @@ __device__ __forceinline__ void pp_tile_f(const ForceArgs &A, const float4 *sH, 
 
 // Per-lane float-float accumulators live in shared memory (touched once per
 // tile), which keeps their 8 NI registers free for the inner loops.
-template <int NI>
-__device__ __forceinline__ void fold(float (&pa)[NI][4], float2 (*acc)[4][32]) {
-    const unsigned lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < NI; k++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            float2 v = acc[k][c][lane];
-            ff_add(v.x, v.y, pa[k][c]);
-            acc[k][c][lane] = v;
-            pa[k][c] = 0.0f;
-        }
-}
+
 template <int NI, int J, int ORDER, bool NB, bool MD>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                             const ChgF &C, double rout2, double rout, float4 (*sA)[kJ],
-                             float4 (*sB)[kJ], ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ],
-                             float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
+                             const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
+                             unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = lane / L, l = lane % L;
@@ -454,15 +430,19 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
                 }
         }
     }
-    // ---- particle-particle: float-float differences
+    // ---- particle-particle: float-float differences, two list entries per
+    // f32x2 operation on the Newtonian path
     {
-        float hx[NI], hy[NI], hz[NI], lx[NI], ly[NI], lz[NI], invs_t[NI];
+        f2x HX[NI], HY[NI], HZ[NI], LX[NI], LY[NI], LZ[NI], PA[NI][4];
+        float invs_t[NI];
 #pragma unroll
         for (int k = 0; k < NI; k++) {
             const float4 H = A.spH[pid[k]], L4 = A.spL[pid[k]];
-            hx[k] = H.x; hy[k] = H.y; hz[k] = H.z;
-            lx[k] = L4.x; ly[k] = L4.y; lz[k] = L4.z;
+            HX[k] = pk2(H.x, H.x); HY[k] = pk2(H.y, H.y); HZ[k] = pk2(H.z, H.z);
+            LX[k] = pk2(L4.x, L4.x); LY[k] = pk2(L4.y, L4.y); LZ[k] = pk2(L4.z, L4.z);
             invs_t[k] = L4.w;                                    // 1 / s_i
+#pragma unroll
+            for (int c = 0; c < 4; c++) PA[k][c] = 0ull;
         }
         int nvalid = 0;
 #pragma unroll
@@ -470,32 +450,57 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         unsigned n_full = 0, n_fast = 0;
         const unsigned np = A.gr_np[g];
         const unsigned long long po = A.gr_po[g];
+        constexpr int R = 4 * (kJ / 2);                 // floats per row of the pair layout
+        float *rows = reinterpret_cast<float *>(sP[w]);
         for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
             const int cnt = (int)min((unsigned)kJ, np - t);
-            const int cntJ = (cnt + J - 1) / J * J;
+            const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
 #pragma unroll
             for (int h = 0; h < kJ / 32; h++) {
                 const int e = lane + 32 * h;
-                if (e < cnt) {
-                    const unsigned p = A.pp[po + t + e];
-                    sA[w][e] = A.spH[p];
-                    sB[w][e] = A.spL[p];
-                    sI[w][e] = p;
-                } else if (e < cntJ) {                    // massless, far away
-                    sA[w][e] = make_float4(1e15f, 1e15f, 1e15f, 0.0f);
-                    sB[w][e] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
-                    sI[w][e] = 0xffffffffu;
+                if (e < cnt2) {
+                    const int m = e / (2 * J), r = e - m * 2 * J;
+                    const int half = r >= J ? 1 : 0;
+                    const int P = m * J + r - half * J;
+                    float4 H = make_float4(1e15f, 1e15f, 1e15f, 0.0f);   // padding: massless, far away
+                    float4 L = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+                    unsigned p = 0xffffffffu;
+                    if (e < cnt) {
+                        p = A.pp[po + t + e];
+                        H = A.spH[p];
+                        L = A.spL[p];
+                    }
+                    float *b = rows + 4 * P + half;
+                    b[0] = H.x;
+                    b[2] = H.y;
+                    b[R] = H.z;
+                    b[R + 2] = H.w;
+                    b[2 * R] = L.x;
+                    b[2 * R + 2] = L.y;
+                    b[3 * R] = L.z;
+                    b[3 * R + 2] = L.w;
+                    sI[w][2 * P + half] = p;
                 }
             }
             __syncwarp();
             if (NB && A.want_nb)
-                pp_tile_f<NI, J, true, MD>(A, sA[w], sB[w], sI[w], s, cnt, C, hx, hy, hz, lx, ly, lz,
-                                           invs_t, pid, valid, nvalid, rout2, rout, pa, n_full, n_fast);
+                pp_tile_f2<NI, J, true, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, HX, HY, HZ, LX, LY, LZ,
+                                            invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
             else
-                pp_tile_f<NI, J, false, MD>(A, sA[w], sB[w], sI[w], s, cnt, C, hx, hy, hz, lx, ly, lz,
-                                            invs_t, pid, valid, nvalid, rout2, rout, pa, n_full, n_fast);
+                pp_tile_f2<NI, J, false, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, HX, HY, HZ, LX, LY, LZ,
+                                             invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
             __syncwarp();
-            fold<NI>(pa, acc);
+#pragma unroll
+            for (int k = 0; k < NI; k++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float2 v = up2(PA[k][c]);
+                    float2 a = acc[k][c][lane];
+                    ff_add(a.x, a.y, (v.x + v.y) + pa[k][c]);
+                    acc[k][c][lane] = a;
+                    PA[k][c] = 0ull;
+                    pa[k][c] = 0.0f;
+                }
         }
         n_full = warp_sum(n_full);
         n_fast = warp_sum(n_fast);
@@ -564,22 +569,19 @@ __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, d
 // runs the matching instantiation.
 template <int ORDER, bool NB, bool MD>
 __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                               const ChgF &C, double rout2, double rout, float4 (*sA)[kJ],
-                               float4 (*sB)[kJ], ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ],
-                               float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
+                               const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
+                               unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
-    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 24; }
-    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 32; }
-    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 48; }
-    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red); return 64; }
-    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sA, sB, sP, sI, sF, red);
+    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 24; }
+    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 32; }
+    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 48; }
+    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 64; }
+    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red);
     return 96;
 }
 
 template <int ORDER, bool NB, bool MD>
 __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(ForceArgs A) {
-    __shared__ float4 sA[kFWarps][kJ];
-    __shared__ float4 sB[kFWarps][kJ];
     __shared__ ulonglong2 sP[kFWarps][5][kJ / 2];
     __shared__ float2 sF[kFWarps][3][4][32];
     __shared__ unsigned sI[kFWarps][kJ];
@@ -612,7 +614,7 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y;) {
             const unsigned slots =
-                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sA, sB, sP, sI, sF, red);
+                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sP, sI, sF, red);
             __syncthreads();
             write_targets(A, gr, i0, slots, C64.c2, red, ep);
             __syncthreads();
