@@ -58,9 +58,9 @@ SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maximum SM clock
 
 # DRAM bytes per launch of the mixed force kernel from one ncu capture of the
-# same kernel build on this workload (profiles/force_mixed_plummer1m.md);
+# same kernel build on this workload (dram__bytes_read.sum + dram__bytes_write.sum);
 # None when the kernel changed after the capture.
-FORCE_MIXED_DRAM_BYTES = None
+FORCE_MIXED_DRAM_BYTES = 1_374_823_000
 
 
 def workload_config(n):
@@ -428,7 +428,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--cpu-sample", type=int, default=262144,
+                    help="oracle targets per CPU sample (about 10 s on 16 host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="skip the FP64, e2e and batch legs (profiling)")
