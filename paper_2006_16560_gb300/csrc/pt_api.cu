@@ -126,6 +126,7 @@ struct pt_tree {
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
     Buf in_scale, scale_buf, set_mean, ssc, nd_thr, gr_thr;   // mass-dependent radii
     Buf orb_vel, orb_sv, orb_rnbf, orb_ndr, orb_ndthr, orb_grthr, orb_ctr, orb_rnb;   // orbit-dependent search
+    Buf walk_spill;                                        // spill areas of the walk stacks
     Buf out_acc, out_pot;                                  // staging for host outputs
     // batch state (the context's batch tree only)
     Buf d_tab, d_totals, d_acc, d_pot;
@@ -146,6 +147,7 @@ struct pt_tree {
     // last results
     Status h{};
     unsigned walk_stack = kWalkStackSmall;
+    unsigned walk_spill_cap = 0;               // spill entries per warp allocated (0: none yet)
     // list sizes of the last successful walk of this tree: the one-pass walk
     // sizes its arrays from them (0: no estimate yet, walk in two passes)
     unsigned long long est_cells = 0, est_pp = 0;
@@ -162,7 +164,7 @@ struct pt_tree {
                       &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
-                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv, &orb_rnbf,
+                      &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv, &orb_rnbf, &walk_spill,
                       &orb_ndr, &orb_ndthr, &orb_grthr, &orb_ctr, &orb_rnb};
         for (Buf *b : all) b->release();
         d_tab.release(); d_totals.release(); d_acc.release(); d_pot.release();
@@ -403,6 +405,8 @@ WalkArgs walk_args(pt_tree *t) {
     A.chunk_cells = t->chunk_cells;
     A.chunk_pp = t->chunk_pp;
     A.stack_cap = t->walk_stack;
+    A.spill = t->walk_spill.as<unsigned>();
+    A.spill_cap = t->walk_spill_cap;
     A.st = t->status.as<Status>();
     A.scan_tmp = scan_tmp_of(t);
     return A;
@@ -487,6 +491,24 @@ int alloc_pairs(pt_tree *t, unsigned long long cap) {
     return PT_OK;
 }
 
+// A walk stack overflowed: first give the warps spill areas in global memory
+// (sized for the launch with the small stack, the widest), then a larger
+// shared stack.
+int on_walk_overflow(pt_tree *t) {
+    pt_ctx *ctx = t->ctx;
+    if (t->walk_spill_cap == 0) {
+        TRY(ensure(ctx, t->walk_spill, (size_t)walk_warps(kWalkStackSmall) * kWalkSpill * 4));
+        t->walk_spill_cap = kWalkSpill;
+        return PT_OK;
+    }
+    if (t->walk_stack < kWalkStackLarge) {
+        t->walk_stack = kWalkStackLarge;
+        return PT_OK;
+    }
+    return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %u pending nodes)",
+                kWalkStackLarge + kWalkSpill);
+}
+
 // Walk + force (+ neighbour CSR) on a built tree; acc/pot are device
 // pointers in input order.  On return t->h holds the status.
 int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long long nb_cap_hint,
@@ -543,7 +565,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
             TRY(read_status(t));
             const unsigned f = t->h.flags;
             if (f & (kErrStack | kErrListCap)) {
-                if ((f & kErrStack) && t->walk_stack < kWalkStackLarge) t->walk_stack = kWalkStackLarge;
+                if (f & kErrStack) TRY(on_walk_overflow(t));
                 onepass = false;                         // size the lists exactly
                 continue;
             }
@@ -565,12 +587,8 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         CK(cudaGetLastError());
         TRY(read_status(t));
         if (t->h.flags & kErrStack) {
-            if (t->walk_stack < kWalkStackLarge) {   // rare: deep or very unbalanced tree
-                t->walk_stack = kWalkStackLarge;
-                continue;
-            }
-            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %u pending nodes)",
-                        kWalkStackLarge);
+            TRY(on_walk_overflow(t));
+            continue;
         }
         if (t->h.cell_total > t->cap_cells || !t->cells.p) {
             t->cap_cells = t->h.cell_total + t->h.cell_total / 8 + 1024;
@@ -593,8 +611,10 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         CK(cudaEventRecord(ctx->ev[5], st));
         TRY(read_status(t));
         const unsigned f = t->h.flags;
-        if (f & kErrStack)
-            return fail(ctx, PT_ERR_INTERNAL, "walk stack overflow (more than %u pending nodes)", t->walk_stack);
+        if (f & kErrStack) {                            // cannot happen after the counting pass
+            TRY(on_walk_overflow(t));
+            continue;
+        }
         if (f & kErrListCap) continue;                  // cannot happen after sizing; retry
         if (want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= nb_cap_hint) {
             TRY(alloc_pairs(t, t->h.npairs + t->h.npairs / 8));
@@ -1248,7 +1268,7 @@ int pt_orbit_neighbours(pt_tree *t, const double *vel, const pt_orbit_params *op
     const bool want_nb = nb_offsets != nullptr;
     TRY(alloc_pairs(t, std::max<unsigned long long>((unsigned long long)nb_capacity, 2ull * n)));
     Status *dS = t->status.as<Status>();
-    unsigned stack = kWalkStackSmall;
+    unsigned stack = kOrbitStack;
     unsigned long long ctr[2] = {0, 0};
     for (int attempt = 0; attempt < 6; attempt++) {
         CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));

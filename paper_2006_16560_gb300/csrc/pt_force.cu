@@ -149,7 +149,7 @@ template <int NI, int J, int ORDER>
 __device__ __forceinline__ void cells_tile_f2(const ulonglong2 (*sP)[kJ / 2], int s, int npairs,
                                               const f2x (&OX)[NI], const f2x (&OY)[NI],
                                               const f2x (&OZ)[NI], f2x (&PA)[NI][4]) {
-    const f2x m25 = pk2(-2.5f, -2.5f), mhalf = pk2(-0.5f, -0.5f), mone = pk2(-1.0f, -1.0f);
+    const f2x m25 = pk2(-2.5f, -2.5f), mhalf = pk2(-0.5f, -0.5f);
 #pragma unroll kUnrollPairs
     for (int P = s; P < npairs; P += J) {
         const ulonglong2 xy = sP[0][P], zm = sP[1][P];
@@ -168,18 +168,17 @@ __device__ __forceinline__ void cells_tile_f2(const ulonglong2 (*sP)[kJ / 2], in
             const f2x mr = mul2(zm.y, rinv);
             const f2x mr3 = mul2(mr, rinv2);
             if (ORDER == 2) {
-                // qa = (Qxx, Qyy), qb = (Qzz, Qxy), qc = (Qxz, Qyz)
-                const f2x qx = fma2(qc.x, dz, fma2(qb.y, dy, mul2(qa.x, dx)));
+                // the tile holds -Q: qa = -(Qxx, Qyy), qb = -(Qzz, Qxy), qc = -(Qxz, Qyz)
+                const f2x qx = fma2(qc.x, dz, fma2(qb.y, dy, mul2(qa.x, dx)));   // (-Q d)_x
                 const f2x qy = fma2(qc.y, dz, fma2(qa.y, dy, mul2(qb.y, dx)));
                 const f2x qz = fma2(qb.x, dz, fma2(qc.y, dy, mul2(qc.x, dx)));
-                const f2x dqd = fma2(dz, qz, fma2(dy, qy, mul2(dx, qx)));
-                const f2x nrinv5 = mul2(mul2(mul2(rinv2, rinv2), rinv), mone);   // -1/r^5
-                const f2x nt = mul2(dqd, nrinv5);                   // -t, t = (d.Q.d) / r^5
+                const f2x rinv5 = mul2(mul2(rinv2, rinv2), rinv);
+                const f2x nt = mul2(fma2(dz, qz, fma2(dy, qy, mul2(dx, qx))), rinv5);   // -t, t = d.Q.d / r^5
                 // f = mr3 + 2.5 t / r^2;  a += f d - Q d / r^5;  P += mr + t / 2
                 const f2x f = fma2(mul2(nt, m25), rinv2, mr3);
-                PA[k][0] = fma2(qx, nrinv5, fma2(f, dx, PA[k][0]));
-                PA[k][1] = fma2(qy, nrinv5, fma2(f, dy, PA[k][1]));
-                PA[k][2] = fma2(qz, nrinv5, fma2(f, dz, PA[k][2]));
+                PA[k][0] = fma2(qx, rinv5, fma2(f, dx, PA[k][0]));
+                PA[k][1] = fma2(qy, rinv5, fma2(f, dy, PA[k][1]));
+                PA[k][2] = fma2(qz, rinv5, fma2(f, dz, PA[k][2]));
                 PA[k][3] = fma2(nt, mhalf, add2(PA[k][3], mr));
             } else {
                 PA[k][0] = fma2(mr3, dx, PA[k][0]);
@@ -397,7 +396,8 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
                         ms = f0.w;
                         if (ORDER == 2) {
                             const float4 f2 = A.nd_f[4 * v + 2], f3 = A.nd_f[4 * v + 3];
-                            q0 = f1.w; q1 = f2.x; q2 = f2.y; q3 = f2.z; q4 = f2.w; q5 = f3.x;
+                            // stored negated: -Q d then feeds the acceleration directly
+                            q0 = -f1.w; q1 = -f2.x; q2 = -f2.y; q3 = -f2.z; q4 = -f2.w; q5 = -f3.x;
                         }
                     }
                     float *b = rows + 4 * P + half;

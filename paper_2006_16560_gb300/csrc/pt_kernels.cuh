@@ -8,8 +8,9 @@ struct pt_ctx;
 
 namespace pt {
 
-constexpr unsigned kWalkStackSmall = 2048;   // per-warp walk stack entries (shared memory)
+constexpr unsigned kWalkStackSmall = 768;    // per-warp walk stack entries (shared memory)
 constexpr unsigned kWalkStackLarge = 12288;  // retry size after an overflow
+constexpr unsigned kOrbitStack = 2048;       // per-warp stack of the orbit-dependent search
 constexpr unsigned kWalkMaxIters = 1u << 24;   // safety cap on walk iterations per group
 constexpr unsigned long long kWalkChunkEntries = 8192;   // one-pass list allocation granule
 
@@ -69,6 +70,8 @@ struct WalkArgs {
     unsigned long long cap_cells, cap_pp;
     unsigned long long chunk_cells, chunk_pp;   // one-pass allocation granules (entries)
     unsigned stack_cap;                  // stack entries per warp
+    unsigned *spill;                     // per-warp spill areas of the stack (global memory)
+    unsigned spill_cap;                  // entries per warp in the spill area
     Status *st;
     ScanTmp scan_tmp;
 };
@@ -167,6 +170,7 @@ int walk_init();   // once per context: kernel attributes of the walk
 cudaStream_t ctx_enter(pt_ctx *ctx);
 int ctx_fail(pt_ctx *ctx, int code, const char *msg);
 int walk_warps(unsigned stack_cap);   // warps of a walk launch with this stack size
+constexpr unsigned kWalkSpill = 4096;    // per-warp spill entries of the walk stack (global memory)
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill, 2 one pass
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st);
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st);

@@ -62,6 +62,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     const unsigned ng = A.st->ngroups;
     unsigned *stk = stack_mem + (size_t)w * A.stack_cap;
     const int cap = (int)A.stack_cap;
+    // the bottom half of a full shared stack moves to the warp's spill area in
+    // global memory and comes back when the shared part runs empty
+    unsigned *gstk = A.spill + (size_t)(blockIdx.x * kWalkWarps + w) * A.spill_cap;
+    const int half = cap / 2;            // >= 32 x 8, the most one step can push
     int max_sp = 0;
     // one pass: the warp's current chunks [.., c_end) and [.., p_end) and their
     // first free entries (uniform across the warp)
@@ -92,10 +96,18 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
         // a walk visits each node at most once; the cap only guards against a
         // corrupted tree turning into an endless loop
         unsigned iters = 0;
-        while (sp > 0) {
+        int gsp = 0;
+        while (sp > 0 || gsp > 0) {
             if (++iters > kWalkMaxIters) {
                 overflow = true;
                 break;
+            }
+            if (sp == 0) {               // refill from the spill area (its newest entries)
+                const int r = gsp < half ? gsp : half;
+                for (int e = lane; e < r; e += 32) stk[e] = gstk[gsp - r + e];
+                gsp -= r;
+                sp = r;
+                __syncwarp();
             }
             const int k = sp < 32 ? sp : 32;
             sp -= k;
@@ -180,8 +192,23 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
             const unsigned cincl = warp_incl_scan(nch);
             const unsigned ctot = __shfl_sync(0xffffffffu, cincl, 31);
             if (sp + (int)ctot > cap) {
-                overflow = true;
-                break;
+                if (gsp + half > (int)A.spill_cap) {
+                    overflow = true;
+                    break;
+                }
+                for (int e = lane; e < half; e += 32) gstk[gsp + e] = stk[e];
+                __syncwarp();
+                // shift the top part down by `half`, 32 entries at a time in
+                // ascending order (each chunk is read before anything overlaps it)
+                for (int e0 = half; e0 < sp; e0 += 32) {
+                    const int e = e0 + (int)lane;
+                    const unsigned x = e < sp ? stk[e] : 0u;
+                    __syncwarp();
+                    if (e < sp) stk[e - half] = x;
+                    __syncwarp();
+                }
+                gsp += half;
+                sp -= half;
             }
             for (unsigned j = 0; j < nch; j++) stk[sp + (cincl - nch) + j] = first + j;
             sp += (int)ctot;
@@ -226,7 +253,7 @@ int walk_init() {
 static int walk_blocks(unsigned stack_cap) {
     const size_t smem = (size_t)kWalkWarps * stack_cap * sizeof(unsigned);
     int per_sm = (int)((200u * 1024u) / (smem + 2048));
-    per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 16 ? 16 : per_sm);   // 16 x 4 warps: the SM's limit
     return 152 * per_sm;
 }
 
