@@ -50,7 +50,7 @@ SEED = 2
 # changeover path ("pp") or, when no pair of the warp's iteration is within
 # r_out, the plain Newtonian pair ("pp_newton"), which is exact there.
 FLOPS = {
-    ("mixed", "cell", 2): 57, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 77,
+    ("mixed", "cell", 2): 56, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 77,
     ("mixed", "pp_newton", None): 28,
     ("fp64", "cell", 2): 56, ("fp64", "cell", 0): 22, ("fp64", "pp", None): 53,
 }
