@@ -204,12 +204,13 @@ __device__ __forceinline__ void level_range(const Status *st, int l, unsigned ca
 }
 
 __global__ void k_topo_roots(const SetInfo *sets, int nsets, uint4 *nd_a, uint4 *nd_b,
-                             uint2 *nd_r, Status *st) {
+                             uint2 *nd_r, unsigned *nd_p, Status *st) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < nsets) {
         nd_r[s] = make_uint2(sets[s].begin, sets[s].n);
         nd_a[s] = make_uint4(0, 0, 0, make_meta(0, 0, 0));
         nd_b[s] = make_uint4(0, 0, 0, 0);
+        nd_p[s] = 0xffffffffu;
     }
     if (s == 0) {
         st->lvl_begin[0] = 0;
@@ -221,12 +222,25 @@ __global__ void k_topo_roots(const SetInfo *sets, int nsets, uint4 *nd_a, uint4 
     }
 }
 
-// Boundaries of the 8 key digits of level l+1 inside [b, b+c).
+// Boundaries of the 8 key digits of level l+1 inside [b, b+c).  The digits
+// are nondecreasing there, so B[k] = b + #{keys with digit < k}: small nodes
+// count them in one independent pass over their keys, large ones bisect.
 __device__ __forceinline__ void child_bounds(const unsigned long long *skey, unsigned b, unsigned c,
                                              int l, unsigned B[9]) {
     const int sh = 3 * (kBits - 1 - l);
     B[0] = b;
     B[8] = b + c;
+    if (c <= 128) {
+        unsigned n_lt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (unsigned p = b; p < b + c; p++) {
+            const unsigned dg = (unsigned)(skey[p] >> sh) & 7u;
+#pragma unroll
+            for (unsigned k = 1; k < 8; k++) n_lt[k] += dg < k ? 1u : 0u;
+        }
+#pragma unroll
+        for (unsigned k = 1; k < 8; k++) B[k] = b + n_lt[k];
+        return;
+    }
     for (unsigned k = 1; k < 8; k++) {
         unsigned lo = B[k - 1], hi = b + c;      // first p >= lo with digit >= k
         while (lo < hi) {
@@ -238,10 +252,11 @@ __device__ __forceinline__ void child_bounds(const unsigned long long *skey, uns
     }
 }
 
-// Number of children of every node of level l (0 for a leaf); writes meta.
+// Number of children of every node of level l (0 for a leaf); writes meta
+// and keeps the child boundaries of split nodes for k_topo_emit.
 __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long long *skey,
                                                    uint4 *nd_a, const uint2 *nd_r, unsigned *nch,
-                                                   int n_leaf, unsigned cap, const Status *st) {
+                                                   uint4 *bnd, int n_leaf, unsigned cap, const Status *st) {
     unsigned b0, cnt;
     level_range(st, l, cap, b0, cnt);
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
@@ -252,6 +267,8 @@ __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long lo
             unsigned B[9];
             child_bounds(skey, r.x, r.y, l, B);
             for (int j = 0; j < 8; j++) nc += (B[j + 1] > B[j]) ? 1u : 0u;
+            bnd[2 * v] = make_uint4(B[0], B[1], B[2], B[3]);
+            bnd[2 * v + 1] = make_uint4(B[4], B[5], B[6], B[7]);
         }
         nch[k] = nc;
         uint4 a = nd_a[v];
@@ -260,8 +277,8 @@ __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long lo
     }
 }
 
-__global__ void __launch_bounds__(kT) k_topo_emit(int l, const unsigned long long *skey,
-                                                  uint4 *nd_a, uint4 *nd_b, uint2 *nd_r,
+__global__ void __launch_bounds__(kT) k_topo_emit(int l, const uint4 *bnd,
+                                                  uint4 *nd_a, uint4 *nd_b, uint2 *nd_r, unsigned *nd_p,
                                                   const unsigned *nch, const unsigned *choff,
                                                   unsigned cap, Status *st) {
     unsigned b0, cnt;
@@ -281,8 +298,8 @@ __global__ void __launch_bounds__(kT) k_topo_emit(int l, const unsigned long lon
         if (nch[k] == 0) continue;
         unsigned v = b0 + k;
         uint2 r = nd_r[v];
-        unsigned B[9];
-        child_bounds(skey, r.x, r.y, l, B);
+        const uint4 b1 = bnd[2 * v], b2 = bnd[2 * v + 1];
+        const unsigned B[9] = {b1.x, b1.y, b1.z, b1.w, b2.x, b2.y, b2.z, b2.w, r.x + r.y};
         unsigned first = next + choff[k], c = first;
         for (int j = 0; j < 8; j++) {
             if (B[j + 1] == B[j]) continue;
@@ -290,6 +307,7 @@ __global__ void __launch_bounds__(kT) k_topo_emit(int l, const unsigned long lon
                 nd_r[c] = make_uint2(B[j], B[j + 1] - B[j]);
                 nd_a[c] = make_uint4(0, 0, 0, make_meta((unsigned)l + 1, 1, 0));
                 nd_b[c] = make_uint4(0, 0, 0, 0);
+                nd_p[c] = v;
             }
             c++;
         }
@@ -320,100 +338,133 @@ __global__ void k_topo_finish(Status *st, unsigned cap) {
 // stored quadrupole is Q = 3T - tr(T) I (twice the traceless A' of Eq. 31).
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kT) k_moments(int l, const double4 *sp64, const uint4 *sq,
-                                                uint4 *nd_a, uint4 *nd_b, const uint2 *nd_r,
-                                                double4 *nd_c, double4 *nd_q, double4 *nd_t,
-                                                float4 *nd_f, const double *ssc, const SetInfo *sets,
-                                                long long *nd_thr, unsigned cap, const Status *st) {
-    unsigned b0, cnt;
-    level_range(st, l, cap, b0, cnt);
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        unsigned v = b0 + k;
-        uint4 a = nd_a[v], bb = nd_b[v];
-        uint2 r = nd_r[v];
-        double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3], smax = 0.0;
-        unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
-        if (meta_leaf(a.w)) {
-            double4 p0 = sp64[r.x];
-            double x0[3] = {p0.x, p0.y, p0.z};
-            double s2[6] = {0, 0, 0, 0, 0, 0};
-            for (unsigned p = r.x; p < r.x + r.y; p++) {
-                double4 P = sp64[p];
-                uint4 q = sq[p];
-                double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
-                M += m;
-                s1[0] += m * d0; s1[1] += m * d1; s1[2] += m * d2;
-                s2[0] += m * d0 * d0; s2[1] += m * d1 * d1; s2[2] += m * d2 * d2;
-                s2[3] += m * d0 * d1; s2[4] += m * d0 * d2; s2[5] += m * d1 * d2;
-                qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
-                qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
-                smax = fmax(smax, ssc[p]);
-            }
-            if (M > 0.0) {
-                double dc[3] = {s1[0] / M, s1[1] / M, s1[2] / M};
-                for (int d = 0; d < 3; d++) com[d] = x0[d] + dc[d];
-                T[0] = s2[0] - M * dc[0] * dc[0];
-                T[1] = s2[1] - M * dc[1] * dc[1];
-                T[2] = s2[2] - M * dc[2] * dc[2];
-                T[3] = s2[3] - M * dc[0] * dc[1];
-                T[4] = s2[4] - M * dc[0] * dc[2];
-                T[5] = s2[5] - M * dc[1] * dc[2];
-            } else {
-                for (int d = 0; d < 3; d++) com[d] = x0[d];
+// Loads through L2 (bypassing L1) of records another thread of the same
+// launch may have written.
+__device__ __forceinline__ double4 ldcg4(const double4 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// Moments of node v: leaves sum their particles about the first particle,
+// internal nodes combine their children with the parallel-axis shift.  The
+// children's records were written by other threads of the same launch, so
+// they are read through L2 (ld.cg).
+__device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, const uint4 *sq, uint4 *nd_a,
+                                             uint4 *nd_b, const uint2 *nd_r, double4 *nd_c, double4 *nd_q,
+                                             double4 *nd_t, float4 *nd_f, const double *ssc,
+                                             const SetInfo *sets, long long *nd_thr, unsigned cap) {
+    uint4 a = nd_a[v], bb = nd_b[v];
+    uint2 r = nd_r[v];
+    double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3], smax = 0.0;
+    unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
+    if (meta_leaf(a.w)) {
+        double4 p0 = sp64[r.x];
+        double x0[3] = {p0.x, p0.y, p0.z};
+        double s2[6] = {0, 0, 0, 0, 0, 0};
+        for (unsigned p = r.x; p < r.x + r.y; p++) {
+            double4 P = sp64[p];
+            uint4 q = sq[p];
+            double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
+            M += m;
+            s1[0] += m * d0; s1[1] += m * d1; s1[2] += m * d2;
+            s2[0] += m * d0 * d0; s2[1] += m * d1 * d1; s2[2] += m * d2 * d2;
+            s2[3] += m * d0 * d1; s2[4] += m * d0 * d2; s2[5] += m * d1 * d2;
+            qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
+            qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
+            smax = fmax(smax, ssc[p]);
+        }
+        if (M > 0.0) {
+            double dc[3] = {s1[0] / M, s1[1] / M, s1[2] / M};
+            for (int d = 0; d < 3; d++) com[d] = x0[d] + dc[d];
+            T[0] = s2[0] - M * dc[0] * dc[0];
+            T[1] = s2[1] - M * dc[1] * dc[1];
+            T[2] = s2[2] - M * dc[2] * dc[2];
+            T[3] = s2[3] - M * dc[0] * dc[1];
+            T[4] = s2[4] - M * dc[0] * dc[2];
+            T[5] = s2[5] - M * dc[1] * dc[2];
+        } else {
+            for (int d = 0; d < 3; d++) com[d] = x0[d];
+        }
+    } else {
+        const unsigned fc = bb.w, nc = meta_nchild(a.w);
+        if (fc >= cap || nc > cap - fc) return;     // truncated build (capacity flag is set)
+        double4 c0 = ldcg4(&nd_c[fc]);
+        double x0[3] = {c0.x, c0.y, c0.z};
+        for (unsigned c = fc; c < fc + nc; c++) {
+            double4 C = ldcg4(&nd_c[c]);
+            M += C.w;
+            s1[0] += C.w * (C.x - x0[0]);
+            s1[1] += C.w * (C.y - x0[1]);
+            s1[2] += C.w * (C.z - x0[2]);
+            uint4 ca = __ldcg(&nd_a[c]), cb = __ldcg(&nd_b[c]);
+            smax = fmax(smax, ldcg4(&nd_t[2 * c + 1]).z);
+            qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
+            qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
+        }
+        if (M > 0.0) {
+            for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] / M;
+            for (unsigned c = fc; c < fc + nc; c++) {
+                double4 C = ldcg4(&nd_c[c]);
+                double4 t0 = ldcg4(&nd_t[2 * c]), t1 = ldcg4(&nd_t[2 * c + 1]);
+                double e0 = C.x - com[0], e1 = C.y - com[1], e2 = C.z - com[2], m = C.w;
+                T[0] += t0.x + m * e0 * e0;
+                T[1] += t0.y + m * e1 * e1;
+                T[2] += t0.z + m * e2 * e2;
+                T[3] += t0.w + m * e0 * e1;
+                T[4] += t1.x + m * e0 * e2;
+                T[5] += t1.y + m * e1 * e2;
             }
         } else {
-            const unsigned fc = bb.w, nc = meta_nchild(a.w);
-            if (fc >= cap || nc > cap - fc) continue;   // truncated build (capacity flag is set)
-            double4 c0 = nd_c[fc];
-            double x0[3] = {c0.x, c0.y, c0.z};
-            for (unsigned c = fc; c < fc + nc; c++) {
-                double4 C = nd_c[c];
-                M += C.w;
-                s1[0] += C.w * (C.x - x0[0]);
-                s1[1] += C.w * (C.y - x0[1]);
-                s1[2] += C.w * (C.z - x0[2]);
-                uint4 ca = nd_a[c], cb = nd_b[c];
-                smax = fmax(smax, nd_t[2 * c + 1].z);
-                qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
-                qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
-            }
-            if (M > 0.0) {
-                for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] / M;
-                for (unsigned c = fc; c < fc + nc; c++) {
-                    double4 C = nd_c[c];
-                    double4 t0 = nd_t[2 * c], t1 = nd_t[2 * c + 1];
-                    double e0 = C.x - com[0], e1 = C.y - com[1], e2 = C.z - com[2], m = C.w;
-                    T[0] += t0.x + m * e0 * e0;
-                    T[1] += t0.y + m * e1 * e1;
-                    T[2] += t0.z + m * e2 * e2;
-                    T[3] += t0.w + m * e0 * e1;
-                    T[4] += t1.x + m * e0 * e2;
-                    T[5] += t1.y + m * e1 * e2;
-                }
-            } else {
-                for (int d = 0; d < 3; d++) com[d] = x0[d];
-            }
+            for (int d = 0; d < 3; d++) com[d] = x0[d];
         }
-        double tr = T[0] + T[1] + T[2];
-        double Q[6] = {3 * T[0] - tr, 3 * T[1] - tr, 3 * T[2] - tr, 3 * T[3], 3 * T[4], 3 * T[5]};
-        nd_c[v] = make_double4(com[0], com[1], com[2], M);
-        nd_q[2 * v] = make_double4(Q[0], Q[1], Q[2], Q[3]);
-        nd_q[2 * v + 1] = make_double4(Q[4], Q[5], 0.0, 0.0);
-        nd_t[2 * v] = make_double4(T[0], T[1], T[2], T[3]);
-        nd_t[2 * v + 1] = make_double4(T[4], T[5], smax, 0.0);
-        if (nd_thr) nd_thr[v] = gap_threshold(sets[sq[r.x].w], smax);
-        a.x = qmn[0]; a.y = qmn[1]; a.z = qmn[2];
-        bb.x = qmx[0]; bb.y = qmx[1]; bb.z = qmx[2];
-        nd_a[v] = a;
-        nd_b[v] = bb;
-        float hx = __double2float_rn(com[0]), hy = __double2float_rn(com[1]), hz = __double2float_rn(com[2]);
-        nd_f[4 * v] = make_float4(hx, hy, hz, __double2float_rn(M));
-        nd_f[4 * v + 1] = make_float4(__double2float_rn(com[0] - (double)hx),
-                                      __double2float_rn(com[1] - (double)hy),
-                                      __double2float_rn(com[2] - (double)hz), __double2float_rn(Q[0]));
-        nd_f[4 * v + 2] = make_float4(__double2float_rn(Q[1]), __double2float_rn(Q[2]),
-                                      __double2float_rn(Q[3]), __double2float_rn(Q[4]));
-        nd_f[4 * v + 3] = make_float4(__double2float_rn(Q[5]), 0.f, 0.f, 0.f);
+    }
+    double tr = T[0] + T[1] + T[2];
+    double Q[6] = {3 * T[0] - tr, 3 * T[1] - tr, 3 * T[2] - tr, 3 * T[3], 3 * T[4], 3 * T[5]};
+    nd_c[v] = make_double4(com[0], com[1], com[2], M);
+    nd_q[2 * v] = make_double4(Q[0], Q[1], Q[2], Q[3]);
+    nd_q[2 * v + 1] = make_double4(Q[4], Q[5], 0.0, 0.0);
+    nd_t[2 * v] = make_double4(T[0], T[1], T[2], T[3]);
+    nd_t[2 * v + 1] = make_double4(T[4], T[5], smax, 0.0);
+    if (nd_thr) nd_thr[v] = gap_threshold(sets[sq[r.x].w], smax);
+    a.x = qmn[0]; a.y = qmn[1]; a.z = qmn[2];
+    bb.x = qmx[0]; bb.y = qmx[1]; bb.z = qmx[2];
+    nd_a[v] = a;
+    nd_b[v] = bb;
+    float hx = __double2float_rn(com[0]), hy = __double2float_rn(com[1]), hz = __double2float_rn(com[2]);
+    nd_f[4 * v] = make_float4(hx, hy, hz, __double2float_rn(M));
+    nd_f[4 * v + 1] = make_float4(__double2float_rn(com[0] - (double)hx),
+                                  __double2float_rn(com[1] - (double)hy),
+                                  __double2float_rn(com[2] - (double)hz), __double2float_rn(Q[0]));
+    nd_f[4 * v + 2] = make_float4(__double2float_rn(Q[1]), __double2float_rn(Q[2]),
+                                  __double2float_rn(Q[3]), __double2float_rn(Q[4]));
+    nd_f[4 * v + 3] = make_float4(__double2float_rn(Q[5]), 0.f, 0.f, 0.f);
+}
+
+// All multipoles in one launch, bottom-up: a thread per leaf computes it,
+// then climbs; at each parent the last child to arrive (atomic counter,
+// after a fence that publishes its own record) computes the parent.  The
+// arithmetic is the same as a level-by-level sweep, so the results are too.
+__global__ void __launch_bounds__(kT) k_moments(const double4 *sp64, const uint4 *sq, uint4 *nd_a,
+                                                uint4 *nd_b, const uint2 *nd_r, const unsigned *nd_p,
+                                                unsigned *arrive, double4 *nd_c, double4 *nd_q,
+                                                double4 *nd_t, float4 *nd_f, const double *ssc,
+                                                const SetInfo *sets, long long *nd_thr, unsigned cap,
+                                                const Status *st) {
+    const unsigned nn = min(st->nnodes, cap);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+        if (!meta_leaf(nd_a[v].w)) continue;
+        unsigned u = v;
+        for (int up = 0; up <= kMaxLevel; up++) {
+            node_moments(u, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr, cap);
+            __threadfence();
+            const unsigned p = nd_p[u];
+            if (p >= cap) break;                                       // a root
+            const unsigned nch = meta_nchild(__ldcg(&nd_a[p]).w);
+            if (atomicAdd(&arrive[p], 1u) + 1u != nch) break;          // not the last child
+            __threadfence();
+            u = p;
+        }
     }
 }
 
@@ -536,26 +587,26 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     k_gather<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, A.mass, n, A.perm, A.qbuf, scale, A.ssc,
                                                    A.sp64, A.spH, A.spL, A.sq);
     // topology
-    k_topo_roots<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.nd_a, A.nd_b, A.nd_r, S);
+    k_topo_roots<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.nd_a, A.nd_b, A.nd_r, A.nd_p, S);
     nk += 2;
     for (int l = 0; l <= kMaxLevel; l++) {
-        k_topo_count<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_r, A.tmp_u32a, A.n_leaf, A.cap_nodes, S);
+        k_topo_count<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_r, A.tmp_u32a, A.nd_bnd, A.n_leaf,
+                                          A.cap_nodes, S);
         nk++;
         if (l == kMaxLevel) break;
         nk += scan_exclusive<unsigned>(A.tmp_u32a, A.tmp_u32b, &S->lvl_count[l], nullptr,
                                        &S->lvl_count[l + 1], A.scan_tmp, st);
-        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_b, A.nd_r, A.tmp_u32a, A.tmp_u32b,
-                                         A.cap_nodes, S);
+        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.nd_bnd, A.nd_a, A.nd_b, A.nd_r, A.nd_p, A.tmp_u32a,
+                                         A.tmp_u32b, A.cap_nodes, S);
         nk++;
     }
     k_topo_finish<<<1, 1, 0, st>>>(S, A.cap_nodes);
     nk++;
-    for (int l = kMaxLevel; l >= 0; l--) {
-        k_moments<<<gmax, kT, 0, st>>>(l, A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q,
-                                       A.nd_t, A.nd_f, A.ssc, A.sets, A.massdep ? A.nd_thr : nullptr,
-                                       A.cap_nodes, S);
-        nk++;
-    }
+    cudaMemsetAsync(A.nd_arrive, 0, (size_t)A.cap_nodes * sizeof(unsigned), st);
+    k_moments<<<gmax, kT, 0, st>>>(A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_p, A.nd_arrive, A.nd_c,
+                                   A.nd_q, A.nd_t, A.nd_f, A.ssc, A.sets, A.massdep ? A.nd_thr : nullptr,
+                                   A.cap_nodes, S);
+    nk++;
     // groups
     cudaMemsetAsync(A.gflag, 0, (size_t)n * sizeof(unsigned), st);
     k_group_mark<<<gmax, kT, 0, st>>>(A.nd_a, A.nd_b, A.nd_r, A.gflag, A.n_group, S);

@@ -36,6 +36,8 @@ struct BuildArgs {
     uint2 *nd_r;
     double4 *nd_c, *nd_q, *nd_t;
     float4 *nd_f;
+    uint4 *nd_bnd;                   // 2 per node: child boundaries of split nodes (build only)
+    unsigned *nd_p, *nd_arrive;      // parent of each node; arrival counters of the moments pass
     unsigned *tmp_u32a, *tmp_u32b;   // max(cap_nodes, n) each
     // groups
     unsigned *gflag, *gbegin;        // n each
