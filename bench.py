@@ -63,6 +63,28 @@ FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maxi
 FORCE_MIXED_DRAM_BYTES = 1_376_413_000
 
 
+def rank_env():
+    """(rank, world size, local rank) from the torchrun environment (1 process: 0, 1, 0)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over all ranks of the initialised process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas (weak scaling): every
+    rank processes the same workload, the job takes as long as its slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def workload_config(n):
     return {
         "workload": f"Plummer N={n}, Kroupa IMF 0.08-150 Msun (total mass 1), Henon units, seed {SEED}; "
@@ -427,7 +449,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--particles", "--n", dest="n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-sample", type=int, default=262144,
                     help="oracle targets per CPU sample (about 10 s on 16 host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -442,9 +464,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     if args.impl == "reference":
         reference_main(args, rank, world)
         return
@@ -489,11 +509,9 @@ def main():
     pot_mx = out[1].cpu().numpy().copy()
     nb_total = int(st["neighbours"])
     ms_step = statistics.mean(times)
-    ms_max = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_max, op=dist.ReduceOp.MAX)
+    ms_max = max_over_ranks(ms_step, device="cuda")
     inter = st["cell_interactions"] + st["pp_interactions"]
-    value = world * inter / (ms_max.item() * 1e-3)
+    value = replica_value(inter, ms_max, world)
     # force kernel alone (CUDA events on the launching stream, inside the library)
     kernel_ms = []
     for _ in range(max(3, min(args.steps, 10))):
@@ -504,10 +522,10 @@ def main():
     achieved = flops_of(st, "mixed") / (k_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max.item(),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed",
         "data": "synthetic", "config": workload_config(n),
-        "particles_per_s": world * n / (ms_max.item() * 1e-3),
+        "particles_per_s": replica_value(n, ms_max, world),
         "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                        "wall_per_step": 1000 * t_wall / args.steps},
         "interactions_per_step": inter, "cell_interactions": st["cell_interactions"],
