@@ -549,6 +549,10 @@ def main():
                                      "(152 SMs x 128 lanes x 2 flop)"}
     if clocks.get("sm_mhz"):
         line["roofline"]["frac_at_measured_clock"] = achieved / (SM_COUNT * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6)
+    rc, probe = B.pt_probe_fp32_peak(ctx.h)
+    if rc == B.PT_OK and probe > 0:
+        line["roofline"]["fp32_fma_probe_tflops"] = probe
+        line["roofline"]["frac_of_probe"] = achieved / (probe * 1e12)
 
     if not args.only_mixed:
         # ---- float64 path on the same workload ----

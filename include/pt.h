@@ -397,6 +397,17 @@ int pt_tidal_tensor(pt_ctx *ctx, int order, int64_t n, const double *acc, const 
 int pt_tidal_eval(pt_ctx *ctx, int order, int64_t n_query, const int64_t *owner, const double *T,
                   int64_t n_binaries, const double *acc_cm, const double *rel, double *acc_out);
 
+/* ---- measurement ---- */
+
+/* Measures the float32 FMA throughput of the context's GPU: independent
+ * fmaf chains, eight per thread, over 8 blocks of 256 threads per SM;
+ * best of three timed launches after a warm-up (CUDA events on the
+ * context's stream), in TFLOP/s (2 flops per FMA) written to *tflops.
+ * About 5 ms of GPU time; allocates and frees 16 bytes.  It is the measured
+ * denominator for the force kernel's fraction of peak; the paper has no
+ * counterpart.  Returns PT_OK, PT_ERR_ARG, PT_ERR_OOM or PT_ERR_CUDA. */
+int pt_probe_fp32_peak(pt_ctx *ctx, double *tflops);
+
 /* ---- allocation-free entry point ---- */
 
 /* Stable ascending sort of n 64-bit keys: keys_sorted[s] is the s-th

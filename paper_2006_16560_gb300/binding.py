@@ -94,6 +94,7 @@ def lib():
                 "pt_tree_lists": (I, [P, P, P, P, P]),
                 "pt_orbit_neighbours": (I, [P, P, C.POINTER(pt_orbit_params), P, P, I64, C.POINTER(I64),
                                             C.POINTER(I64), P]),
+                "pt_probe_fp32_peak": (I, [P, C.POINTER(C.c_double)]),
                 "pt_tidal_points": (I, [P, I, I64, P, P, P]),
                 "pt_tidal_tensor": (I, [P, I, I64, P, P, P]),
                 "pt_tidal_eval": (I, [P, I, I64, P, P, I64, P, P, P]),
@@ -173,6 +174,13 @@ def pt_orbit_neighbours(tree, vel_ptr, op: pt_orbit_params, nb_off_ptr, nb_idx_p
     rc = lib().pt_orbit_neighbours(tree, vel_ptr, C.byref(op), nb_off_ptr, nb_idx_ptr, nb_capacity,
                                    C.byref(tot), C.byref(cand), rnb_ptr)
     return rc, tot.value, cand.value
+
+
+def pt_probe_fp32_peak(ctx):
+    """(status, measured float32 FMA throughput in TFLOP/s)."""
+    v = C.c_double(0.0)
+    rc = lib().pt_probe_fp32_peak(ctx, C.byref(v))
+    return rc, v.value
 
 
 def pt_tidal_points(ctx, order, n, r_cm_ptr, d_c_ptr, points_ptr) -> int:

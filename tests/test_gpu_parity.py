@@ -280,3 +280,12 @@ def test_one_pass_walk_matches_two_pass(ctx, precision):
     assert st.launches_force == ref["stats"]["launches_force"]      # the two-pass sequence ran
     assert np.array_equal(acc.cpu().numpy(), ref["acc"])
     assert np.array_equal(pot.cpu().numpy(), ref["pot"])
+
+
+def test_fp32_probe(ctx):
+    """The measured float32 FMA rate is in the GB300's range (about 80 TFLOP/s
+    at the 2.07 GHz maximum clock: 152 SMs x 128 lanes x 2 flops)."""
+    rc, tf = B.pt_probe_fp32_peak(ctx.h)
+    assert rc == B.PT_OK
+    assert 30.0 < tf < 90.0
+    assert B.pt_probe_fp32_peak(None)[0] == B.PT_ERR_ARG
