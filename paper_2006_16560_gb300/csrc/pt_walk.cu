@@ -53,8 +53,6 @@ __device__ __forceinline__ bool grow_list(unsigned *arr, unsigned long long cap,
 template <bool FILL, bool MD, bool ONEPASS>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     extern __shared__ unsigned stack_mem[];      // kWalkWarps x A.stack_cap entries
-    __shared__ unsigned pfx[kWalkWarps][32];
-    __shared__ unsigned pbeg[kWalkWarps][32];
     __shared__ long long ithr[kLevels];
     if (threadIdx.x < kLevels) ithr[threadIdx.x] = A.wp.ithr[threadIdx.x];
     __syncthreads();
@@ -168,24 +166,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
                 dead = !grow_list(A.pp, A.cap_pp, &A.st->work[3], pbase, p_end, np, np + ptot,
                                   A.chunk_pp, &A.st->flags);
             if (FILL && ptot && !dead) {
-                pfx[w][lane] = pincl - pcount;
-                pbeg[w][lane] = pbegin;
-                __syncwarp();
-                for (unsigned e = lane; e < ptot; e += 32) {
-                    // the owner of entry e is the last lane whose prefix is
-                    // <= e (a lane with no particles shares its prefix with
-                    // the next lane, and no prefix after the last owner is
-                    // <= e, so the search always lands on an owner)
-                    int lo = 0, hi = 31;
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (pfx[w][mid] <= e) lo = mid; else hi = mid - 1;
-                    }
-                    unsigned long long pos = pbase + np + e;
-                    if (pos < A.cap_pp) A.pp[pos] = pbeg[w][lo] + (e - pfx[w][lo]);
-                    else atomicOr(&A.st->flags, kErrListCap);
+                // every lane writes its own leaf's particle range at its offset
+                const unsigned long long at = pbase + np + (pincl - pcount);
+                if (at + pcount <= A.cap_pp) {
+                    for (unsigned e = 0; e < pcount; e++) A.pp[at + e] = pbegin + e;
+                } else if (pcount) {
+                    atomicOr(&A.st->flags, kErrListCap);
                 }
-                __syncwarp();
             }
             np += ptot;
             // children of opened internal nodes
