@@ -4,7 +4,7 @@
 // One CTA (4 warps) evaluates one walk group at a time, taking groups from
 // an atomic work counter.  Every warp holds all of the group's targets (one
 // or two per lane) and streams its own quarter of the group's lists: it
-// gathers 128 list entries into shared memory, then every lane reads them by
+// gathers 64 list entries into shared memory, then every lane reads them by
 // broadcast and accumulates.  The four warps' partial sums are reduced in
 // float64 at the end of the group.
 //
@@ -33,7 +33,7 @@ namespace pt {
 constexpr int kFWarps = 4;
 constexpr int kFThreads = 32 * kFWarps;
 #ifndef PT_FORCE_TILE
-#define PT_FORCE_TILE 128
+#define PT_FORCE_TILE 64
 #endif
 #ifndef PT_FORCE_UNROLL
 #define PT_FORCE_UNROLL 2
