@@ -9,6 +9,7 @@
 namespace pt {
 
 constexpr int kT = 256;
+constexpr unsigned kTopoBig = 4096;   // nodes above this size get a warp in the topology count
 
 // ---------------------------------------------------------------------------
 // Sets (clusters) and the root box
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long lo
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         unsigned v = b0 + k;
         uint2 r = nd_r[v];
+        if (r.y > kTopoBig && (int)r.y > n_leaf && l < kMaxLevel) continue;   // k_topo_count_big's
         unsigned nc = 0;
         if ((int)r.y > n_leaf && l < kMaxLevel) {
             unsigned B[9];
@@ -311,6 +313,52 @@ __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long lo
         uint4 a = nd_a[v];
         a.w = make_meta((unsigned)l, nc == 0 ? 1u : 0u, nc);
         nd_a[v] = a;
+    }
+}
+
+// The same for nodes of more than kTopoBig particles, one warp per node:
+// lanes 1..7 bisect for the seven digit boundaries at once (a thread doing
+// them one after another waits on ~140 dependent loads at the top levels).
+__global__ void __launch_bounds__(kT) k_topo_count_big(int l, const unsigned long long *skey,
+                                                       uint4 *nd_a, const uint2 *nd_r, unsigned *nch,
+                                                       uint4 *bnd, int n_leaf, unsigned cap,
+                                                       const Status *st) {
+    unsigned b0, cnt;
+    level_range(st, l, cap, b0, cnt);
+    if (l >= kMaxLevel) return;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int sh = 3 * (kBits - 1 - l);
+    for (unsigned k = warp; k < cnt; k += nwarps) {
+        const unsigned v = b0 + k;
+        const uint2 r = nd_r[v];
+        if (r.y <= kTopoBig || (int)r.y <= n_leaf) continue;   // uniform across the warp
+        const unsigned e = r.x + r.y;
+        unsigned pos = r.x;                              // lane 0: B[0]
+        if (lane >= 1 && lane < 8) {                     // first p with digit >= lane
+            unsigned lo = r.x, hi = e;
+            while (lo < hi) {
+                const unsigned mid = lo + ((hi - lo) >> 1);
+                const unsigned dg = (unsigned)(skey[mid] >> sh) & 7u;
+                if (dg >= lane) hi = mid; else lo = mid + 1;
+            }
+            pos = lo;
+        }
+        unsigned B[9];
+#pragma unroll
+        for (int j = 0; j < 8; j++) B[j] = __shfl_sync(0xffffffffu, pos, j);
+        B[8] = e;
+        if (lane == 0) {
+            unsigned nc = 0;
+            for (int j = 0; j < 8; j++) nc += (B[j + 1] > B[j]) ? 1u : 0u;
+            bnd[2 * v] = make_uint4(B[0], B[1], B[2], B[3]);
+            bnd[2 * v + 1] = make_uint4(B[4], B[5], B[6], B[7]);
+            nch[k] = nc;
+            uint4 a = nd_a[v];
+            a.w = make_meta((unsigned)l, nc == 0 ? 1u : 0u, nc);
+            nd_a[v] = a;
+        }
     }
 }
 
@@ -631,7 +679,9 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     for (int l = 0; l <= kMaxLevel; l++) {
         k_topo_count<<<gmax, kT, 0, st>>>(l, A.skey, A.lcp, A.nd_a, A.nd_r, A.tmp_u32a, A.nd_bnd,
                                           A.n_leaf, A.cap_nodes, S);
-        nk++;
+        k_topo_count_big<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_r, A.tmp_u32a, A.nd_bnd,
+                                              A.n_leaf, A.cap_nodes, S);
+        nk += 2;
         if (l == kMaxLevel) break;
         nk += scan_exclusive<unsigned>(A.tmp_u32a, A.tmp_u32b, &S->lvl_count[l], nullptr,
                                        &S->lvl_count[l + 1], A.scan_tmp, st);
