@@ -9,7 +9,7 @@
 namespace pt {
 
 constexpr int kT = 256;
-constexpr unsigned kTopoBig = 4096;   // nodes above this size get a warp in the topology count
+constexpr unsigned kTopoBig = 256;    // nodes above this size get a warp in the topology count
 
 // ---------------------------------------------------------------------------
 // Sets (clusters) and the root box
