@@ -573,7 +573,7 @@ __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, u
                                unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
     if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 24; }
-    if (rem <= 32) { group_pass_f<1, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 32; }
+    if (rem <= 32) { group_pass_f<2, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 32; }
     if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 48; }
     if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 64; }
     group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red);
