@@ -252,27 +252,28 @@ __device__ __forceinline__ void pp_changeover_f(const ForceArgs &A, const float4
     pa[k][3] = fmaf(omw, mr, pa[k][3]);
 }
 
-// PP tile in pair layout: pair P holds list entries (a, b) as four float4
-// rows (Hx, Hy), (Hz, m), (Lx, Ly), (Lz, 1/s) of packed (a, b) halves, and
-// their particle ids in sI[2P], sI[2P + 1].  Every lane runs the same number
-// of iterations (the tile is padded to a multiple of 2J with massless
-// entries far away), so the warp can vote per iteration: when neither entry
-// of any lane lies within r_out (float r^2 below r_out^2 (1 + 2^-10)),
-// K = W = 0 exactly and both plain Newtonian pairs are evaluated with packed
-// f32x2 arithmetic; otherwise every lane takes the full changeover path for
-// both entries, with neighbour candidates confirmed in float64.
+// PP tile in pair layout: pair P holds list entries (a, b) as float4 rows
+// (ox, oy), (oz, m) of packed (a, b) halves -- float offsets from the
+// group's first particle, formed from the float-float positions -- plus
+// (1/s, -) for mass-dependent radii, and their particle ids in sI[2P],
+// sI[2P + 1].  Every lane runs the same number of iterations (the tile is
+// padded to a multiple of 2J with massless entries far away), so the warp can
+// vote per iteration: when neither entry of any lane lies within r_out
+// (float r^2 below r_out^2 (1 + 2^-10)), K = W = 0 exactly and both plain
+// Newtonian pairs are evaluated with packed f32x2 arithmetic on the offsets;
+// otherwise every lane takes the full changeover path for both entries on
+// float-float differences, with neighbour candidates confirmed in float64.
 template <int NI, int J, bool NB, bool MD>
 __device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 (*sQ)[kJ / 2],
                                            const unsigned *sI, int s, int npairs, int cnt, const ChgF &C,
-                                           const f2x (&HX)[NI], const f2x (&HY)[NI], const f2x (&HZ)[NI],
-                                           const f2x (&LX)[NI], const f2x (&LY)[NI], const f2x (&LZ)[NI],
+                                           const f2x (&OX)[NI], const f2x (&OY)[NI], const f2x (&OZ)[NI],
                                            const float (&invs_t)[NI], const unsigned (&pid)[NI],
                                            const bool (&valid)[NI], int nvalid, double rout2, double rout,
                                            f2x (&PA)[NI][4], float (&pa)[NI][4], unsigned &n_full,
                                            unsigned &n_fast) {
 #pragma unroll kUnrollPP
     for (int P = s; P < npairs; P += J) {
-        const ulonglong2 q0 = sQ[0][P], q1 = sQ[1][P], q2 = sQ[2][P], q3 = sQ[3][P];
+        const ulonglong2 q0 = sQ[0][P], q1 = sQ[1][P];
         // list positions of the two entries (for the padding test)
         const int ea = (P / J) * 2 * J + (P % J), eb = ea + J;
         f2x dx[NI], dy[NI], dz[NI];
@@ -280,13 +281,13 @@ __device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 
         bool near = false;
 #pragma unroll
         for (int k = 0; k < NI; k++) {
-            dx[k] = add2(sub2(q0.x, HX[k]), sub2(q2.x, LX[k]));
-            dy[k] = add2(sub2(q0.y, HY[k]), sub2(q2.y, LY[k]));
-            dz[k] = add2(sub2(q1.x, HZ[k]), sub2(q3.x, LZ[k]));
+            dx[k] = sub2(q0.x, OX[k]);
+            dy[k] = sub2(q0.y, OY[k]);
+            dz[k] = sub2(q1.x, OZ[k]);
             r2[k] = up2(fma2(dz[k], dz[k], fma2(dy[k], dy[k], mul2(dx[k], dx[k]))));
             float qa = r2[k].x, qb = r2[k].y;
             if (MD) {
-                const float2 w = up2(q3.y);
+                const float2 w = up2(sQ[2][P].x);
                 const float ia = fminf(invs_t[k], w.x), ib = fminf(invs_t[k], w.y);
                 qa *= ia * ia;
                 qb *= ib * ib;
@@ -296,19 +297,17 @@ __device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 
         const unsigned real = (ea < cnt ? (unsigned)nvalid : 0u) + (eb < cnt ? (unsigned)nvalid : 0u);
         if (__any_sync(0xffffffffu, near)) {
             n_full += real;
-            const float2 hxy = up2(q0.x), hyy = up2(q0.y), hzz = up2(q1.x), mm = up2(q1.y);
-            const float2 lxx = up2(q2.x), lyy = up2(q2.y), lzz = up2(q3.x), ww = up2(q3.y);
-            const float4 Ha = make_float4(hxy.x, hyy.x, hzz.x, mm.x), Hb = make_float4(hxy.y, hyy.y, hzz.y, mm.y);
-            const float4 La = make_float4(lxx.x, lyy.x, lzz.x, ww.x), Lb = make_float4(lxx.y, lyy.y, lzz.y, ww.y);
             const unsigned pa_id = sI[2 * P], pb_id = sI[2 * P + 1];
+            const float4 far = make_float4(1e15f, 1e15f, 1e15f, 0.0f), far_l = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+            const float4 Ha = ea < cnt ? A.spH[pa_id] : far, La = ea < cnt ? A.spL[pa_id] : far_l;
+            const float4 Hb = eb < cnt ? A.spH[pb_id] : far, Lb = eb < cnt ? A.spL[pb_id] : far_l;
 #pragma unroll
             for (int k = 0; k < NI; k++) {
-                const float2 hx = up2(HX[k]), hy = up2(HY[k]), hz = up2(HZ[k]);
-                const float2 lx = up2(LX[k]), ly = up2(LY[k]), lz = up2(LZ[k]);
-                pp_changeover_f<NI, NB, MD>(A, Ha, La, pa_id, ea < cnt, C, k, hx.x, hy.x, hz.x, lx.x, ly.x,
-                                            lz.x, invs_t[k], pid[k], valid[k], rout2, rout, pa);
-                pp_changeover_f<NI, NB, MD>(A, Hb, Lb, pb_id, eb < cnt, C, k, hx.x, hy.x, hz.x, lx.x, ly.x,
-                                            lz.x, invs_t[k], pid[k], valid[k], rout2, rout, pa);
+                const float4 Hi = A.spH[pid[k]], Li = A.spL[pid[k]];
+                pp_changeover_f<NI, NB, MD>(A, Ha, La, pa_id, ea < cnt, C, k, Hi.x, Hi.y, Hi.z, Li.x, Li.y,
+                                            Li.z, invs_t[k], pid[k], valid[k], rout2, rout, pa);
+                pp_changeover_f<NI, NB, MD>(A, Hb, Lb, pb_id, eb < cnt, C, k, Hi.x, Hi.y, Hi.z, Li.x, Li.y,
+                                            Li.z, invs_t[k], pid[k], valid[k], rout2, rout, pa);
             }
         } else {
             n_fast += real;
@@ -433,13 +432,15 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
     // ---- particle-particle: float-float differences, two list entries per
     // f32x2 operation on the Newtonian path
     {
-        f2x HX[NI], HY[NI], HZ[NI], LX[NI], LY[NI], LZ[NI], PA[NI][4];
+        f2x OX[NI], OY[NI], OZ[NI], PA[NI][4];
         float invs_t[NI];
 #pragma unroll
         for (int k = 0; k < NI; k++) {
             const float4 H = A.spH[pid[k]], L4 = A.spL[pid[k]];
-            HX[k] = pk2(H.x, H.x); HY[k] = pk2(H.y, H.y); HZ[k] = pk2(H.z, H.z);
-            LX[k] = pk2(L4.x, L4.x); LY[k] = pk2(L4.y, L4.y); LZ[k] = pk2(L4.z, L4.z);
+            const float ox = (H.x - Hg.x) + (L4.x - Lg.x);
+            const float oy = (H.y - Hg.y) + (L4.y - Lg.y);
+            const float oz = (H.z - Hg.z) + (L4.z - Lg.z);
+            OX[k] = pk2(ox, ox); OY[k] = pk2(oy, oy); OZ[k] = pk2(oz, oz);
             invs_t[k] = L4.w;                                    // 1 / s_i
 #pragma unroll
             for (int c = 0; c < 4; c++) PA[k][c] = 0ull;
@@ -462,32 +463,32 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
                     const int m = e / (2 * J), r = e - m * 2 * J;
                     const int half = r >= J ? 1 : 0;
                     const int P = m * J + r - half * J;
-                    float4 H = make_float4(1e15f, 1e15f, 1e15f, 0.0f);   // padding: massless, far away
-                    float4 L = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+                    float ox = 1e15f, oy = 1e15f, oz = 1e15f, ms = 0.0f, wj = 1.0f;   // padding: massless, far away
                     unsigned p = 0xffffffffu;
                     if (e < cnt) {
                         p = A.pp[po + t + e];
-                        H = A.spH[p];
-                        L = A.spL[p];
+                        const float4 H = A.spH[p], L = A.spL[p];
+                        ox = (H.x - Hg.x) + (L.x - Lg.x);
+                        oy = (H.y - Hg.y) + (L.y - Lg.y);
+                        oz = (H.z - Hg.z) + (L.z - Lg.z);
+                        ms = H.w;
+                        wj = L.w;
                     }
                     float *b = rows + 4 * P + half;
-                    b[0] = H.x;
-                    b[2] = H.y;
-                    b[R] = H.z;
-                    b[R + 2] = H.w;
-                    b[2 * R] = L.x;
-                    b[2 * R + 2] = L.y;
-                    b[3 * R] = L.z;
-                    b[3 * R + 2] = L.w;
+                    b[0] = ox;
+                    b[2] = oy;
+                    b[R] = oz;
+                    b[R + 2] = ms;
+                    if (MD) b[2 * R] = wj;
                     sI[w][2 * P + half] = p;
                 }
             }
             __syncwarp();
             if (NB && A.want_nb)
-                pp_tile_f2<NI, J, true, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, HX, HY, HZ, LX, LY, LZ,
+                pp_tile_f2<NI, J, true, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, OX, OY, OZ,
                                             invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
             else
-                pp_tile_f2<NI, J, false, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, HX, HY, HZ, LX, LY, LZ,
+                pp_tile_f2<NI, J, false, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, OX, OY, OZ,
                                              invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
             __syncwarp();
 #pragma unroll
