@@ -51,7 +51,7 @@ SEED = 2
 # r_out, the plain Newtonian pair ("pp_newton"), which is exact there.
 FLOPS = {
     ("mixed", "cell", 2): 56, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 77,
-    ("mixed", "pp_newton", None): 28,
+    ("mixed", "pp_newton", None): 22,
     ("fp64", "cell", 2): 56, ("fp64", "cell", 0): 22, ("fp64", "pp", None): 53,
 }
 SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
