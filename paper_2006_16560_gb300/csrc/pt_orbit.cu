@@ -126,28 +126,48 @@ constexpr int kOrbChunk = 128;     // opened-leaf particles staged per warp
 // Candidate tests of the staged particles against every member of group g:
 // a float32 prefilter on float-float differences with a 2^-10 margin on
 // r_nb^2 (it can only let extra pairs through), then the exact float64 test
-// and the pericentre in orbit_pair.  Candidates are counted, kept pairs
-// appended to the pair buffer.
+// and the pericentre in orbit_pair.  The prefilter runs branch-free over 32
+// staged particles at a time into a bit mask (the chunk is padded to a
+// multiple of 32 with massless particles far away); only the set bits take
+// the float64 path.  Candidates are counted, kept pairs appended to the
+// pair buffer.
 __device__ __forceinline__ void orbit_chunk(const OrbitArgs &A, const uint2 gr, int fill,
-                                            const float4 *cH, const float4 *cL, const float *cR,
-                                            const unsigned *cI, unsigned long long &ncand) {
+                                            float4 *cH, float4 *cL, float *cR, unsigned *cI,
+                                            unsigned long long &ncand) {
     const unsigned lane = threadIdx.x & 31;
+    const int fill32 = (fill + 31) & ~31;             // <= kOrbChunk, a multiple of 32
+    if ((int)lane + fill < fill32) {
+        const int e = fill + (int)lane;
+        cH[e] = make_float4(1e15f, 1e15f, 1e15f, 0.0f);
+        cL[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        cR[e] = 0.0f;
+        cI[e] = 0xffffffffu;
+    }
+    __syncwarp();
     for (unsigned t0 = 0; t0 < gr.y; t0 += 32) {
         const unsigned t = t0 + lane;
         const bool valid = t < gr.y;
         const unsigned pi = gr.x + (valid ? t : 0u);
         const float4 Hi = A.spH[pi], Li = A.spL[pi];
         const float ri = A.rnbf[pi];
-        for (int e = 0; e < fill; e++) {
-            const float4 Hj = cH[e], Lj = cL[e];
-            const float dx = (Hj.x - Hi.x) + (Lj.x - Li.x);
-            const float dy = (Hj.y - Hi.y) + (Lj.y - Li.y);
-            const float dz = (Hj.z - Hi.z) + (Lj.z - Li.z);
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float R = fmaxf(ri, cR[e]);
-            if (valid && r2 < R * R * (1.0f + 1.0f / 1024.0f)) {
-                const unsigned pj = cI[e];
-                if (pj != pi) {
+        for (int e0 = 0; e0 < fill32; e0 += 32) {
+            unsigned hit = 0u;
+#pragma unroll 8
+            for (int q = 0; q < 32; q++) {
+                const float4 Hj = cH[e0 + q], Lj = cL[e0 + q];
+                const float dx = (Hj.x - Hi.x) + (Lj.x - Li.x);
+                const float dy = (Hj.y - Hi.y) + (Lj.y - Li.y);
+                const float dz = (Hj.z - Hi.z) + (Lj.z - Li.z);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float R = fmaxf(ri, cR[e0 + q]);
+                hit |= (r2 < R * R * (1.0f + 1.0f / 1024.0f) ? 1u : 0u) << q;
+            }
+            if (!valid) hit = 0u;
+            while (hit) {
+                const int q = __ffs(hit) - 1;
+                hit &= hit - 1u;
+                const unsigned pj = cI[e0 + q];
+                if (pj != pi && pj != 0xffffffffu) {
                     const int state = orbit_pair(A, pi, pj);
                     ncand += state > 0;
                     if (state == 2) {
