@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--no-widened", action="store_true",
                     help="skip the orbit-neighbour and tidal-tensor legs")
+    ap.add_argument("--only-leg", choices=["orbit", "tidal"], default=None,
+                    help="run one widened leg alone on the headline set and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -467,6 +469,15 @@ def main():
     rank, world, local = rank_env()
     if args.impl == "reference":
         reference_main(args, rank, world)
+        return
+    if args.only_leg:
+        from paper_2006_16560_gb300 import binding as B
+        from paper_2006_16560_gb300 import inputs
+        d = inputs.plummer(args.n, SEED, masses="kroupa")
+        ctx = B.Context(local)
+        leg = orbit_leg(ctx, d, args.steps) if args.only_leg == "orbit" else tidal_leg(ctx, d, args.steps)
+        print(json.dumps({"leg": args.only_leg, **leg}), flush=True)
+        ctx.close()
         return
 
     import torch
