@@ -35,11 +35,7 @@ constexpr int kFThreads = 32 * kFWarps;
 #ifndef PT_FORCE_TILE
 #define PT_FORCE_TILE 64
 #endif
-#ifndef PT_FORCE_UNROLL
-#define PT_FORCE_UNROLL 2
-#endif
 constexpr int kJ = PT_FORCE_TILE;   // list entries per warp tile
-constexpr int kUnroll = PT_FORCE_UNROLL;   // unroll of the inner list loops
 #ifndef PT_FORCE_UNROLL_PAIRS
 #define PT_FORCE_UNROLL_PAIRS 2
 #endif
