@@ -544,6 +544,35 @@ int alloc_pairs(pt_tree *t, unsigned long long cap) {
     return PT_OK;
 }
 
+// Sizes the list arrays and chunk granules of a one-pass walk from the last
+// walk's totals: chunks of about four groups' lists (about one move of a
+// partial list per four groups); arrays for the estimate plus a quarter (the
+// moves leave up to an eighth behind) and per active warp one and a half
+// chunks left unused at the end.
+int size_onepass(pt_tree *t) {
+    pt_ctx *ctx = t->ctx;
+    const unsigned long long ngr = std::max<unsigned long long>(t->h.ngroups, 1);
+    auto granule = [&](unsigned long long est) {
+        unsigned long long c = 4 * (est / ngr + 1);
+        return std::min<unsigned long long>(std::max<unsigned long long>(c, kWalkChunkEntries), 1ull << 22);
+    };
+    t->chunk_cells = granule(t->est_cells);
+    t->chunk_pp = granule(t->est_pp);
+    const unsigned long long warps =
+        std::min<unsigned long long>((unsigned long long)walk_warps(t->walk_stack), ngr);
+    const unsigned long long need_c = t->est_cells + t->est_cells / 4 + warps * t->chunk_cells * 3 / 2;
+    const unsigned long long need_p = t->est_pp + t->est_pp / 4 + warps * t->chunk_pp * 3 / 2;
+    if (need_c > t->cap_cells || !t->cells.p) {
+        t->cap_cells = need_c;
+        TRY(ensure(ctx, t->cells, t->cap_cells * 4));
+    }
+    if (need_p > t->cap_pp || !t->pp.p) {
+        t->cap_pp = need_p;
+        TRY(ensure(ctx, t->pp, t->cap_pp * 4));
+    }
+    return PT_OK;
+}
+
 // A walk stack overflowed: first give the warps spill areas in global memory
 // (sized for the launch with the small stack, the widest), then a larger
 // shared stack.
@@ -578,30 +607,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         CK(cudaMemsetAsync(&dS->work, 0, sizeof(dS->work), st));
         CK(cudaMemsetAsync(&dS->npairs, 0, 3 * sizeof(unsigned long long), st));   // npairs, pp_full, pp_fast
         if (onepass) {
-            // chunks of about four groups' lists (about one move of a partial
-            // list per four groups); arrays for the estimate plus a quarter
-            // (the moves leave up to an eighth behind) and per active warp one
-            // and a half chunks left unused at the end
-            const unsigned long long ngr = std::max<unsigned long long>(t->h.ngroups, 1);
-            auto granule = [&](unsigned long long est) {
-                unsigned long long c = 4 * (est / ngr + 1);
-                return std::min<unsigned long long>(std::max<unsigned long long>(c, kWalkChunkEntries),
-                                                    1ull << 22);
-            };
-            t->chunk_cells = granule(t->est_cells);
-            t->chunk_pp = granule(t->est_pp);
-            const unsigned long long warps =
-                std::min<unsigned long long>((unsigned long long)walk_warps(t->walk_stack), ngr);
-            const unsigned long long need_c = t->est_cells + t->est_cells / 4 + warps * t->chunk_cells * 3 / 2;
-            const unsigned long long need_p = t->est_pp + t->est_pp / 4 + warps * t->chunk_pp * 3 / 2;
-            if (need_c > t->cap_cells || !t->cells.p) {
-                t->cap_cells = need_c;
-                TRY(ensure(ctx, t->cells, t->cap_cells * 4));
-            }
-            if (need_p > t->cap_pp || !t->pp.p) {
-                t->cap_pp = need_p;
-                TRY(ensure(ctx, t->pp, t->cap_pp * 4));
-            }
+            TRY(size_onepass(t));
             CK(cudaMemsetAsync(&dS->cell_total, 0, 2 * sizeof(unsigned long long), st));   // cell, pp totals
             CK(cudaEventRecord(ctx->ev[2], st));
             WalkArgs W = walk_args(t);
@@ -781,8 +787,7 @@ int enqueue_batch(pt_tree *t, cudaStream_t st, bool host_io, bool want_nb) {
     nk += build_launch(build_args(t, ip, im), st);
     CK(cudaMemsetAsync(&dS->flags, 0, sizeof(unsigned), st));
     WalkArgs W = walk_args(t);
-    nk += walk_launch(W, 0, st);
-    nk += walk_launch(W, 1, st);
+    nk += walk_launch(W, 2, st);              // one pass (arrays sized before the capture)
     ForceArgs F = force_args(t, t->d_acc.as<double>(), t->d_pot.as<double>(), want_nb);
     nk += force_launch(F, t->prm.precision, st);
     nk += force_reduce_launch(F, st);
@@ -952,11 +957,11 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
         if (flags & PT_BATCH_GRAPH) {
-            // leave head room so that later steps of the same shape fit
-            const unsigned long long cc = t->h.cell_total + t->h.cell_total / 4 + 4096;
-            const unsigned long long pc = t->h.pp_total + t->h.pp_total / 4 + 4096;
-            if (cc > t->cap_cells) { t->cap_cells = cc; TRY(ensure(ctx, t->cells, cc * 4)); }
-            if (pc > t->cap_pp) { t->cap_pp = pc; TRY(ensure(ctx, t->pp, pc * 4)); }
+            // the captured walk runs in one pass: lists sized from this step's
+            // totals with head room, so that later steps of the same shape fit
+            t->est_cells = t->h.cell_total;
+            t->est_pp = t->h.pp_total;
+            TRY(size_onepass(t));
             if (t->h.nnodes + t->h.nnodes / 4 > t->cap_nodes) {
                 t->cap_nodes = t->h.nnodes + t->h.nnodes / 4 + 1024;
                 t->nd_a.release(); t->nd_b.release(); t->nd_r.release(); t->nd_c.release();
