@@ -119,7 +119,7 @@ struct pt_tree {
     Buf status, sets, set_of, bmin, bmax, n_dev;
     Buf in_pos, in_mass;                                   // staging for host inputs
     Buf keys_in, vals_in, qbuf, skey, perm, sp64, spH, spL, sq;
-    Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, nd_p, nd_arrive, tmp_a, tmp_b, lcp;
+    Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, tmp_a, tmp_b, lcp;
     Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gpart;
     Buf cells, pp;
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
@@ -165,7 +165,7 @@ struct pt_tree {
     void release() {
         Buf *all[] = {&status, &sets, &set_of, &bmin, &bmax, &n_dev, &in_pos, &in_mass, &keys_in,
                       &vals_in, &qbuf, &skey, &perm, &sp64, &spH, &spL, &sq, &nd_a, &nd_b, &nd_r,
-                      &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &nd_p, &nd_arrive, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
+                      &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
                       &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
@@ -269,8 +269,6 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->nd_t, C * 64));
     TRY(ensure(ctx, t->nd_f, C * 64));
     TRY(ensure(ctx, t->nd_bnd, C * 32));
-    TRY(ensure(ctx, t->nd_p, C * 4));
-    TRY(ensure(ctx, t->nd_arrive, C * 4));
     TRY(ensure(ctx, t->lcp, N + 32));
     TRY(ensure(ctx, t->tmp_a, std::max(C, N) * 4));
     TRY(ensure(ctx, t->tmp_b, std::max(C, N) * 4));
@@ -331,8 +329,6 @@ BuildArgs build_args(pt_tree *t, const double *pos, const double *mass) {
     A.nd_t = t->nd_t.as<double4>();
     A.nd_f = t->nd_f.as<float4>();
     A.nd_bnd = t->nd_bnd.as<uint4>();
-    A.nd_p = t->nd_p.as<unsigned>();
-    A.nd_arrive = t->nd_arrive.as<unsigned>();
     A.lcp = t->lcp.as<unsigned char>();
     A.tmp_u32a = t->tmp_a.as<unsigned>();
     A.tmp_u32b = t->tmp_b.as<unsigned>();
@@ -424,7 +420,7 @@ int run_build(pt_tree *t, const double *pos, const double *mass) {
             t->cap_nodes = (unsigned)c;
             t->nd_a.release();   // force re-allocation of node arrays
             t->nd_b.release(); t->nd_r.release(); t->nd_c.release(); t->nd_q.release();
-            t->nd_t.release(); t->nd_f.release(); t->nd_bnd.release(); t->nd_p.release(); t->nd_arrive.release(); t->tmp_a.release(); t->tmp_b.release();
+            t->nd_t.release(); t->nd_f.release(); t->nd_bnd.release(); t->tmp_a.release(); t->tmp_b.release();
             continue;
         }
         t->built = true;
@@ -965,7 +961,7 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
             if (t->h.nnodes + t->h.nnodes / 4 > t->cap_nodes) {
                 t->cap_nodes = t->h.nnodes + t->h.nnodes / 4 + 1024;
                 t->nd_a.release(); t->nd_b.release(); t->nd_r.release(); t->nd_c.release();
-                t->nd_q.release(); t->nd_t.release(); t->nd_f.release(); t->nd_bnd.release(); t->nd_p.release(); t->nd_arrive.release(); t->tmp_a.release(); t->tmp_b.release();
+                t->nd_q.release(); t->nd_t.release(); t->nd_f.release(); t->nd_bnd.release(); t->tmp_a.release(); t->tmp_b.release();
                 TRY(alloc_build(t, n, C));
             }
             if (want_nb) TRY(alloc_pairs(t, std::max<unsigned long long>(t->cap_pairs, t->h.npairs * 2 + 1024)));

@@ -205,13 +205,12 @@ __device__ __forceinline__ void level_range(const Status *st, int l, unsigned ca
 }
 
 __global__ void k_topo_roots(const SetInfo *sets, int nsets, uint4 *nd_a, uint4 *nd_b,
-                             uint2 *nd_r, unsigned *nd_p, Status *st) {
+                             uint2 *nd_r, Status *st) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < nsets) {
         nd_r[s] = make_uint2(sets[s].begin, sets[s].n);
         nd_a[s] = make_uint4(0, 0, 0, make_meta(0, 0, 0));
         nd_b[s] = make_uint4(0, 0, 0, 0);
-        nd_p[s] = 0xffffffffu;
     }
     if (s == 0) {
         st->lvl_begin[0] = 0;
@@ -363,7 +362,7 @@ __global__ void __launch_bounds__(kT) k_topo_count_big(int l, const unsigned lon
 }
 
 __global__ void __launch_bounds__(kT) k_topo_emit(int l, const uint4 *bnd,
-                                                  uint4 *nd_a, uint4 *nd_b, uint2 *nd_r, unsigned *nd_p,
+                                                  uint4 *nd_a, uint4 *nd_b, uint2 *nd_r,
                                                   const unsigned *nch, const unsigned *choff,
                                                   unsigned cap, Status *st) {
     unsigned b0, cnt;
@@ -392,7 +391,6 @@ __global__ void __launch_bounds__(kT) k_topo_emit(int l, const uint4 *bnd,
                 nd_r[c] = make_uint2(B[j], B[j + 1] - B[j]);
                 nd_a[c] = make_uint4(0, 0, 0, make_meta((unsigned)l + 1, 1, 0));
                 nd_b[c] = make_uint4(0, 0, 0, 0);
-                nd_p[c] = v;
             }
             c++;
         }
@@ -423,18 +421,9 @@ __global__ void k_topo_finish(Status *st, unsigned cap) {
 // stored quadrupole is Q = 3T - tr(T) I (twice the traceless A' of Eq. 31).
 // ---------------------------------------------------------------------------
 
-// Loads through L2 (bypassing L1) of records another thread of the same
-// launch may have written.
-__device__ __forceinline__ double4 ldcg4(const double4 *p) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    const double2 a = __ldcg(q), b = __ldcg(q + 1);
-    return make_double4(a.x, a.y, b.x, b.y);
-}
-
 // Moments of node v: leaves sum their particles about the first particle,
-// internal nodes combine their children with the parallel-axis shift.  The
-// children's records were written by other threads of the same launch, so
-// they are read through L2 (ld.cg).
+// internal nodes combine their children (complete: a deeper level or a leaf,
+// from an earlier launch) with the parallel-axis shift.
 __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, const uint4 *sq, uint4 *nd_a,
                                              uint4 *nd_b, const uint2 *nd_r, double4 *nd_c, double4 *nd_q,
                                              double4 *nd_t, float4 *nd_f, const double *ssc,
@@ -474,24 +463,24 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
     } else {
         const unsigned fc = bb.w, nc = meta_nchild(a.w);
         if (fc >= cap || nc > cap - fc) return;     // truncated build (capacity flag is set)
-        double4 c0 = ldcg4(&nd_c[fc]);
+        double4 c0 = nd_c[fc];
         double x0[3] = {c0.x, c0.y, c0.z};
         for (unsigned c = fc; c < fc + nc; c++) {
-            double4 C = ldcg4(&nd_c[c]);
+            double4 C = nd_c[c];
             M += C.w;
             s1[0] += C.w * (C.x - x0[0]);
             s1[1] += C.w * (C.y - x0[1]);
             s1[2] += C.w * (C.z - x0[2]);
-            uint4 ca = __ldcg(&nd_a[c]), cb = __ldcg(&nd_b[c]);
-            smax = fmax(smax, ldcg4(&nd_t[2 * c + 1]).z);
+            uint4 ca = nd_a[c], cb = nd_b[c];
+            smax = fmax(smax, nd_t[2 * c + 1].z);
             qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
             qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
         }
         if (M > 0.0) {
             for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] / M;
             for (unsigned c = fc; c < fc + nc; c++) {
-                double4 C = ldcg4(&nd_c[c]);
-                double4 t0 = ldcg4(&nd_t[2 * c]), t1 = ldcg4(&nd_t[2 * c + 1]);
+                double4 C = nd_c[c];
+                double4 t0 = nd_t[2 * c], t1 = nd_t[2 * c + 1];
                 double e0 = C.x - com[0], e1 = C.y - com[1], e2 = C.z - com[2], m = C.w;
                 T[0] += t0.x + m * e0 * e0;
                 T[1] += t0.y + m * e1 * e1;
@@ -526,30 +515,33 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
     nd_f[4 * v + 3] = make_float4(__double2float_rn(Q[5]), 0.f, 0.f, 0.f);
 }
 
-// All multipoles in one launch, bottom-up: a thread per leaf computes it,
-// then climbs; at each parent the last child to arrive (atomic counter,
-// after a fence that publishes its own record) computes the parent.  The
-// arithmetic is the same as a level-by-level sweep, so the results are too.
-__global__ void __launch_bounds__(kT) k_moments(const double4 *sp64, const uint4 *sq, uint4 *nd_a,
-                                                uint4 *nd_b, const uint2 *nd_r, const unsigned *nd_p,
-                                                unsigned *arrive, double4 *nd_c, double4 *nd_q,
-                                                double4 *nd_t, float4 *nd_f, const double *ssc,
-                                                const SetInfo *sets, long long *nd_thr, unsigned cap,
-                                                const Status *st) {
+// Multipoles bottom-up: every leaf at once (k_moments_leaves), then the
+// internal nodes one level at a time, deepest first (k_moments_level), so
+// that each level finds its children complete.  (A single launch in which
+// the last child to arrive computes its parent was measured slower: its
+// climb is a 21-step chain of dependent loads.)
+__global__ void __launch_bounds__(kT) k_moments_leaves(const double4 *sp64, const uint4 *sq, uint4 *nd_a,
+                                                       uint4 *nd_b, const uint2 *nd_r, double4 *nd_c,
+                                                       double4 *nd_q, double4 *nd_t, float4 *nd_f,
+                                                       const double *ssc, const SetInfo *sets,
+                                                       long long *nd_thr, unsigned cap, const Status *st) {
     const unsigned nn = min(st->nnodes, cap);
-    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
-        if (!meta_leaf(nd_a[v].w)) continue;
-        unsigned u = v;
-        for (int up = 0; up <= kMaxLevel; up++) {
-            node_moments(u, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr, cap);
-            __threadfence();
-            const unsigned p = nd_p[u];
-            if (p >= cap) break;                                       // a root
-            const unsigned nch = meta_nchild(__ldcg(&nd_a[p]).w);
-            if (atomicAdd(&arrive[p], 1u) + 1u != nch) break;          // not the last child
-            __threadfence();
-            u = p;
-        }
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x)
+        if (meta_leaf(nd_a[v].w))
+            node_moments(v, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr, cap);
+}
+
+__global__ void __launch_bounds__(kT) k_moments_level(int l, const double4 *sp64, const uint4 *sq,
+                                                      uint4 *nd_a, uint4 *nd_b, const uint2 *nd_r,
+                                                      double4 *nd_c, double4 *nd_q, double4 *nd_t,
+                                                      float4 *nd_f, const double *ssc, const SetInfo *sets,
+                                                      long long *nd_thr, unsigned cap, const Status *st) {
+    unsigned b0, cnt;
+    level_range(st, l, cap, b0, cnt);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        const unsigned v = b0 + k;
+        if (!meta_leaf(nd_a[v].w))
+            node_moments(v, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr, cap);
     }
 }
 
@@ -674,7 +666,7 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     // topology
     k_lcp<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.skey, A.n_dev, A.lcp);
     nk++;
-    k_topo_roots<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.nd_a, A.nd_b, A.nd_r, A.nd_p, S);
+    k_topo_roots<<<(A.nsets + 127) / 128, 128, 0, st>>>(A.sets, A.nsets, A.nd_a, A.nd_b, A.nd_r, S);
     nk += 2;
     for (int l = 0; l <= kMaxLevel; l++) {
         k_topo_count<<<gmax, kT, 0, st>>>(l, A.skey, A.lcp, A.nd_a, A.nd_r, A.tmp_u32a, A.nd_bnd,
@@ -685,17 +677,19 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
         if (l == kMaxLevel) break;
         nk += scan_exclusive<unsigned>(A.tmp_u32a, A.tmp_u32b, &S->lvl_count[l], nullptr,
                                        &S->lvl_count[l + 1], A.scan_tmp, st);
-        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.nd_bnd, A.nd_a, A.nd_b, A.nd_r, A.nd_p, A.tmp_u32a,
-                                         A.tmp_u32b, A.cap_nodes, S);
+        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.nd_bnd, A.nd_a, A.nd_b, A.nd_r, A.tmp_u32a, A.tmp_u32b,
+                                         A.cap_nodes, S);
         nk++;
     }
     k_topo_finish<<<1, 1, 0, st>>>(S, A.cap_nodes);
     nk++;
-    cudaMemsetAsync(A.nd_arrive, 0, (size_t)A.cap_nodes * sizeof(unsigned), st);
-    k_moments<<<gmax, kT, 0, st>>>(A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_p, A.nd_arrive, A.nd_c,
-                                   A.nd_q, A.nd_t, A.nd_f, A.ssc, A.sets, A.massdep ? A.nd_thr : nullptr,
-                                   A.cap_nodes, S);
+    long long *thr = A.massdep ? A.nd_thr : nullptr;
+    k_moments_leaves<<<gmax, kT, 0, st>>>(A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,
+                                          A.nd_f, A.ssc, A.sets, thr, A.cap_nodes, S);
     nk++;
+    for (int l = kMaxLevel - 1; l >= 0; l--, nk++)
+        k_moments_level<<<gmax, kT, 0, st>>>(l, A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q,
+                                             A.nd_t, A.nd_f, A.ssc, A.sets, thr, A.cap_nodes, S);
     // groups
     cudaMemsetAsync(A.gflag, 0, (size_t)n * sizeof(unsigned), st);
     k_group_mark<<<gmax, kT, 0, st>>>(A.nd_a, A.nd_b, A.nd_r, A.gflag, A.n_group, S);

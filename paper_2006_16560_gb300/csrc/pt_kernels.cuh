@@ -37,7 +37,6 @@ struct BuildArgs {
     double4 *nd_c, *nd_q, *nd_t;
     float4 *nd_f;
     uint4 *nd_bnd;                   // 2 per node: child boundaries of split nodes (build only)
-    unsigned *nd_p, *nd_arrive;      // parent of each node; arrival counters of the moments pass
     unsigned char *lcp;              // n + 32 bytes: shared key digits of neighbours (build only)
     unsigned *tmp_u32a, *tmp_u32b;   // max(cap_nodes, n) each
     // groups
