@@ -289,3 +289,27 @@ def test_fp32_probe(ctx):
     assert rc == B.PT_OK
     assert 30.0 < tf < 90.0
     assert B.pt_probe_fp32_peak(None)[0] == B.PT_ERR_ARG
+
+
+def test_build_graph_replay_sees_new_data(ctx):
+    """Rebuilding a tree from the same device buffers replays a captured build
+    graph from the third build on; it must read the buffers' current contents
+    (the positions drift between steps, as in a simulation)."""
+    import torch
+    n = 30000
+    d = inputs.plummer(n, 29, masses="kroupa")
+    p = c1_params(order=2, precision=B.PT_MIXED)
+    p.r_out, p.r_in = 0.01, 0.001
+    pos, mass = torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["mass"]).cuda()
+    t = B.Tree(ctx, pos, mass, p)
+    rng = np.random.default_rng(29)
+    for step in range(4):
+        pos += torch.from_numpy(rng.normal(scale=1e-3, size=(n, 3))).cuda()    # drift in place
+        t.rebuild(pos, mass, p)
+        acc = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        t.force(acc, pot)
+        ref = run_gpu(ctx, pos.cpu().numpy(), d["mass"], p, neighbours=False)
+        assert np.array_equal(acc.cpu().numpy(), ref["acc"]), step
+        assert np.array_equal(pot.cpu().numpy(), ref["pot"]), step
+    t.free()
