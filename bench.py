@@ -50,7 +50,7 @@ SEED = 2
 # changeover path ("pp") or, when no pair of the warp's iteration is within
 # r_out, the plain Newtonian pair ("pp_newton"), which is exact there.
 FLOPS = {
-    ("mixed", "cell", 2): 56, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 77,
+    ("mixed", "cell", 2): 55, ("mixed", "cell", 0): 22, ("mixed", "pp", None): 77,
     ("mixed", "pp_newton", None): 22,
     ("fp64", "cell", 2): 56, ("fp64", "cell", 0): 22, ("fp64", "pp", None): 53,
 }
@@ -60,7 +60,7 @@ FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maxi
 # DRAM bytes per launch of the mixed force kernel from one ncu capture of the
 # same kernel build on this workload (dram__bytes_read.sum + dram__bytes_write.sum);
 # None when the kernel changed after the capture.
-FORCE_MIXED_DRAM_BYTES = 1_368_980_000
+FORCE_MIXED_DRAM_BYTES = 1_536_100_000
 
 
 def rank_env():

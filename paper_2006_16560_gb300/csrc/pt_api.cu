@@ -120,7 +120,7 @@ struct pt_tree {
     Buf in_pos, in_mass;                                   // staging for host inputs
     Buf keys_in, vals_in, qbuf, skey, perm, sp64, spH, spL, sq;
     Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, tmp_a, tmp_b, lcp;
-    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gpart;
+    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gr_ord, gpart;
     Buf cells, pp;
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
@@ -166,7 +166,7 @@ struct pt_tree {
         Buf *all[] = {&status, &sets, &set_of, &bmin, &bmax, &n_dev, &in_pos, &in_mass, &keys_in,
                       &vals_in, &qbuf, &skey, &perm, &sp64, &spH, &spL, &sq, &nd_a, &nd_b, &nd_r,
                       &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
-                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gpart, &cells, &pp, &pairs,
+                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gr_ord, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
                       &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv, &orb_rnbf, &walk_spill,
@@ -279,6 +279,7 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->gr_b, N * 16));
     TRY(ensure(ctx, t->gr_nc, N * 4));
     TRY(ensure(ctx, t->gr_np, N * 4));
+    TRY(ensure(ctx, t->gr_ord, N * 4));
     TRY(ensure(ctx, t->gr_co, (N + 1) * 8));
     TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
     TRY(ensure(ctx, t->gpart, N * 32));
@@ -469,6 +470,7 @@ ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
     A.gr_np = t->gr_np.as<unsigned>();
     A.gr_co = t->gr_co.as<unsigned long long>();
     A.gr_po = t->gr_po.as<unsigned long long>();
+    A.gr_ord = t->gr_ord.as<unsigned>();
     A.cells = t->cells.as<unsigned>();
     A.pp = t->pp.as<unsigned>();
     A.sp64 = t->sp64.as<double4>();

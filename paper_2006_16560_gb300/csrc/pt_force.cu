@@ -162,7 +162,6 @@ __device__ __forceinline__ void cells_tile_f2(const ulonglong2 (*sP)[kJ / 2], in
             const f2x rinv = pk2(rsqrtf(r2.x), rsqrtf(r2.y));
             const f2x rinv2 = mul2(rinv, rinv);
             const f2x mr = mul2(zm.y, rinv);
-            const f2x mr3 = mul2(mr, rinv2);
             if (ORDER == 2) {
                 // the tile holds -Q: qa = -(Qxx, Qyy), qb = -(Qzz, Qxy), qc = -(Qxz, Qyz)
                 const f2x qx = fma2(qc.x, dz, fma2(qb.y, dy, mul2(qa.x, dx)));   // (-Q d)_x
@@ -170,13 +169,14 @@ __device__ __forceinline__ void cells_tile_f2(const ulonglong2 (*sP)[kJ / 2], in
                 const f2x qz = fma2(qb.x, dz, fma2(qc.y, dy, mul2(qc.x, dx)));
                 const f2x rinv5 = mul2(mul2(rinv2, rinv2), rinv);
                 const f2x nt = mul2(fma2(dz, qz, fma2(dy, qy, mul2(dx, qx))), rinv5);   // -t, t = d.Q.d / r^5
-                // f = mr3 + 2.5 t / r^2;  a += f d - Q d / r^5;  P += mr + t / 2
-                const f2x f = fma2(mul2(nt, m25), rinv2, mr3);
+                // f = (mr + 2.5 t) / r^2;  a += f d - Q d / r^5;  P += mr + t / 2
+                const f2x f = mul2(fma2(nt, m25, mr), rinv2);
                 PA[k][0] = fma2(qx, rinv5, fma2(f, dx, PA[k][0]));
                 PA[k][1] = fma2(qy, rinv5, fma2(f, dy, PA[k][1]));
                 PA[k][2] = fma2(qz, rinv5, fma2(f, dz, PA[k][2]));
                 PA[k][3] = fma2(nt, mhalf, add2(PA[k][3], mr));
             } else {
+                const f2x mr3 = mul2(mr, rinv2);
                 PA[k][0] = fma2(mr3, dx, PA[k][0]);
                 PA[k][1] = fma2(mr3, dy, PA[k][1]);
                 PA[k][2] = fma2(mr3, dz, PA[k][2]);
@@ -562,6 +562,14 @@ __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, d
     }
 }
 
+// Configuration class of a group's first pass (0: more than 64 targets, more
+// than one pass or the 96-slot one; then 64, 48, 32 and 24 slots), in the
+// order the mixed kernel takes the groups.
+__device__ __forceinline__ int pass_class(unsigned n) {
+    return n > 64 ? 0 : n > 48 ? 1 : n > 32 ? 2 : n > 24 ? 3 : 4;
+}
+constexpr int kPassClasses = 5;
+
 // Pass configuration for `rem` remaining targets: returns the slot count and
 // runs the matching instantiation.
 template <int ORDER, bool NB, bool MD>
@@ -593,8 +601,8 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         __syncthreads();
         if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
         __syncthreads();
-        const unsigned g = gsh;
-        if (g >= ng) break;
+        if (gsh >= ng) break;
+        const unsigned g = A.gr_ord[gsh];
         const uint2 gr = A.gr_r[g];
         const Chg C64 = make_chg(A.sets[A.gr_a[g].w]);
         ChgF C;
@@ -860,10 +868,80 @@ __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, con
     }
 }
 
+// Order in which the mixed kernel takes the groups: class by class (largest
+// pass configuration first), group order within a class.  Consecutive groups
+// then run the same instantiation, which keeps one code path in the SMs'
+// instruction caches, and the largest groups start first, which shortens the
+// tail of the atomic work queue.  One CTA: thread t classifies a contiguous
+// chunk of groups, a block-wide exclusive scan per class gives each chunk its
+// output positions, and a second pass over the chunk writes them (stable).
+__global__ void __launch_bounds__(1024) k_group_order(const uint2 *gr_r, unsigned *gr_ord,
+                                                      const Status *st) {
+    __shared__ unsigned wsum[32][kPassClasses];
+    __shared__ unsigned base[kPassClasses];
+    const unsigned ng = st->ngroups;
+    const unsigned t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const unsigned per = (ng + 1023) / 1024;
+    const unsigned b = min(t * per, ng), e = min(b + per, ng);
+    unsigned c[kPassClasses], x[kPassClasses];
+#pragma unroll
+    for (int k = 0; k < kPassClasses; k++) c[k] = 0;
+    for (unsigned g = b; g < e; g++) c[pass_class(gr_r[g].y)]++;
+#pragma unroll
+    for (int k = 0; k < kPassClasses; k++) {       // inclusive scan within the warp
+        unsigned v = c[k];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= (unsigned)d) v += u;
+        }
+        x[k] = v;
+        if (lane == 31) wsum[w][k] = v;
+    }
+    __syncthreads();
+    if (w == 0) {                                   // inclusive scan over the warps
+        unsigned v[kPassClasses];
+#pragma unroll
+        for (int k = 0; k < kPassClasses; k++) v[k] = wsum[lane][k];
+#pragma unroll
+        for (int k = 0; k < kPassClasses; k++) {
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned u = __shfl_up_sync(0xffffffffu, v[k], d);
+                if (lane >= (unsigned)d) v[k] += u;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < kPassClasses; k++) wsum[lane][k] = v[k];
+    }
+    __syncthreads();
+    if (t == 0) {
+        unsigned sum = 0;
+        for (int k = 0; k < kPassClasses; k++) {
+            base[k] = sum;
+            sum += wsum[31][k];
+        }
+    }
+    __syncthreads();
+    unsigned o[kPassClasses];
+#pragma unroll
+    for (int k = 0; k < kPassClasses; k++) o[k] = base[k] + (w ? wsum[w - 1][k] : 0u) + x[k] - c[k];
+    for (unsigned g = b; g < e; g++) {
+        const int k = pass_class(gr_r[g].y);
+        unsigned pos = 0;
+#pragma unroll
+        for (int j = 0; j < kPassClasses; j++)      // register-indexed: no local-memory array
+            if (j == k) pos = o[j]++;
+        gr_ord[pos] = g;
+    }
+}
+
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
     const int blocks = 152 * 8;
     const bool md = A.massdep != 0;
     if (precision == 1) {
+        k_group_order<<<1, 1024, 0, st>>>(A.gr_r, A.gr_ord, A.st);
         if (A.order == 2) {
             if (md) k_force_mixed<2, true, true><<<blocks, kFThreads, 0, st>>>(A);
             else k_force_mixed<2, true, false><<<blocks, kFThreads, 0, st>>>(A);
@@ -880,7 +958,7 @@ int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
             else k_force_fp64<0, true, false><<<blocks, kFThreads, 0, st>>>(A);
         }
     }
-    return 1;
+    return precision == 1 ? 2 : 1;
 }
 
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st) {

@@ -83,6 +83,7 @@ struct ForceArgs {
     const uint4 *gr_a;
     const unsigned *gr_nc, *gr_np;
     const unsigned long long *gr_co, *gr_po;
+    unsigned *gr_ord;                // mixed kernel: group processing order (written per launch)
     const unsigned *cells, *pp;
     const double4 *sp64;
     const float4 *spH, *spL;

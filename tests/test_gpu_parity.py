@@ -103,6 +103,31 @@ def test_plummer4096_fp64_vs_oracle(ctx, order):
     assert np.percentile(rel_err(g["acc"], ad), 99) < 0.05
 
 
+@pytest.mark.parametrize("n_group", [8, 24, 40, 96, 200])
+def test_mixed_every_pass_configuration(ctx, n_group):
+    """Group sizes that select each pass configuration of the mixed kernel
+    (24 to 96 slots, and several passes for groups above 96 targets), taken in
+    the kernel's class order: every target is evaluated once, within the
+    mixed bound of the FP64 path, and the energy sums agree."""
+    d = inputs.plummer(6000, 300 + n_group, masses="kroupa")
+    kw = dict(order=2, n_leaf=8, n_group=n_group)
+    g64 = run_gpu(ctx, d["pos"], d["mass"], c1_params(**kw))
+    gmx = run_gpu(ctx, d["pos"], d["mass"], c1_params(precision=B.PT_MIXED, **kw))
+    sizes = gmx["tree"].groups()["count"]
+    assert sizes.sum() == len(d["mass"]) and sizes.max() > min(n_group, 96) // 2
+    if n_group > 96:
+        assert (sizes > 96).any()          # several passes per group
+    e = rel_err(gmx["acc"], g64["acc"])
+    assert np.percentile(e, 99) <= MIXED_P99
+    assert e.max() <= MIXED_MAX
+    ep = np.abs(gmx["pot"] - g64["pot"]) / np.abs(g64["pot"])
+    assert np.percentile(ep, 99) <= MIXED_P99
+    for k in ("cell_interactions", "pp_interactions"):
+        assert gmx["stats"][k] == g64["stats"][k]
+    assert gmx["stats"]["energy"] == pytest.approx(g64["stats"]["energy"], rel=1e-6)
+    assert np.array_equal(gmx["nb_idx"], g64["nb_idx"])
+
+
 @pytest.mark.parametrize("order", [0, 2])
 def test_plummer4096_mixed(ctx, order):
     d = inputs.plummer(4096, 1)
