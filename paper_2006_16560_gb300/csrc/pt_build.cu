@@ -40,6 +40,56 @@ __global__ void __launch_bounds__(kT) k_box(const double *pos, const double *mas
                                             const unsigned *set_of, unsigned long long *bmin,
                                             unsigned long long *bmax, Status *st) {
     unsigned bad = 0;
+    if (!set_of) {
+        // one set: per-thread extrema over the grid-stride loop, reduced over
+        // the warp and the block, then one atomic per block and component
+        __shared__ unsigned long long sb[kT / 32][6];
+        unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const double x[3] = {pos[3ull * i], pos[3ull * i + 1], pos[3ull * i + 2]};
+            const double m = mass[i];
+            if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]) || !isfinite(m)) bad |= kErrNonFinite;
+            if (m < 0.0) bad |= kErrNegMass;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const unsigned long long o = dbl_to_ordered(x[d]);
+                lo[d] = o < lo[d] ? o : lo[d];
+                hi[d] = o > hi[d] ? o : hi[d];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[d], o);
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi[d], o);
+                lo[d] = a < lo[d] ? a : lo[d];
+                hi[d] = b > hi[d] ? b : hi[d];
+            }
+        }
+        const unsigned w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                sb[w][d] = lo[d];
+                sb[w][3 + d] = hi[d];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6 && blockIdx.x * blockDim.x < n) {
+            const int c = threadIdx.x;
+            unsigned long long v = sb[0][c];
+            for (int k = 1; k < kT / 32; k++) {
+                const unsigned long long u = sb[k][c];
+                v = c < 3 ? (u < v ? u : v) : (u > v ? u : v);
+            }
+            if (c < 3) atomicMin(&bmin[c], v);
+            else atomicMax(&bmax[c - 3], v);
+        }
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        if ((threadIdx.x & 31) == 0 && bad) atomicOr(&st->flags, bad);
+        return;
+    }
     for (unsigned base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         unsigned i = base + threadIdx.x;
         bool valid = i < n;
@@ -126,10 +176,10 @@ __global__ void __launch_bounds__(kT) k_keys(const double *pos, unsigned n, cons
         const SetInfo &S = sets[s];
         unsigned q[3];
         for (int d = 0; d < 3; d++) {
-            double u = floor(__dmul_rn(__dsub_rn(pos[3ull * i + d], S.origin[d]), S.scale));
-            u = u < 0.0 ? 0.0 : u;
-            u = u > (double)(kGrid - 1) ? (double)(kGrid - 1) : u;
-            q[d] = (unsigned)u;
+            // floor((x - origin) scale) clamped to the grid: the conversion
+            // rounds down and saturates, the clamp is integer
+            const long long u = __double2ll_rd(__dmul_rn(__dsub_rn(pos[3ull * i + d], S.origin[d]), S.scale));
+            q[d] = (unsigned)min(max(u, 0ll), (long long)(kGrid - 1));
         }
         keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
         vals[i] = i;
@@ -146,13 +196,14 @@ __global__ void __launch_bounds__(kT) k_gather(const double *pos, const double *
     for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         unsigned i = perm[p];
         const double sc = scale ? scale[i] : 1.0;
+        const float inv_sc = scale ? __double2float_rn(1.0 / sc) : 1.0f;
         ssc[p] = sc;
         double x = pos[3ull * i], y = pos[3ull * i + 1], z = pos[3ull * i + 2], m = mass[i];
         sp64[p] = make_double4(x, y, z, m);
         float xh = __double2float_rn(x), yh = __double2float_rn(y), zh = __double2float_rn(z);
         spH[p] = make_float4(xh, yh, zh, __double2float_rn(m));
         spL[p] = make_float4(__double2float_rn(x - (double)xh), __double2float_rn(y - (double)yh),
-                             __double2float_rn(z - (double)zh), __double2float_rn(1.0 / sc));
+                             __double2float_rn(z - (double)zh), inv_sc);
         sq[p] = qbuf[i];
     }
 }
@@ -440,10 +491,12 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
             double4 P = sp64[p];
             uint4 q = sq[p];
             double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
+            // float64 is GB300's slow pipe: m d formed once, reused by both sums
+            const double md0 = m * d0, md1 = m * d1, md2 = m * d2;
             M += m;
-            s1[0] += m * d0; s1[1] += m * d1; s1[2] += m * d2;
-            s2[0] += m * d0 * d0; s2[1] += m * d1 * d1; s2[2] += m * d2 * d2;
-            s2[3] += m * d0 * d1; s2[4] += m * d0 * d2; s2[5] += m * d1 * d2;
+            s1[0] += md0; s1[1] += md1; s1[2] += md2;
+            s2[0] = fma(md0, d0, s2[0]); s2[1] = fma(md1, d1, s2[1]); s2[2] = fma(md2, d2, s2[2]);
+            s2[3] = fma(md0, d1, s2[3]); s2[4] = fma(md0, d2, s2[4]); s2[5] = fma(md1, d2, s2[5]);
             qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
             qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
             smax = fmax(smax, ssc[p]);

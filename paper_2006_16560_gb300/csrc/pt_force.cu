@@ -37,7 +37,7 @@ constexpr int kFThreads = 32 * kFWarps;
 #endif
 constexpr int kJ = PT_FORCE_TILE;   // list entries per warp tile
 #ifndef PT_FORCE_UNROLL_PAIRS
-#define PT_FORCE_UNROLL_PAIRS 2
+#define PT_FORCE_UNROLL_PAIRS 1
 #endif
 constexpr int kUnrollPairs = PT_FORCE_UNROLL_PAIRS;   // unroll of the packed cell-pair loop
 #ifndef PT_FORCE_UNROLL_PP
@@ -834,9 +834,11 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
 __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, const uint2 *gr_r,
                                                        const unsigned *gr_nc, const unsigned *gr_np,
                                                        Status *st) {
-    __shared__ double se[1024][4];
-    __shared__ unsigned long long si[1024][2];
-    const unsigned ng = st->ngroups;
+    // fixed reduction order (thread strides, then butterflies over the warp
+    // and over the warps' sums): the same sums every run
+    __shared__ double se[32][4];
+    __shared__ unsigned long long si[32][2];
+    const unsigned ng = st->ngroups, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double e[4] = {0, 0, 0, 0};
     unsigned long long ci = 0, pi = 0;
     for (unsigned g = threadIdx.x; g < ng; g += blockDim.x) {
@@ -846,25 +848,39 @@ __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, con
         ci += n * gr_nc[g];
         pi += n * gr_np[g];
     }
-    for (int c = 0; c < 4; c++) se[threadIdx.x][c] = e[c];
-    si[threadIdx.x][0] = ci;
-    si[threadIdx.x][1] = pi;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            for (int c = 0; c < 4; c++) se[threadIdx.x][c] += se[threadIdx.x + s][c];
-            si[threadIdx.x][0] += si[threadIdx.x + s][0];
-            si[threadIdx.x][1] += si[threadIdx.x + s][1];
-        }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) e[c] += __shfl_xor_sync(0xffffffffu, e[c], o);
+        ci += __shfl_xor_sync(0xffffffffu, ci, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
     }
-    if (threadIdx.x == 0) {
-        st->energy = se[0][0];
-        st->mom[0] = se[0][1];
-        st->mom[1] = se[0][2];
-        st->mom[2] = se[0][3];
-        st->cell_inter = si[0][0];
-        st->pp_inter = si[0][1];
+    if (lane == 0) {
+        for (int c = 0; c < 4; c++) se[w][c] = e[c];
+        si[w][0] = ci;
+        si[w][1] = pi;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const bool have = lane < (blockDim.x >> 5);
+        for (int c = 0; c < 4; c++) e[c] = have ? se[lane][c] : 0.0;
+        ci = have ? si[lane][0] : 0ull;
+        pi = have ? si[lane][1] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) e[c] += __shfl_xor_sync(0xffffffffu, e[c], o);
+            ci += __shfl_xor_sync(0xffffffffu, ci, o);
+            pi += __shfl_xor_sync(0xffffffffu, pi, o);
+        }
+        if (lane == 0) {
+            st->energy = e[0];
+            st->mom[0] = e[1];
+            st->mom[1] = e[2];
+            st->mom[2] = e[3];
+            st->cell_inter = ci;
+            st->pp_inter = pi;
+        }
     }
 }
 
