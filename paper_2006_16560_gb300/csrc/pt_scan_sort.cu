@@ -137,9 +137,18 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const unsigned long 
     __syncthreads();
     unsigned lo, hi;
     chunk_of(*n_dev, blockIdx.x, gridDim.x, lo, hi);
-    for (unsigned i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        unsigned d = digit_of<SET_PASS>(SET_PASS ? 0ull : keys[i], SET_PASS ? vals[i] : 0u, shift, set_of);
-        atomicAdd(&h[d], 1u);
+    constexpr int U = 4;                 // loads in flight per thread
+    for (unsigned i = lo + threadIdx.x; i < hi; i += U * blockDim.x) {
+        unsigned d[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const unsigned j = i + u * blockDim.x;
+            d[u] = j < hi ? digit_of<SET_PASS>(SET_PASS ? 0ull : keys[j], SET_PASS ? vals[j] : 0u, shift, set_of)
+                          : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (d[u] != 0xffffffffu) atomicAdd(&h[d[u]], 1u);
     }
     __syncthreads();
     counts[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
