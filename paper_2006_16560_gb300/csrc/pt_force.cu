@@ -563,12 +563,12 @@ __device__ __forceinline__ void group_partials(const ForceArgs &A, unsigned g, d
 }
 
 // Configuration class of a group's first pass (0: more than 64 targets, more
-// than one pass or the 96-slot one; then 64, 48, 32 and 24 slots), in the
+// than one pass or the 96-slot one; then 64, 48, 32, 24 and 16 slots), in the
 // order the mixed kernel takes the groups.
 __device__ __forceinline__ int pass_class(unsigned n) {
-    return n > 64 ? 0 : n > 48 ? 1 : n > 32 ? 2 : n > 24 ? 3 : 4;
+    return n > 64 ? 0 : n > 48 ? 1 : n > 32 ? 2 : n > 24 ? 3 : n > 16 ? 4 : 5;
 }
-constexpr int kPassClasses = 5;
+constexpr int kPassClasses = 6;
 
 // Pass configuration for `rem` remaining targets: returns the slot count and
 // runs the matching instantiation.
@@ -577,6 +577,7 @@ __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, u
                                const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
                                unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
+    if (rem <= 16) { group_pass_f<2, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 16; }
     if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 24; }
     if (rem <= 32) { group_pass_f<2, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 32; }
     if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 48; }

@@ -103,7 +103,7 @@ def test_plummer4096_fp64_vs_oracle(ctx, order):
     assert np.percentile(rel_err(g["acc"], ad), 99) < 0.05
 
 
-@pytest.mark.parametrize("n_group", [8, 24, 40, 96, 200])
+@pytest.mark.parametrize("n_group", [8, 16, 24, 40, 96, 200])
 def test_mixed_every_pass_configuration(ctx, n_group):
     """Group sizes that select each pass configuration of the mixed kernel
     (24 to 96 slots, and several passes for groups above 96 targets), taken in
