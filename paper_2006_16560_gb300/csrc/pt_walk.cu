@@ -159,9 +159,23 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
                 else atomicOr(&A.st->flags, kErrListCap);
             }
             nc += __popc(amask);
-            // particles of opened leaves
-            const unsigned pincl = warp_incl_scan(pcount);
-            const unsigned ptot = __shfl_sync(0xffffffffu, pincl, 31);
+            // particles of opened leaves and children of opened internal nodes:
+            // one scan of both counts in 16-bit fields unless a depth-capped
+            // leaf could overflow its field
+            unsigned pincl, ptot, cincl, ctot;
+            if (__any_sync(0xffffffffu, pcount > 2047u)) {
+                pincl = warp_incl_scan(pcount);
+                ptot = __shfl_sync(0xffffffffu, pincl, 31);
+                cincl = warp_incl_scan(nch);
+                ctot = __shfl_sync(0xffffffffu, cincl, 31);
+            } else {
+                const unsigned both = warp_incl_scan(pcount | (nch << 16));
+                const unsigned tot = __shfl_sync(0xffffffffu, both, 31);
+                pincl = both & 0xffffu;
+                cincl = both >> 16;
+                ptot = tot & 0xffffu;
+                ctot = tot >> 16;
+            }
             if (ONEPASS && ptot && !dead && pbase + np + ptot > p_end)
                 dead = !grow_list(A.pp, A.cap_pp, &A.st->work[3], pbase, p_end, np, np + ptot,
                                   A.chunk_pp, &A.st->flags);
@@ -175,9 +189,6 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
                 }
             }
             np += ptot;
-            // children of opened internal nodes
-            const unsigned cincl = warp_incl_scan(nch);
-            const unsigned ctot = __shfl_sync(0xffffffffu, cincl, 31);
             if (sp + (int)ctot > cap) {
                 if (gsp + half > (int)A.spill_cap) {
                     overflow = true;
