@@ -306,7 +306,10 @@ int pt_tree_groups(pt_tree *tree, int64_t *g);
 
 /* Interaction lists of the last pt_longrange_force on this tree:
  * cell_off/pp_off (groups+1 int64), cells (node indices), pp (sorted
- * particle indices), in the order the force kernel consumed them. */
+ * particle indices), in the order the force kernel consumed them: a group's
+ * PP entries from leaves whose box lies within r_out of the group's box
+ * first, then those from leaves opened for the opening angle alone (every
+ * pair at least r_out apart, evaluated without the changeover test). */
 int pt_tree_lists(pt_tree *tree, int64_t *cell_off, uint32_t *cells,
                   int64_t *pp_off, uint32_t *pp);
 

@@ -120,7 +120,7 @@ struct pt_tree {
     Buf in_pos, in_mass;                                   // staging for host inputs
     Buf keys_in, vals_in, qbuf, skey, perm, sp64, spH, spL, sq;
     Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, tmp_a, tmp_b, lcp;
-    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gr_ord, gpart;
+    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gr_nf, gr_fo, gr_ord, gpart;
     Buf cells, pp;
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
@@ -166,7 +166,7 @@ struct pt_tree {
         Buf *all[] = {&status, &sets, &set_of, &bmin, &bmax, &n_dev, &in_pos, &in_mass, &keys_in,
                       &vals_in, &qbuf, &skey, &perm, &sp64, &spH, &spL, &sq, &nd_a, &nd_b, &nd_r,
                       &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
-                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gr_ord, &gpart, &cells, &pp, &pairs,
+                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gr_nf, &gr_fo, &gr_ord, &gpart, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
                       &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv, &orb_rnbf, &walk_spill,
@@ -279,6 +279,8 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->gr_b, N * 16));
     TRY(ensure(ctx, t->gr_nc, N * 4));
     TRY(ensure(ctx, t->gr_np, N * 4));
+    TRY(ensure(ctx, t->gr_nf, N * 4));
+    TRY(ensure(ctx, t->gr_fo, (N + 1) * 8));
     TRY(ensure(ctx, t->gr_ord, N * 4));
     TRY(ensure(ctx, t->gr_co, (N + 1) * 8));
     TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
@@ -448,6 +450,8 @@ WalkArgs walk_args(pt_tree *t) {
     A.gr_np = t->gr_np.as<unsigned>();
     A.gr_co = t->gr_co.as<unsigned long long>();
     A.gr_po = t->gr_po.as<unsigned long long>();
+    A.gr_nf = t->gr_nf.as<unsigned>();
+    A.gr_fo = t->gr_fo.as<unsigned long long>();
     A.cells = t->cells.as<unsigned>();
     A.pp = t->pp.as<unsigned>();
     A.cap_cells = t->cap_cells;
@@ -470,6 +474,8 @@ ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
     A.gr_np = t->gr_np.as<unsigned>();
     A.gr_co = t->gr_co.as<unsigned long long>();
     A.gr_po = t->gr_po.as<unsigned long long>();
+    A.gr_nf = t->gr_nf.as<unsigned>();
+    A.gr_fo = t->gr_fo.as<unsigned long long>();
     A.gr_ord = t->gr_ord.as<unsigned>();
     A.cells = t->cells.as<unsigned>();
     A.pp = t->pp.as<unsigned>();
@@ -546,7 +552,8 @@ int alloc_pairs(pt_tree *t, unsigned long long cap) {
 // walk's totals: chunks of about four groups' lists (about one move of a
 // partial list per four groups); arrays for the estimate plus a quarter (the
 // moves leave up to an eighth behind) and per active warp one and a half
-// chunks left unused at the end.
+// chunks left unused at the end (three for the PP array: a warp holds a near
+// and a far chunk).
 int size_onepass(pt_tree *t) {
     pt_ctx *ctx = t->ctx;
     const unsigned long long ngr = std::max<unsigned long long>(t->h.ngroups, 1);
@@ -559,7 +566,7 @@ int size_onepass(pt_tree *t) {
     const unsigned long long warps =
         std::min<unsigned long long>((unsigned long long)walk_warps(t->walk_stack), ngr);
     const unsigned long long need_c = t->est_cells + t->est_cells / 4 + warps * t->chunk_cells * 3 / 2;
-    const unsigned long long need_p = t->est_pp + t->est_pp / 4 + warps * t->chunk_pp * 3 / 2;
+    const unsigned long long need_p = t->est_pp + t->est_pp / 4 + warps * t->chunk_pp * 3;
     if (need_c > t->cap_cells || !t->cells.p) {
         t->cap_cells = need_c;
         TRY(ensure(ctx, t->cells, t->cap_cells * 4));
@@ -1511,16 +1518,23 @@ int pt_tree_groups(pt_tree *t, int64_t *g) {
 // Group-order CSR copy of one list kind; the device arrays hold each group's
 // entries contiguously at its offset (in group order after a two-pass walk,
 // in allocation order after a one-pass walk).
-static int lists_csr(pt_tree *t, const Buf &off_b, const Buf &cnt_b, const Buf &arr, int64_t *off_out,
-                     uint32_t *out) {
+// Per-group lists as CSR: each group's segment (off_b, cnt_b) followed by its
+// second segment (off2_b, cnt2_b) when given (the far PP entries).
+static int lists_csr(pt_tree *t, const Buf &off_b, const Buf &cnt_b, const Buf *off2_b, const Buf *cnt2_b,
+                     const Buf &arr, int64_t *off_out, uint32_t *out) {
     pt_ctx *ctx = t->ctx;
     const size_t ng = t->h.ngroups;
-    std::vector<unsigned long long> off(ng);
-    std::vector<unsigned> cnt(ng);
+    const int nseg = off2_b ? 2 : 1;
+    std::vector<unsigned long long> off(nseg * ng);
+    std::vector<unsigned> cnt(nseg * ng);
     CK(cudaMemcpy(off.data(), off_b.p, ng * 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(cnt.data(), cnt_b.p, ng * 4, cudaMemcpyDeviceToHost));
+    if (off2_b) {
+        CK(cudaMemcpy(off.data() + ng, off2_b->p, ng * 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(cnt.data() + ng, cnt2_b->p, ng * 4, cudaMemcpyDeviceToHost));
+    }
     unsigned long long extent = 0, total = 0;
-    for (size_t k = 0; k < ng; k++) {
+    for (size_t k = 0; k < nseg * ng; k++) {
         extent = std::max(extent, off[k] + cnt[k]);
         total += cnt[k];
     }
@@ -1528,7 +1542,7 @@ static int lists_csr(pt_tree *t, const Buf &off_b, const Buf &cnt_b, const Buf &
         int64_t acc = 0;
         for (size_t k = 0; k < ng; k++) {
             off_out[k] = acc;
-            acc += cnt[k];
+            for (int q = 0; q < nseg; q++) acc += cnt[q * ng + k];
         }
         off_out[ng] = acc;
     }
@@ -1537,15 +1551,16 @@ static int lists_csr(pt_tree *t, const Buf &off_b, const Buf &cnt_b, const Buf &
         CK(cudaMemcpy(all.data(), arr.p, extent * 4, cudaMemcpyDeviceToHost));
         size_t at = 0;
         for (size_t k = 0; k < ng; k++)
-            for (unsigned e = 0; e < cnt[k]; e++) out[at++] = all[off[k] + e];
+            for (int q = 0; q < nseg; q++)
+                for (unsigned e = 0; e < cnt[q * ng + k]; e++) out[at++] = all[off[q * ng + k] + e];
     }
     return PT_OK;
 }
 
 int pt_tree_lists(pt_tree *t, int64_t *cell_off, uint32_t *cells, int64_t *pp_off, uint32_t *pp) {
     if (!t || !t->lists_valid) return PT_ERR_ARG;
-    TRY(lists_csr(t, t->gr_co, t->gr_nc, t->cells, cell_off, cells));
-    TRY(lists_csr(t, t->gr_po, t->gr_np, t->pp, pp_off, pp));
+    TRY(lists_csr(t, t->gr_co, t->gr_nc, nullptr, nullptr, t->cells, cell_off, cells));
+    TRY(lists_csr(t, t->gr_po, t->gr_np, &t->gr_fo, &t->gr_nf, t->pp, pp_off, pp));
     return PT_OK;
 }
 

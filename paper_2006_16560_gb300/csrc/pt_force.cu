@@ -321,6 +321,31 @@ __device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 
     }
 }
 
+// Far PP entries (the walk guarantees every pair at least r_out apart, so
+// K = W = 0): plain Newtonian pairs, two list entries per f32x2 operation,
+// with no per-iteration test.
+template <int NI, int J>
+__device__ __forceinline__ void pp_tile_far(const ulonglong2 (*sQ)[kJ / 2], int s, int npairs,
+                                            const f2x (&OX)[NI], const f2x (&OY)[NI],
+                                            const f2x (&OZ)[NI], f2x (&PA)[NI][4]) {
+#pragma unroll kUnrollPP
+    for (int P = s; P < npairs; P += J) {
+        const ulonglong2 q0 = sQ[0][P], q1 = sQ[1][P];
+#pragma unroll
+        for (int k = 0; k < NI; k++) {
+            const f2x dx = sub2(q0.x, OX[k]), dy = sub2(q0.y, OY[k]), dz = sub2(q1.x, OZ[k]);
+            const float2 r2 = up2(fma2(dz, dz, fma2(dy, dy, mul2(dx, dx))));
+            const f2x rinv = pk2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const f2x mr = mul2(q1.y, rinv);
+            const f2x mr3 = mul2(mr, mul2(rinv, rinv));
+            PA[k][0] = fma2(mr3, dx, PA[k][0]);
+            PA[k][1] = fma2(mr3, dy, PA[k][1]);
+            PA[k][2] = fma2(mr3, dz, PA[k][2]);
+            PA[k][3] = add2(PA[k][3], mr);
+        }
+    }
+}
+
 // Per-lane float-float accumulators live in shared memory (touched once per
 // tile), which keeps their 8 NI registers free for the inner loops.
 
@@ -445,59 +470,67 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
 #pragma unroll
         for (int k = 0; k < NI; k++) nvalid += valid[k] ? 1 : 0;
         unsigned n_full = 0, n_fast = 0;
-        const unsigned np = A.gr_np[g];
-        const unsigned long long po = A.gr_po[g];
+        const unsigned ntarg = min((unsigned)(NI * L), gr.y - i0);   // targets of this pass
         constexpr int R = 4 * (kJ / 2);                 // floats per row of the pair layout
         float *rows = reinterpret_cast<float *>(sP[w]);
-        for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
-            const int cnt = (int)min((unsigned)kJ, np - t);
-            const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
+        // the near segment (changeover test per iteration), then the far one
+        for (int seg = 0; seg < 2; seg++) {
+            const unsigned np = seg == 0 ? A.gr_np[g] : A.gr_nf[g];
+            const unsigned long long po = seg == 0 ? A.gr_po[g] : A.gr_fo[g];
+            for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
+                const int cnt = (int)min((unsigned)kJ, np - t);
+                const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
 #pragma unroll
-            for (int h = 0; h < kJ / 32; h++) {
-                const int e = lane + 32 * h;
-                if (e < cnt2) {
-                    const int m = e / (2 * J), r = e - m * 2 * J;
-                    const int half = r >= J ? 1 : 0;
-                    const int P = m * J + r - half * J;
-                    float ox = 1e15f, oy = 1e15f, oz = 1e15f, ms = 0.0f, wj = 1.0f;   // padding: massless, far away
-                    unsigned p = 0xffffffffu;
-                    if (e < cnt) {
-                        p = A.pp[po + t + e];
-                        const float4 H = A.spH[p], L = A.spL[p];
-                        ox = (H.x - Hg.x) + (L.x - Lg.x);
-                        oy = (H.y - Hg.y) + (L.y - Lg.y);
-                        oz = (H.z - Hg.z) + (L.z - Lg.z);
-                        ms = H.w;
-                        wj = L.w;
+                for (int h = 0; h < kJ / 32; h++) {
+                    const int e = lane + 32 * h;
+                    if (e < cnt2) {
+                        const int m = e / (2 * J), r = e - m * 2 * J;
+                        const int half = r >= J ? 1 : 0;
+                        const int P = m * J + r - half * J;
+                        float ox = 1e15f, oy = 1e15f, oz = 1e15f, ms = 0.0f, wj = 1.0f;   // padding: massless, far away
+                        unsigned p = 0xffffffffu;
+                        if (e < cnt) {
+                            p = A.pp[po + t + e];
+                            const float4 H = A.spH[p], L = A.spL[p];
+                            ox = (H.x - Hg.x) + (L.x - Lg.x);
+                            oy = (H.y - Hg.y) + (L.y - Lg.y);
+                            oz = (H.z - Hg.z) + (L.z - Lg.z);
+                            ms = H.w;
+                            wj = L.w;
+                        }
+                        float *b = rows + 4 * P + half;
+                        b[0] = ox;
+                        b[2] = oy;
+                        b[R] = oz;
+                        b[R + 2] = ms;
+                        if (MD) b[2 * R] = wj;
+                        sI[w][2 * P + half] = p;
                     }
-                    float *b = rows + 4 * P + half;
-                    b[0] = ox;
-                    b[2] = oy;
-                    b[R] = oz;
-                    b[R + 2] = ms;
-                    if (MD) b[2 * R] = wj;
-                    sI[w][2 * P + half] = p;
                 }
+                __syncwarp();
+                if (seg == 1) {
+                    pp_tile_far<NI, J>(sP[w], s, cnt2 / 2, OX, OY, OZ, PA);
+                    if (lane == 0) n_fast += (unsigned)cnt * ntarg;
+                } else if (NB && A.want_nb) {
+                    pp_tile_f2<NI, J, true, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, OX, OY, OZ,
+                                                invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
+                } else {
+                    pp_tile_f2<NI, J, false, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, OX, OY, OZ,
+                                                 invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < NI; k++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const float2 v = up2(PA[k][c]);
+                        float2 a = acc[k][c][lane];
+                        ff_add(a.x, a.y, (v.x + v.y) + pa[k][c]);
+                        acc[k][c][lane] = a;
+                        PA[k][c] = 0ull;
+                        pa[k][c] = 0.0f;
+                    }
             }
-            __syncwarp();
-            if (NB && A.want_nb)
-                pp_tile_f2<NI, J, true, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, OX, OY, OZ,
-                                            invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
-            else
-                pp_tile_f2<NI, J, false, MD>(A, sP[w], sI[w], s, cnt2 / 2, cnt, C, OX, OY, OZ,
-                                             invs_t, pid, valid, nvalid, rout2, rout, PA, pa, n_full, n_fast);
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < NI; k++)
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const float2 v = up2(PA[k][c]);
-                    float2 a = acc[k][c][lane];
-                    ff_add(a.x, a.y, (v.x + v.y) + pa[k][c]);
-                    acc[k][c][lane] = a;
-                    PA[k][c] = 0ull;
-                    pa[k][c] = 0.0f;
-                }
         }
         n_full = warp_sum(n_full);
         n_fast = warp_sum(n_fast);
@@ -765,26 +798,29 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
         cells_tile_d<NI, ORDER>(sA[w], sB[w], sC[w], cnt, xx, xy, xz, pa);
         __syncwarp();
     }
-    const unsigned np = A.gr_np[g];
-    const unsigned long long po = A.gr_po[g];
-    for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
-        const int cnt = (int)min((unsigned)kJ, np - t);
+    // near PP segment, then the far one (no neighbour candidates there)
+    for (int seg = 0; seg < 2; seg++) {
+        const unsigned np = seg == 0 ? A.gr_np[g] : A.gr_nf[g];
+        const unsigned long long po = seg == 0 ? A.gr_po[g] : A.gr_fo[g];
+        for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
+            const int cnt = (int)min((unsigned)kJ, np - t);
 #pragma unroll
-        for (int h = 0; h < kJ / 32; h++) {
-            const int e = lane + 32 * h;
-            if (e < cnt) {
-                const unsigned p = A.pp[po + t + e];
-                sA[w][e] = A.sp64[p];
-                sI[w][e] = p;
-                if (MD) sS[w][e] = A.ssc[p];
+            for (int h = 0; h < kJ / 32; h++) {
+                const int e = lane + 32 * h;
+                if (e < cnt) {
+                    const unsigned p = A.pp[po + t + e];
+                    sA[w][e] = A.sp64[p];
+                    sI[w][e] = p;
+                    if (MD) sS[w][e] = A.ssc[p];
+                }
             }
+            __syncwarp();
+            if (NB && A.want_nb && seg == 0)
+                pp_tile_d<NI, true, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
+            else
+                pp_tile_d<NI, false, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
+            __syncwarp();
         }
-        __syncwarp();
-        if (NB && A.want_nb)
-            pp_tile_d<NI, true, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
-        else
-            pp_tile_d<NI, false, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
-        __syncwarp();
     }
 #pragma unroll
     for (int s = 0; s < 2; s++)
@@ -834,7 +870,7 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
 
 __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, const uint2 *gr_r,
                                                        const unsigned *gr_nc, const unsigned *gr_np,
-                                                       Status *st) {
+                                                       const unsigned *gr_nf, Status *st) {
     // fixed reduction order (thread strides, then butterflies over the warp
     // and over the warps' sums): the same sums every run
     __shared__ double se[32][4];
@@ -847,7 +883,7 @@ __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, con
         e[0] += p.x; e[1] += p.y; e[2] += p.z; e[3] += p.w;
         const unsigned long long n = gr_r[g].y;
         ci += n * gr_nc[g];
-        pi += n * gr_np[g];
+        pi += n * (gr_np[g] + gr_nf[g]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -979,7 +1015,7 @@ int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
 }
 
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st) {
-    k_force_reduce<<<1, 1024, 0, st>>>(A.gpart, A.gr_r, A.gr_nc, A.gr_np, A.st);
+    k_force_reduce<<<1, 1024, 0, st>>>(A.gpart, A.gr_r, A.gr_nc, A.gr_np, A.gr_nf, A.st);
     return 1;
 }
 

@@ -14,7 +14,9 @@
 //              nd_c  double4 (com xyz, M);  nd_q double4 x 2 (Q xx yy zz xy, xz yz T-trace 0)
 //              nd_f  float4 x 4 (hi(com) M | lo(com) Qxx | Qyy Qzz Qxy Qxz | Qyz 0 0 0)
 //   groups     gr_r  uint2 (begin, count); gr_a uint4 (qmin, set); gr_b uint4 (qmax, root)
-//              gr_nc, gr_np u32 list lengths; gr_co, gr_po u64 list offsets
+//              gr_nc, gr_np u32 list lengths; gr_co, gr_po u64 list offsets;
+//              gr_nf u32, gr_fo u64: far PP segment (leaves opened for the
+//              opening angle only, every pair at least r_out apart)
 #pragma once
 
 #include <cuda_runtime.h>

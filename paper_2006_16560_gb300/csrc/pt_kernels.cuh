@@ -68,6 +68,10 @@ struct WalkArgs {
     WalkParams wp;
     unsigned *gr_nc, *gr_np;
     unsigned long long *gr_co, *gr_po;   // ngroups + 1
+    // PP entries of leaves whose box is at least r_out from the group's box
+    // (opened for the opening angle only: no pair within r_out), kept apart
+    unsigned *gr_nf;
+    unsigned long long *gr_fo;
     unsigned *cells, *pp;
     unsigned long long cap_cells, cap_pp;
     unsigned long long chunk_cells, chunk_pp;   // one-pass allocation granules (entries)
@@ -83,6 +87,8 @@ struct ForceArgs {
     const uint4 *gr_a;
     const unsigned *gr_nc, *gr_np;
     const unsigned long long *gr_co, *gr_po;
+    const unsigned *gr_nf;           // far PP segment (no pair within r_out)
+    const unsigned long long *gr_fo;
     unsigned *gr_ord;                // mixed kernel: group processing order (written per launch)
     const unsigned *cells, *pp;
     const double4 *sp64;

@@ -5,7 +5,11 @@
 // stack, tests them in parallel and emits accepted cells, opened leaves'
 // particles and opened internal nodes' children with warp prefix sums.  All
 // tests are exact integer arithmetic on the grid boxes (see pt.h), so the
-// lists are identical to the CPU oracle's.  Two ways to place the lists:
+// lists are identical to the CPU oracle's.  A leaf opened for the opening
+// angle alone (its box at least r_out from the group's box, so no pair can be
+// within r_out) goes to the group's far PP segment, every other opened leaf
+// to the near one; the force kernel skips the changeover test on the far
+// segment.  Two ways to place the lists:
 // - two passes: a counting pass sizes every group's lists, an exclusive scan
 //   places them, and a filling pass writes them (both visit nodes in the
 //   same order); used when no size estimate exists, and by batches;
@@ -65,9 +69,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
     unsigned *gstk = A.spill + (size_t)(blockIdx.x * kWalkWarps + w) * A.spill_cap;
     const int half = cap / 2;            // >= 32 x 8, the most one step can push
     int max_sp = 0;
-    // one pass: the warp's current chunks [.., c_end) and [.., p_end) and their
-    // first free entries (uniform across the warp)
-    unsigned long long c_free = 0, c_end = 0, p_free = 0, p_end = 0;
+    // one pass: the warp's current chunks [.., c_end), [.., p_end) (near PP)
+    // and [.., f_end) (far PP) and their first free entries (uniform across
+    // the warp)
+    unsigned long long c_free = 0, c_end = 0, p_free = 0, p_end = 0, f_free = 0, f_end = 0;
     bool dead = false;          // list array exhausted: keep walking, write nothing
     for (;;) {
         unsigned g = 0;
@@ -78,15 +83,19 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
         const long long r2thr = MD ? A.gr_thr[g] : A.sets[ga.w].r2thr;
         const int glo[3] = {2 * (int)ga.x, 2 * (int)ga.y, 2 * (int)ga.z};
         const int ghi[3] = {2 * (int)gb.x + 2, 2 * (int)gb.y + 2, 2 * (int)gb.z + 2};
-        unsigned long long cbase = 0, pbase = 0;
+        unsigned long long cbase = 0, pbase = 0, fbase = 0;
         if (ONEPASS) {
             cbase = c_free;
             pbase = p_free;
+            fbase = f_free;
         } else if (FILL) {
+            // the counting pass left the total PP count in gr_np: the group's
+            // segment holds the near entries, then the far ones
             cbase = A.gr_co[g];
             pbase = A.gr_po[g];
+            fbase = pbase + (A.gr_np[g] - A.gr_nf[g]);
         }
-        unsigned nc = 0, np = 0;
+        unsigned nc = 0, nn = 0, nf = 0;
         if (lane == 0) stk[0] = gb.w;      // root of the group's set
         __syncwarp();
         int sp = 1;
@@ -112,7 +121,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
             const bool valid = (int)lane < k;
             const unsigned v = valid ? stk[sp + lane] : 0u;
             __syncwarp();
-            bool accept = false, leaf = false;
+            bool accept = false, leaf = false, pfar = false;
             unsigned nch = 0, first = 0, pcount = 0, pbegin = 0;
             if (valid) {
                 const uint4 a = A.nd_a[v], b = A.nd_b[v];
@@ -142,6 +151,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
                         const uint2 r = A.nd_r[v];
                         pbegin = r.x;
                         pcount = r.y;
+                        pfar = gap2 >= thr;      // opened for the opening angle only
                     } else {
                         nch = meta_nchild(a.w);
                         first = b.w;
@@ -159,36 +169,46 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
                 else atomicOr(&A.st->flags, kErrListCap);
             }
             nc += __popc(amask);
-            // particles of opened leaves and children of opened internal nodes:
-            // one scan of both counts in 16-bit fields unless a depth-capped
-            // leaf could overflow its field
-            unsigned pincl, ptot, cincl, ctot;
-            if (__any_sync(0xffffffffu, pcount > 2047u)) {
-                pincl = warp_incl_scan(pcount);
-                ptot = __shfl_sync(0xffffffffu, pincl, 31);
+            // particles of opened leaves (near and far) and children of opened
+            // internal nodes: one scan of the three counts in 11-, 11- and
+            // 10-bit fields (warp sums below 2^11 when no leaf holds more
+            // than 63 particles), else three scans
+            const unsigned pn = pfar ? 0u : pcount, pf = pfar ? pcount : 0u;
+            unsigned nincl, ntot, fincl, ftot, cincl, ctot;
+            if (__any_sync(0xffffffffu, pcount > 63u)) {
+                nincl = warp_incl_scan(pn);
+                ntot = __shfl_sync(0xffffffffu, nincl, 31);
+                fincl = warp_incl_scan(pf);
+                ftot = __shfl_sync(0xffffffffu, fincl, 31);
                 cincl = warp_incl_scan(nch);
                 ctot = __shfl_sync(0xffffffffu, cincl, 31);
             } else {
-                const unsigned both = warp_incl_scan(pcount | (nch << 16));
-                const unsigned tot = __shfl_sync(0xffffffffu, both, 31);
-                pincl = both & 0xffffu;
-                cincl = both >> 16;
-                ptot = tot & 0xffffu;
-                ctot = tot >> 16;
+                const unsigned all = warp_incl_scan(pn | (pf << 11) | (nch << 22));
+                const unsigned tot = __shfl_sync(0xffffffffu, all, 31);
+                nincl = all & 0x7ffu;
+                fincl = (all >> 11) & 0x7ffu;
+                cincl = all >> 22;
+                ntot = tot & 0x7ffu;
+                ftot = (tot >> 11) & 0x7ffu;
+                ctot = tot >> 22;
             }
-            if (ONEPASS && ptot && !dead && pbase + np + ptot > p_end)
-                dead = !grow_list(A.pp, A.cap_pp, &A.st->work[3], pbase, p_end, np, np + ptot,
+            if (ONEPASS && ntot && !dead && pbase + nn + ntot > p_end)
+                dead = !grow_list(A.pp, A.cap_pp, &A.st->work[3], pbase, p_end, nn, nn + ntot,
                                   A.chunk_pp, &A.st->flags);
-            if (FILL && ptot && !dead) {
+            if (ONEPASS && ftot && !dead && fbase + nf + ftot > f_end)
+                dead = !grow_list(A.pp, A.cap_pp, &A.st->work[3], fbase, f_end, nf, nf + ftot,
+                                  A.chunk_pp, &A.st->flags);
+            if (FILL && (ntot | ftot) && !dead) {
                 // every lane writes its own leaf's particle range at its offset
-                const unsigned long long at = pbase + np + (pincl - pcount);
+                const unsigned long long at = pfar ? fbase + nf + (fincl - pf) : pbase + nn + (nincl - pn);
                 if (at + pcount <= A.cap_pp) {
                     for (unsigned e = 0; e < pcount; e++) A.pp[at + e] = pbegin + e;
                 } else if (pcount) {
                     atomicOr(&A.st->flags, kErrListCap);
                 }
             }
-            np += ptot;
+            nn += ntot;
+            nf += ftot;
             if (sp + (int)ctot > cap) {
                 if (gsp + half > (int)A.spill_cap) {
                     overflow = true;
@@ -215,19 +235,28 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
         }
         if (overflow && lane == 0) atomicOr(&A.st->flags, kErrStack);
         if ((!FILL || ONEPASS) && lane == 0) atomicMax(&A.st->max_stack, (unsigned)max_sp);
-        if ((!FILL || ONEPASS) && lane == 0) {
-            A.gr_nc[g] = nc;
-            A.gr_np[g] = np;
+        if (lane == 0) {
+            if (!FILL) {                 // counting pass: gr_np holds the total for the scan
+                A.gr_nc[g] = nc;
+                A.gr_np[g] = nn + nf;
+                A.gr_nf[g] = nf;
+            } else {
+                A.gr_np[g] = nn;
+                A.gr_nf[g] = nf;
+                A.gr_fo[g] = fbase;
+                if (ONEPASS) A.gr_nc[g] = nc;
+            }
         }
         if (ONEPASS) {
             if (lane == 0) {
                 A.gr_co[g] = cbase;
                 A.gr_po[g] = pbase;
                 atomicAdd(&A.st->cell_total, (unsigned long long)nc);
-                atomicAdd(&A.st->pp_total, (unsigned long long)np);
+                atomicAdd(&A.st->pp_total, (unsigned long long)(nn + nf));
             }
             c_free = cbase + nc;
-            p_free = pbase + np;
+            p_free = pbase + nn;
+            f_free = fbase + nf;
         }
         __syncwarp();
     }
