@@ -169,6 +169,33 @@ def test_mixed_companions_across_the_changeover(ctx):
     assert e.max() <= MIXED_MAX
 
 
+@pytest.mark.parametrize("spacing", [0.9999, 1.0001, 1.5])
+def test_lattice_at_the_r_out_boundary(ctx, spacing):
+    """A jittered cubic lattice whose spacing is just inside, just outside or
+    well outside r_out: the walk puts every leaf that may hold a pair within
+    r_out in a group's near PP segment and evaluates the rest without the
+    changeover test, so the neighbour sets must equal brute force and both
+    precisions must agree with the oracle tree."""
+    r_out = 0.05
+    k = 14
+    g1 = (np.arange(k) - k / 2) * spacing * r_out
+    pos = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    pos = pos + np.random.default_rng(3).normal(scale=1e-7, size=pos.shape)
+    mass = np.full(len(pos), 1.0 / len(pos))
+    T = oracle.Tree(pos, mass, 8, 64)
+    a, phi, _ = T.force(0.5, 0.1 * r_out, r_out, order=2)
+    for prec in (B.PT_FP64, B.PT_MIXED):
+        g = run_gpu(ctx, pos, mass, c1_params(order=2, precision=prec, r_out=r_out, r_in=0.1 * r_out))
+        check_neighbours(g, pos, r_out)
+        # the lattice's pulls cancel near its centre: errors relative to the
+        # median force
+        e = np.linalg.norm(g["acc"] - a, axis=1) / np.median(np.linalg.norm(a, axis=1))
+        if prec == B.PT_FP64:
+            assert e.max() <= FP64_TOL
+        else:
+            assert np.percentile(e, 99) <= MIXED_P99 and e.max() <= MIXED_MAX
+
+
 def test_theta0_equals_direct(ctx):
     d = inputs.plummer(1500, 5, masses="kroupa")
     p = c1_params(theta=0.0, order=2)
