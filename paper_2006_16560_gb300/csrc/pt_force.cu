@@ -939,7 +939,12 @@ __global__ void __launch_bounds__(1024) k_group_order(const uint2 *gr_r, unsigne
     unsigned c[kPassClasses], x[kPassClasses];
 #pragma unroll
     for (int k = 0; k < kPassClasses; k++) c[k] = 0;
-    for (unsigned g = b; g < e; g++) c[pass_class(gr_r[g].y)]++;
+#pragma unroll 4
+    for (unsigned g = b; g < e; g++) {
+        const int k = pass_class(gr_r[g].y);
+#pragma unroll
+        for (int j = 0; j < kPassClasses; j++) c[j] += j == k ? 1u : 0u;   // stays in registers
+    }
 #pragma unroll
     for (int k = 0; k < kPassClasses; k++) {       // inclusive scan within the warp
         unsigned v = c[k];

@@ -55,7 +55,8 @@ __device__ __forceinline__ bool grow_list(unsigned *arr, unsigned long long cap,
 }
 
 template <bool FILL, bool MD, bool ONEPASS>
-__global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs A) {
+// 14 blocks per SM: the most the small stacks' shared memory allows (32 registers)
+__global__ void __launch_bounds__(kWalkThreads, 14) k_walk(WalkArgs A) {
     extern __shared__ unsigned stack_mem[];      // kWalkWarps x A.stack_cap entries
     __shared__ long long ithr[kLevels];
     if (threadIdx.x < kLevels) ithr[threadIdx.x] = A.wp.ithr[threadIdx.x];
