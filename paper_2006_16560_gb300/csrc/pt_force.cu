@@ -754,6 +754,28 @@ __device__ __forceinline__ void pp_tile_d(const ForceArgs &A, const double4 *sP,
     }
 }
 
+// Far PP entries in float64 (every pair at least r_out apart: K = W = 0):
+// plain Newtonian pairs.
+template <int NI>
+__device__ __forceinline__ void pp_tile_d_far(const double4 *sP, int cnt, const double (&xx)[2],
+                                              const double (&xy)[2], const double (&xz)[2],
+                                              double (&pa)[2][4]) {
+    for (int j = 0; j < cnt; j++) {
+        const double4 P = sP[j];
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+            const double dx = P.x - xx[s], dy = P.y - xy[s], dz = P.z - xz[s];
+            const double rinv = rsqrt(fma(dz, dz, fma(dy, dy, dx * dx)));
+            const double mr = P.w * rinv;
+            const double fk = mr * (rinv * rinv);
+            pa[s][0] = fma(fk, dx, pa[s][0]);
+            pa[s][1] = fma(fk, dy, pa[s][1]);
+            pa[s][2] = fma(fk, dz, pa[s][2]);
+            pa[s][3] += mr;
+        }
+    }
+}
+
 template <int NI, int ORDER, bool NB, bool MD>
 __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                              const Chg &C, double4 (*sA)[kJ], double4 (*sB)[kJ],
@@ -798,7 +820,8 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
         cells_tile_d<NI, ORDER>(sA[w], sB[w], sC[w], cnt, xx, xy, xz, pa);
         __syncwarp();
     }
-    // near PP segment, then the far one (no neighbour candidates there)
+    // near PP segment (changeover and neighbour test per pair), then the far
+    // one (plain Newtonian pairs)
     for (int seg = 0; seg < 2; seg++) {
         const unsigned np = seg == 0 ? A.gr_np[g] : A.gr_nf[g];
         const unsigned long long po = seg == 0 ? A.gr_po[g] : A.gr_fo[g];
@@ -815,7 +838,9 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
                 }
             }
             __syncwarp();
-            if (NB && A.want_nb && seg == 0)
+            if (seg == 1)
+                pp_tile_d_far<NI>(sA[w], cnt, xx, xy, xz, pa);
+            else if (NB && A.want_nb)
                 pp_tile_d<NI, true, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
             else
                 pp_tile_d<NI, false, MD>(A, sA[w], sI[w], sS[w], cnt, C, xx, xy, xz, st, pid, valid, pa);
