@@ -23,6 +23,10 @@ struct pt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+    // private stream that copies host results while the stream's last
+    // kernels (energy sums, neighbour CSR) run, and the event it waits on
+    cudaStream_t out_stream = nullptr;
+    cudaEvent_t ev_out = nullptr;
     char err[512] = {0};
     Status *h_status = nullptr;      // pinned
     cudaEvent_t ev[8] = {};
@@ -599,9 +603,20 @@ int on_walk_overflow(pt_tree *t) {
 // Walk + force (+ neighbour CSR) on a built tree; acc/pot are device
 // pointers in input order.  On return t->h holds the status.
 int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long long nb_cap_hint,
-              float *ms) {
+              float *ms, double *acc_host = nullptr, double *pot_host = nullptr) {
     pt_ctx *ctx = t->ctx;
     cudaStream_t st = ctx->stream;
+    // host outputs: copied on the private stream as soon as the force kernel
+    // has written them, while the energy sums and the neighbour CSR run (a
+    // retried attempt copies again after its own force kernel)
+    auto copy_out = [&]() -> int {
+        if (!acc_host && !pot_host) return PT_OK;
+        CK(cudaEventRecord(ctx->ev_out, st));
+        CK(cudaStreamWaitEvent(ctx->out_stream, ctx->ev_out, 0));
+        if (acc_host) CK(cudaMemcpyAsync(acc_host, acc, (size_t)t->n * 24, cudaMemcpyDeviceToHost, ctx->out_stream));
+        if (pot_host) CK(cudaMemcpyAsync(pot_host, pot, (size_t)t->n * 8, cudaMemcpyDeviceToHost, ctx->out_stream));
+        return PT_OK;
+    };
     Status *dS = t->status.as<Status>();
     TRY(ensure(ctx, t->nb_off, ((size_t)t->n + 1) * 8));
     TRY(alloc_pairs(t, std::max<unsigned long long>(nb_cap_hint, 2ull * t->n)));
@@ -621,6 +636,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
             ForceArgs F = force_args(t, acc, pot, want_nb);
             nk += force_launch(F, t->prm.precision, st);
             CK(cudaEventRecord(ctx->ev[4], st));
+            TRY(copy_out());
             nk += force_reduce_launch(F, st);
             if (want_nb) nk += nb_launch(nb_args(t), st);
             t->launches_force = nk;
@@ -668,6 +684,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         ForceArgs F = force_args(t, acc, pot, want_nb);
         nk += force_launch(F, t->prm.precision, st);
         CK(cudaEventRecord(ctx->ev[4], st));
+        TRY(copy_out());
         nk += force_reduce_launch(F, st);
         if (want_nb) nk += nb_launch(nb_args(t), st);
         t->launches_force = nk;
@@ -1144,6 +1161,8 @@ int pt_ctx_create(pt_ctx **out, int device, void *stream) {
     }
     for (auto &e : ctx->ev) cudaEventCreate(&e);
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->out_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         walk_init() != 0) {
         (void)cudaGetLastError();
         pt_ctx_destroy(ctx);
@@ -1161,6 +1180,8 @@ int pt_ctx_destroy(pt_ctx *ctx) {
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
     return PT_OK;
@@ -1263,10 +1284,14 @@ int pt_longrange_force(pt_ctx *ctx, pt_tree *t, double *acc, double *pot, int64_
     }
     const bool want_nb = nb_offsets != nullptr;
     float ms[3] = {0, 0, 0};
-    TRY(run_force(t, a, p, want_nb, (unsigned long long)nb_capacity, ms));
+    const int rf = run_force(t, a, p, want_nb, (unsigned long long)nb_capacity, ms, dacc ? nullptr : acc,
+                             dpot ? nullptr : pot);
+    // no copy into the caller's host buffers may outlive the call
+    if (rf != PT_OK) {
+        if (!dacc || !dpot) cudaStreamSynchronize(ctx->out_stream);
+        return rf;
+    }
     cudaStream_t st = ctx->stream;
-    if (!dacc) CK(cudaMemcpyAsync(acc, a, n * 24, cudaMemcpyDeviceToHost, st));
-    if (!dpot) CK(cudaMemcpyAsync(pot, p, n * 8, cudaMemcpyDeviceToHost, st));
     int rc = PT_OK;
     const unsigned long long npairs = t->h.npairs;
     if (nb_total) *nb_total = want_nb ? (int64_t)npairs : 0;
@@ -1284,6 +1309,7 @@ int pt_longrange_force(pt_ctx *ctx, pt_tree *t, double *acc, double *pot, int64_
         }
     }
     CK(cudaStreamSynchronize(st));
+    if (!dacc || !dpot) CK(cudaStreamSynchronize(ctx->out_stream));
     fill_stats(t, stats, ms);
     return rc;
 }
