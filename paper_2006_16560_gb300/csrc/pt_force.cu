@@ -2,11 +2,15 @@
 // extraction, the energy / momentum sums and the neighbour CSR.
 //
 // One CTA (4 warps) evaluates one walk group at a time, taking groups from
-// an atomic work counter.  Every warp holds all of the group's targets (one
-// or two per lane) and streams its own quarter of the group's lists: it
+// an atomic work counter in the order k_group_order writes (largest pass
+// configuration first).  Every warp holds all of the group's targets (two or
+// three per lane) and streams its own quarter of the group's lists: it
 // gathers 64 list entries into shared memory, then every lane reads them by
 // broadcast and accumulates.  The four warps' partial sums are reduced in
-// float64 at the end of the group.
+// float64 at the end of the group.  A group has one cell list and two PP
+// segments: near (leaves within r_out of the group's box: changeover and
+// neighbour tests) and far (every pair at least r_out apart: plain
+// Newtonian pairs).
 //
 // Pair force (Sec. 5.1, Eq. 11; Sec. 6.1, Eqs. 15-17), for x_ij > 0:
 //   a_i += m_j (x_j - x_i) (1 - K(x)) / r^3,  P_i += m_j (1 - W(x)) / r
