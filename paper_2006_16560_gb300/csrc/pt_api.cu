@@ -124,7 +124,7 @@ struct pt_tree {
     Buf in_pos, in_mass;                                   // staging for host inputs
     Buf keys_in, vals_in, qbuf, skey, perm, sp64, spH, spL, sq;
     Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, tmp_a, tmp_b, lcp;
-    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gr_nf, gr_fo, gr_ord, gpart;
+    Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gr_nf, gr_fo, gr_ord, gpart, red_part;
     Buf cells, pp;
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
     Buf sort_k2, sort_v2, sort_counts, scan_sums;
@@ -170,7 +170,7 @@ struct pt_tree {
         Buf *all[] = {&status, &sets, &set_of, &bmin, &bmax, &n_dev, &in_pos, &in_mass, &keys_in,
                       &vals_in, &qbuf, &skey, &perm, &sp64, &spH, &spL, &sq, &nd_a, &nd_b, &nd_r,
                       &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
-                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gr_nf, &gr_fo, &gr_ord, &gpart, &cells, &pp, &pairs,
+                      &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gr_nf, &gr_fo, &gr_ord, &gpart, &red_part, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
                       &in_scale, &scale_buf, &set_mean, &ssc, &nd_thr, &gr_thr, &orb_vel, &orb_sv, &orb_rnbf, &walk_spill,
@@ -289,6 +289,7 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->gr_co, (N + 1) * 8));
     TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
     TRY(ensure(ctx, t->gpart, N * 32));
+    TRY(ensure(ctx, t->red_part, 256 * 48));     // reduction partials (152 blocks used)
     TRY(ensure(ctx, t->ssc, N * 8));
     TRY(ensure(ctx, t->set_mean, S * 8));
     if (t->prm.mass_dependent) {
@@ -501,6 +502,8 @@ ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
     A.pairs = t->pairs.as<uint2>();
     A.pair_cap = t->cap_pairs;
     A.gpart = t->gpart.as<double4>();
+    A.red_e = t->red_part.as<double4>();
+    A.red_c = reinterpret_cast<unsigned long long *>(t->red_part.as<double4>() + 256);
     A.st = t->status.as<Status>();
     return A;
 }

@@ -897,19 +897,27 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
 // Totals over groups (fixed-order reduction, one block)
 // ===========================================================================
 
-__global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, const uint2 *gr_r,
-                                                       const unsigned *gr_nc, const unsigned *gr_np,
-                                                       const unsigned *gr_nf, Status *st) {
-    // fixed reduction order (thread strides, then butterflies over the warp
-    // and over the warps' sums): the same sums every run
-    __shared__ double se[32][4];
-    __shared__ unsigned long long si[32][2];
+// Energy / momentum sums and interaction counts over the groups, in two
+// launches with a fixed reduction order (the same sums every run): each of
+// kRedBlocks blocks reduces a contiguous range of groups, then one warp adds
+// the blocks' partials.
+constexpr int kRedBlocks = 152;
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads) k_force_partials(const double4 *gpart, const uint2 *gr_r,
+                                                                const unsigned *gr_nc, const unsigned *gr_np,
+                                                                const unsigned *gr_nf, double4 *red_e,
+                                                                unsigned long long *red_c, const Status *st) {
+    __shared__ double se[kRedThreads / 32][4];
+    __shared__ unsigned long long si[kRedThreads / 32][2];
     const unsigned ng = st->ngroups, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double e[4] = {0, 0, 0, 0};
+    const unsigned per = (ng + gridDim.x - 1) / gridDim.x;
+    const unsigned b = min(blockIdx.x * per, ng), e = min(b + per, ng);
+    double acc[4] = {0, 0, 0, 0};
     unsigned long long ci = 0, pi = 0;
-    for (unsigned g = threadIdx.x; g < ng; g += blockDim.x) {
+    for (unsigned g = b + threadIdx.x; g < e; g += blockDim.x) {
         const double4 p = gpart[g];
-        e[0] += p.x; e[1] += p.y; e[2] += p.z; e[3] += p.w;
+        acc[0] += p.x; acc[1] += p.y; acc[2] += p.z; acc[3] += p.w;
         const unsigned long long n = gr_r[g].y;
         ci += n * gr_nc[g];
         pi += n * (gr_np[g] + gr_nf[g]);
@@ -917,36 +925,55 @@ __global__ void __launch_bounds__(1024) k_force_reduce(const double4 *gpart, con
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int c = 0; c < 4; c++) e[c] += __shfl_xor_sync(0xffffffffu, e[c], o);
+        for (int c = 0; c < 4; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
         ci += __shfl_xor_sync(0xffffffffu, ci, o);
         pi += __shfl_xor_sync(0xffffffffu, pi, o);
     }
     if (lane == 0) {
-        for (int c = 0; c < 4; c++) se[w][c] = e[c];
+        for (int c = 0; c < 4; c++) se[w][c] = acc[c];
         si[w][0] = ci;
         si[w][1] = pi;
     }
     __syncthreads();
-    if (w == 0) {
-        const bool have = lane < (blockDim.x >> 5);
-        for (int c = 0; c < 4; c++) e[c] = have ? se[lane][c] : 0.0;
-        ci = have ? si[lane][0] : 0ull;
-        pi = have ? si[lane][1] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int c = 0; c < 4; c++) e[c] += __shfl_xor_sync(0xffffffffu, e[c], o);
-            ci += __shfl_xor_sync(0xffffffffu, ci, o);
-            pi += __shfl_xor_sync(0xffffffffu, pi, o);
+    if (threadIdx.x == 0) {
+        double t[4] = {0, 0, 0, 0};
+        unsigned long long tc = 0, tp = 0;
+        for (int k = 0; k < kRedThreads / 32; k++) {
+            for (int c = 0; c < 4; c++) t[c] += se[k][c];
+            tc += si[k][0];
+            tp += si[k][1];
         }
-        if (lane == 0) {
-            st->energy = e[0];
-            st->mom[0] = e[1];
-            st->mom[1] = e[2];
-            st->mom[2] = e[3];
-            st->cell_inter = ci;
-            st->pp_inter = pi;
-        }
+        red_e[blockIdx.x] = make_double4(t[0], t[1], t[2], t[3]);
+        red_c[2 * blockIdx.x] = tc;
+        red_c[2 * blockIdx.x + 1] = tp;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_force_reduce(const double4 *red_e, const unsigned long long *red_c,
+                                                     Status *st) {
+    const unsigned lane = threadIdx.x;
+    double acc[4] = {0, 0, 0, 0};
+    unsigned long long ci = 0, pi = 0;
+    for (int b = lane; b < kRedBlocks; b += 32) {
+        const double4 p = red_e[b];
+        acc[0] += p.x; acc[1] += p.y; acc[2] += p.z; acc[3] += p.w;
+        ci += red_c[2 * b];
+        pi += red_c[2 * b + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        ci += __shfl_xor_sync(0xffffffffu, ci, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
+    }
+    if (lane == 0) {
+        st->energy = acc[0];
+        st->mom[0] = acc[1];
+        st->mom[1] = acc[2];
+        st->mom[2] = acc[3];
+        st->cell_inter = ci;
+        st->pp_inter = pi;
     }
 }
 
@@ -1049,8 +1076,10 @@ int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
 }
 
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st) {
-    k_force_reduce<<<1, 1024, 0, st>>>(A.gpart, A.gr_r, A.gr_nc, A.gr_np, A.gr_nf, A.st);
-    return 1;
+    k_force_partials<<<kRedBlocks, kRedThreads, 0, st>>>(A.gpart, A.gr_r, A.gr_nc, A.gr_np, A.gr_nf, A.red_e,
+                                                         A.red_c, A.st);
+    k_force_reduce<<<1, 32, 0, st>>>(A.red_e, A.red_c, A.st);
+    return 2;
 }
 
 // ===========================================================================

@@ -106,6 +106,8 @@ struct ForceArgs {
     uint2 *pairs;                    // (sorted i, sorted j)
     unsigned long long pair_cap;
     double4 *gpart;                  // per group: sum m phi / 2, sum m a
+    double4 *red_e;                  // per reduction block: partial sums of gpart
+    unsigned long long *red_c;       // per reduction block: cell and PP interaction counts
     Status *st;
 };
 
