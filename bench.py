@@ -60,7 +60,7 @@ FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maxi
 # DRAM bytes per launch of the mixed force kernel from one ncu capture of the
 # same kernel build on this workload (dram__bytes_read.sum + dram__bytes_write.sum);
 # None when the kernel changed after the capture.
-FORCE_MIXED_DRAM_BYTES = 1_563_750_000
+FORCE_MIXED_DRAM_BYTES = None
 
 
 def rank_env():

@@ -327,12 +327,13 @@ __device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 
 
 // Far PP entries (the walk guarantees every pair at least r_out apart, so
 // K = W = 0): plain Newtonian pairs, two list entries per f32x2 operation,
-// with no per-iteration test.
+// with no per-iteration test; unrolled twice (the loop is short enough to
+// keep two iterations in flight).
 template <int NI, int J>
 __device__ __forceinline__ void pp_tile_far(const ulonglong2 (*sQ)[kJ / 2], int s, int npairs,
                                             const f2x (&OX)[NI], const f2x (&OY)[NI],
                                             const f2x (&OZ)[NI], f2x (&PA)[NI][4]) {
-#pragma unroll kUnrollPP
+#pragma unroll 2
     for (int P = s; P < npairs; P += J) {
         const ulonglong2 q0 = sQ[0][P], q1 = sQ[1][P];
 #pragma unroll
