@@ -225,6 +225,46 @@ def test_walk_coverage_and_completeness(theta):
             assert _brute_min_dist2(sp[b:b + c], sp[nd["begin"][v]:nd["begin"][v] + nd["count"][v]]) >= r_out ** 2
 
 
+@pytest.mark.parametrize("theta", [0.3, 0.6])
+def test_leaves_passing_the_gap_test_hold_no_changeover_pair(theta):
+    """A leaf opened although its grid box passes the r_out gap test
+    (squared gap between whole-cell boxes >= floor((r_out 2^21/S)^2) + 2) was
+    opened for the opening angle alone: brute force finds no pair of it and
+    the group closer than r_out, so its pairs are plain Newtonian (the far PP
+    segment).  Leaves failing the test are where the changeover pairs are."""
+    d = inputs.plummer(3000, 8)
+    r_out = 0.04
+    T = oracle.Tree(d["pos"], d["mass"], 4, 24)
+    key, q, perm = T.keys()
+    sp = d["pos"][perm]
+    nd = T.nodes()
+    g = T.groups()
+    thr = np.floor((r_out * T.scale) ** 2) + 2
+    leaf_ids = np.flatnonzero(nd["leaf"] == 1)
+    n_far = n_near_close = 0
+    for k in range(0, T.ngroups, 2):
+        _, pp = T.walk(k, theta, r_out)
+        inpp = np.zeros(len(sp), bool)
+        inpp[pp] = True
+        b, c = g["begin"][k], g["count"][k]
+        gmin = g["qmin"][k].astype(np.int64)
+        gmax = g["qmax"][k].astype(np.int64)
+        for v in leaf_ids:
+            lb, lc = nd["begin"][v], nd["count"][v]
+            if not inpp[lb:lb + lc].all():
+                continue
+            cmin = nd["qmin"][v].astype(np.int64)
+            cmax = nd["qmax"][v].astype(np.int64)
+            gap = np.maximum(np.maximum(cmin - (gmax + 1), gmin - (cmax + 1)), 0)
+            d2 = _brute_min_dist2(sp[b:b + c], sp[lb:lb + lc])
+            if float((gap * gap).sum()) >= thr:
+                n_far += 1
+                assert d2 >= r_out ** 2
+            elif d2 < r_out ** 2:
+                n_near_close += 1
+    assert n_far > 0 and n_near_close > 0
+
+
 def test_tree_theta0_equals_direct():
     d = inputs.plummer(2048, 1)
     acc, pot = oracle.direct_force(d["pos"], d["mass"], 0.005, 0.05)
