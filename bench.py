@@ -359,6 +359,7 @@ def tidal_leg(ctx, d, steps, n_bin=65536, order=3):
     import torch
     from paper_2006_16560_gb300 import binding as B
     n = len(d["mass"])
+    n_bin = min(n_bin, n)
     rng = np.random.default_rng(12)
     cm = torch.from_numpy(d["pos"][rng.choice(n, n_bin, replace=False)]).cuda()
     dc = torch.full((n_bin,), 1e-4, dtype=torch.float64, device="cuda")
@@ -402,6 +403,7 @@ def cpu_oracle_sample(pos, mass, nsample, seed=11):
     set, the seconds spent and the threads used."""
     import oracle
     n = len(mass)
+    nsample = min(nsample, n)
     t0 = time.perf_counter()
     T = oracle.Tree(pos, mass, 16, 64)
     t1 = time.perf_counter()
