@@ -221,6 +221,35 @@ def test_small_and_ragged(ctx, n, precision):
     check_neighbours(g, d["pos"], p.r_out)
 
 
+@pytest.mark.parametrize("ncoinc", [64, 130])
+def test_depth_capped_leaf_larger_than_a_warp_scan_field(ctx, ncoinc):
+    """More than 63 coincident particles make a depth-capped leaf whose count
+    does not fit the walk's packed 11-bit scan fields (the walk then scans
+    the counts one by one); the lists and neighbour sets must still be exact
+    and the forces match the oracle tree."""
+    d = inputs.plummer(3000, 21, masses="kroupa")
+    pos = d["pos"].copy()
+    pos[:ncoinc] = pos[0]
+    p = c1_params(order=2)
+    T = oracle.Tree(pos, d["mass"], p.n_leaf, p.n_group)
+    a, phi, _ = T.force(p.theta, p.r_in, p.r_out, order=2)
+    for prec in (B.PT_FP64, B.PT_MIXED):
+        g = run_gpu(ctx, pos, d["mass"], c1_params(order=2, precision=prec))
+        check_neighbours(g, pos, p.r_out)
+        e = np.linalg.norm(g["acc"] - a, axis=1) / np.median(np.linalg.norm(a, axis=1))
+        if prec == B.PT_FP64:
+            assert e.max() <= FP64_TOL
+        else:
+            assert np.percentile(e, 99) <= MIXED_P99 and e.max() <= MIXED_MAX
+    st = g["stats"]
+    co, cells, po, pp = g["tree"].lists(st["cell_list_total"], st["pp_list_total"])
+    gn, on = g["tree"].nodes(), T.nodes()
+    for k in range(T.ngroups):
+        ocells, opp = T.walk(k, p.theta, p.r_out)
+        assert node_ids(gn, cells[co[k]:co[k + 1]]) == node_ids(on, ocells)
+        assert np.array_equal(np.sort(pp[po[k]:po[k + 1]]), np.sort(opp))
+
+
 def test_degenerate_inputs(ctx):
     # all particles at one point: box side 0 -> 1, one depth-capped leaf
     pos = np.zeros((50, 3))
