@@ -39,7 +39,9 @@
  *            gap between the grid boxes, in whole cells, is at least
  *            floor((r_out * 2^21 / S)^2) + 2 (so no pair closer than r_out
  *            is ever inside an accepted cell); otherwise leaves go to the
- *            particle-particle (PP) list and internal cells are opened;
+ *            particle-particle (PP) list and internal cells are opened (a
+ *            leaf that passes the gap test is kept in the group's far PP
+ *            segment, evaluated as plain Newtonian pairs);
  *   neighbours  j != i with dx*dx + dy*dy + dz*dz < r_out*r_out evaluated in
  *            float64 left to right without fused multiply-add.
  *
@@ -51,7 +53,9 @@
  *     device memory inside the call.  The caller owns every buffer it passes.
  *   - All work is ordered on the context's stream.  Calls that return counts
  *     (pt_tree_build, pt_longrange_force, pt_batch_longrange_force)
- *     synchronise that stream before returning.
+ *     synchronise that stream before returning.  pt_longrange_force copies
+ *     host outputs (acc, pot) on a private stream of the context that waits
+ *     for the force kernel; it is synchronised before the call returns.
  *   - Layouts: positions are n x 3 float64, row-major (x, y, z per particle);
  *     masses n float64 (>= 0); accelerations n x 3 float64; potentials n
  *     float64; every output is in the caller's original particle order.
