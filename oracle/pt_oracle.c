@@ -35,9 +35,12 @@
  * the key scheme, the treatment of r <= r_in for the potential) are stated
  * at each function.  Parity status: the changeover functions, the direct
  * sum, the neighbour sets, keys/sort/topology and the theta = 0 tree are
- * pinned by tests against closed forms, identities and brute force; the
- * size of the tree-versus-direct truncation error has no printed value in
- * the paper (parity unpinned for that magnitude; only its scaling is pinned).
+ * pinned by tests against closed forms, identities and brute force; a
+ * cell's potential and acceleration are pinned by the Legendre expansion of
+ * two point masses, by acceleration = -grad(potential) and by their
+ * truncation orders; the size of the tree-versus-direct truncation error has
+ * no printed value in the paper (parity unpinned for that magnitude; only
+ * its scaling is pinned).
  */
 #include <math.h>
 #include <stdint.h>
@@ -689,7 +692,8 @@ static void cell_pull(const orc_node *C, const double *xi, int order, double *ac
     }
 }
 
-/* Exposed for the truncation-scaling pin: pull of node v on point xi. */
+/* Exposed for the cell pins (truncation orders, Legendre closed form,
+ * -grad phi): pull of node v on point xi. */
 void orc_cell_pull(const orc_tree *t, int64_t v, const double *xi, int order,
                    double *acc, double *pot)
 {

@@ -277,38 +277,106 @@ def test_tree_theta0_equals_direct():
 
 
 def test_tree_error_decreases_with_theta_and_order():
+    """Tree against direct summation: the p99 error of the acceleration and of
+    the potential falls with the opening angle and with the expansion order."""
     d = inputs.plummer(4096, 1)
     acc, pot = oracle.direct_force(d["pos"], d["mass"], 0.005, 0.05)
     T = oracle.Tree(d["pos"], d["mass"], 8, 64)
-    err = {}
+    err, perr = {}, {}
     for th in (0.3, 0.6):
         for order in (0, 2):
             a, p, _ = T.force(th, 0.005, 0.05, order=order)
             err[th, order] = np.percentile(np.linalg.norm(a - acc, axis=1) / np.linalg.norm(acc, axis=1), 99)
-    assert err[0.3, 2] < err[0.3, 0] and err[0.6, 2] < err[0.6, 0]
-    assert err[0.3, 0] < err[0.6, 0] and err[0.3, 2] < err[0.6, 2]
+            perr[th, order] = np.percentile(np.abs(p - pot) / np.abs(pot), 99)
+    for e in (err, perr):
+        assert e[0.3, 2] < e[0.3, 0] and e[0.6, 2] < e[0.6, 0]
+        assert e[0.3, 0] < e[0.6, 0] and e[0.3, 2] < e[0.6, 2]
     assert err[0.6, 0] < 0.05
+    # the potential converges faster than the force (one power of s/d more
+    # relative to its own size), so its errors sit well below the force's
+    assert perr[0.6, 0] < 0.01 and perr[0.3, 2] < err[0.3, 2]
 
 
 def test_cell_truncation_order():
     """A far cell's monopole error falls as (s/d)^2 and the quadrupole's as
-    (s/d)^3 against the exact Newtonian sum over its particles."""
+    (s/d)^3 against the exact Newtonian sum over its particles, for the
+    acceleration and for the potential (the centre of mass removes the dipole
+    term from both)."""
     rng = np.random.default_rng(1)
     pts = rng.uniform(-0.5, 0.5, (50, 3))
     m = rng.uniform(0.5, 1.5, 50)
     T = oracle.Tree(pts, m, 64, 64)
     direction = np.array([0.48, 0.6, 0.64])
-    slopes = {}
+    slopes, pslopes = {}, {}
     for order in (0, 2):
-        e = []
+        e, ep = [], []
         ds = np.array([8.0, 16.0, 32.0, 64.0])
         for dist in ds:
             x = direction * dist
-            a, _ = T.cell_pull(0, x, order)
+            a, phi = T.cell_pull(0, x, order)
             dd = pts - x
             r = np.linalg.norm(dd, axis=1)
             exact = (m[:, None] * dd / r[:, None] ** 3).sum(0)
+            exact_phi = -(m / r).sum()
             e.append(np.linalg.norm(a - exact) / np.linalg.norm(exact))
+            ep.append(abs(phi - exact_phi) / abs(exact_phi))
         slopes[order] = np.polyfit(np.log(ds), np.log(e), 1)[0]
+        pslopes[order] = np.polyfit(np.log(ds), np.log(ep), 1)[0]
     assert slopes[0] == pytest.approx(-2.0, abs=0.25)
     assert slopes[2] == pytest.approx(-3.0, abs=0.25)
+    assert pslopes[0] == pytest.approx(-2.0, abs=0.25)
+    assert pslopes[2] == pytest.approx(-3.0, abs=0.25)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.4, math.pi / 2, 2.2])
+def test_cell_potential_legendre_closed_form(gamma):
+    """Two equal masses m at (0, 0, +-a) seen from distance d at polar angle
+    gamma: the exact potential is -m/d sum_l (a/d)^l P_l(cos gamma) (1 + (-1)^l),
+    so the monopole is -2m/d and the quadrupole adds -2 m a^2 P_2(cos gamma)/d^3
+    (Legendre expansion of 1/|x - x'|).  The oracle's cell potential and
+    acceleration must equal those truncations to rounding, and differ from the
+    exact sum by the next (l = 4) term."""
+    m, a, d = 0.7, 0.3, 5.0
+    pts = np.array([[0.0, 0.0, a], [0.0, 0.0, -a]])
+    T = oracle.Tree(pts, np.array([m, m]), 8, 8)
+    u = np.array([math.sin(gamma), 0.0, math.cos(gamma)])
+    x = d * u
+    c = math.cos(gamma)
+    p2 = 0.5 * (3 * c * c - 1)
+    p4 = (35 * c ** 4 - 30 * c * c + 3) / 8
+    _, phi0 = T.cell_pull(0, x, 0)
+    a2, phi2 = T.cell_pull(0, x, 2)
+    assert phi0 == pytest.approx(-2 * m / d, rel=1e-14)
+    assert phi2 == pytest.approx(-2 * m / d - 2 * m * a * a * p2 / d ** 3, rel=1e-14)
+    exact = -(m / np.linalg.norm(pts - x, axis=1)).sum()
+    assert exact - phi2 == pytest.approx(-2 * m * a ** 4 * p4 / d ** 5, rel=0.05, abs=1e-3 * m * a ** 4 / d ** 5)
+    # acceleration of the same truncation, -grad phi with phi(x) =
+    # -2m/|x| - m a^2 (3 z^2 - |x|^2)/|x|^5 (written out by hand)
+    r = d
+    z = x[2]
+    grad = 2 * m * x / r ** 3 - m * a * a * (np.array([0.0, 0.0, 6 * z]) - 2 * x) / r ** 5 \
+        + 5 * m * a * a * (3 * z * z - r * r) * x / r ** 7
+    np.testing.assert_allclose(a2, -grad, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("order", [0, 2])
+def test_cell_acceleration_is_minus_grad_potential(order):
+    """The cell's acceleration is minus the gradient of its potential
+    (central differences of the oracle's own cell potential), at points from
+    twice to ten times the cell's size away."""
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-0.5, 0.5, (40, 3))
+    m = rng.uniform(0.2, 1.8, 40)
+    T = oracle.Tree(pts, m, 64, 64)
+    for dist in (2.0, 4.0, 10.0):
+        for _ in range(3):
+            u = rng.normal(size=3)
+            x = dist * u / np.linalg.norm(u)
+            a, _ = T.cell_pull(0, x, order)
+            h = 1e-5 * dist
+            g = np.zeros(3)
+            for k in range(3):
+                e = np.zeros(3)
+                e[k] = h
+                g[k] = (T.cell_pull(0, x + e, order)[1] - T.cell_pull(0, x - e, order)[1]) / (2 * h)
+            np.testing.assert_allclose(a, -g, rtol=2e-8, atol=1e-9 * np.linalg.norm(a))
