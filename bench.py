@@ -18,10 +18,18 @@ e2e     = the same metric through the C ABI with pinned HOST buffers, the
           host<->device copies inside the timed region
 fp64    = the plain float64 GPU path on the same workload
 roofline: the mixed force kernel against the FP32 CUDA-core peak
-          (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.55 TFLOP/s), flops
-          per interaction counted from the kernel source
+          (SMs x 128 lanes x 2 flop x maximum SM clock; 152 x 128 x 2 x
+          2.07 GHz = 80.55 TFLOP/s on a GB300), flops per interaction
+          counted from the kernel source
+c2_10m  = the same workload at N = 10^7 (mixed throughput, stage times,
+          mixed vs FP64 error)
+binaries_1m = N = 10^6 with every star in a primordial binary (500k pairs):
+          mixed and FP64 step times, mixed vs FP64 error, companions found
 cpu_baseline / --impl reference: the CPU oracle as it stands, on the host
           cores, on a bounded sample of the same workload
+tree_vs_direct: the GPU tree (FP64 and mixed) against the oracle's direct
+          O(N^2) sum on sampled targets, p50 / p99 relative error of the
+          acceleration and the potential (N = 2^20 and 10^7)
 """
 from __future__ import annotations
 
@@ -54,8 +62,18 @@ FLOPS = {
     ("mixed", "pp_newton", None): 22,
     ("fp64", "cell", 2): 56, ("fp64", "cell", 0): 22, ("fp64", "pp", None): 53,
 }
-SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6       # flop/s at the maximum SM clock
+FP32_LANES = 128                 # FP32 lanes per SM (4 SM sub-partitions x 32)
+GB300_SMS, GB300_MAX_MHZ = 152, 2070.0
+
+
+def fp32_peak(sm_count: int, max_mhz: float) -> float:
+    """FP32 CUDA-core peak in flop/s: SMs x 128 lanes x 2 flop (FFMA) x clock."""
+    return sm_count * FP32_LANES * 2 * max_mhz * 1e6
+
+
+def device_sm_count(local: int) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(local).multi_processor_count)
 
 # DRAM bytes per launch of the mixed force kernel from one ncu capture of the
 # same kernel build on this workload (dram__bytes_read.sum + dram__bytes_write.sum);
@@ -397,6 +415,112 @@ def tidal_leg(ctx, d, steps, n_bin=65536, order=3):
             "tensors_per_s": n_bin / (ms * 1e-3)}
 
 
+def _errors(acc, pot, acc_ref, pot_ref):
+    """p50 / p99 / max of the per-particle relative errors |da|/|a| and |dphi|/|phi|."""
+    e = np.linalg.norm(acc - acc_ref, axis=1) / np.linalg.norm(acc_ref, axis=1)
+    ep = np.abs(pot - pot_ref) / np.abs(pot_ref)
+    return {"acc_p50": float(np.percentile(e, 50)), "acc_p99": float(np.percentile(e, 99)),
+            "acc_max": float(e.max()), "pot_p50": float(np.percentile(ep, 50)),
+            "pot_p99": float(np.percentile(ep, 99)), "pot_max": float(ep.max())}
+
+
+def _device_set(d, n):
+    import torch
+    pos = torch.from_numpy(d["pos"]).cuda()
+    mass = torch.from_numpy(d["mass"]).cuda()
+    cap = 8 * n
+    out = (torch.empty((n, 3), dtype=torch.float64, device="cuda"),
+           torch.empty((n,), dtype=torch.float64, device="cuda"),
+           torch.empty((n + 1,), dtype=torch.int64, device="cuda"),
+           torch.empty((cap,), dtype=torch.int32, device="cuda"))
+    return pos, mass, out
+
+
+def c2_10m_leg(ctx, steps, flush):
+    """The headline workload at N = 10^7 (Kroupa Plummer, seed 2, same tree
+    parameters): mixed steps (build + force) timed like the headline, one
+    FP64 step for the mixed-vs-FP64 error.  Returns the record and the mixed
+    and FP64 results for the sampled tree-vs-direct comparison."""
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+    n = 10_000_000
+    d = inputs.plummer(n, SEED, masses="kroupa")
+    pos, mass, out = _device_set(d, n)
+    holder = [None]
+    run_steps(ctx, holder, pos, mass, params(B.PT_MIXED), out, 2, flush)
+    times, st = run_steps(ctx, holder, pos, mass, params(B.PT_MIXED), out, steps, flush)
+    mx = (out[0].cpu().numpy().copy(), out[1].cpu().numpy().copy())
+    nb_mx = int(st["neighbours"])
+    t64, st64 = run_steps(ctx, holder, pos, mass, params(B.PT_FP64), out, 1, flush)
+    f64 = (out[0].cpu().numpy().copy(), out[1].cpu().numpy().copy())
+    holder[0].free()
+    ms = statistics.mean(times)
+    inter = st["cell_interactions"] + st["pp_interactions"]
+    rec = {"workload": f"Plummer N={n}, Kroupa IMF, seed {SEED}; quadrupole tree theta=0.3, n_leaf=16, "
+                       "n_group=64, r_out=0.003, r_in=0.0003; neighbour lists on",
+           "value": inter / (ms * 1e-3), "unit": "interactions/s", "particles_per_s": n / (ms * 1e-3),
+           "ms_per_step": ms, "latency_ms": {"p50": float(np.percentile(times, 50)),
+                                             "p99": float(np.percentile(times, 99))},
+           "interactions_per_step": inter, "neighbours": nb_mx,
+           "neighbours_fp64": int(st64["neighbours"]),
+           "stage_ms": {"build": st["ms_build"], "walk": st["ms_walk"], "force_kernel": st["ms_force"]},
+           "fp64_ms_per_step": t64[0],
+           "mixed_error_vs_fp64": _errors(mx[0], mx[1], f64[0], f64[1])}
+    return rec, d, {"fp64": f64, "mixed": mx}
+
+
+def binaries_leg(ctx, steps, flush):
+    """Precision variant: N = 10^6 with every star in a primordial binary
+    (500,000 pairs, a log-uniform in 0.005-50 AU, thermal e; seed 4) on the
+    headline tree parameters.  Mixed and FP64 step times, mixed vs FP64
+    error, and the fraction of stars whose companion is in their neighbour
+    list (every pair is closer than r_in, so all of them must be)."""
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+    d = inputs.plummer_binaries(500_000, 4)
+    n = len(d["mass"])
+    pos, mass, out = _device_set(d, n)
+    holder = [None]
+    run_steps(ctx, holder, pos, mass, params(B.PT_MIXED), out, 2, flush)
+    times, st = run_steps(ctx, holder, pos, mass, params(B.PT_MIXED), out, steps, flush)
+    mx = (out[0].cpu().numpy().copy(), out[1].cpu().numpy().copy())
+    off, idx = out[2].cpu().numpy(), out[3][: int(st["neighbours"])].cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(off))
+    found = np.zeros(n, dtype=bool)
+    found[rows[idx == (rows ^ 1)]] = True
+    run_steps(ctx, holder, pos, mass, params(B.PT_FP64), out, 1, flush)
+    t64, st64 = run_steps(ctx, holder, pos, mass, params(B.PT_FP64), out, 2, flush)
+    f64 = (out[0].cpu().numpy(), out[1].cpu().numpy())
+    holder[0].free()
+    ms, ms64 = statistics.mean(times), statistics.mean(t64)
+    inter = st["cell_interactions"] + st["pp_interactions"]
+    return {"workload": "Plummer centres N=500000 pairs (10^6 stars), Kroupa masses, a log-uniform "
+                        "0.005-50 AU, thermal e (seed 4); quadrupole tree theta=0.3, n_leaf=16, n_group=64, "
+                        "r_out=0.003, r_in=0.0003",
+            "value": inter / (ms * 1e-3), "unit": "interactions/s", "ms_per_step": ms,
+            "fp64_ms_per_step": ms64, "speedup_mixed_vs_fp64": ms64 / ms,
+            "pp_changeover_interactions": st["pp_changeover_interactions"],
+            "interactions_per_step": inter, "neighbours": int(st["neighbours"]),
+            "neighbours_fp64": int(st64["neighbours"]),
+            "companions_found": float(found.mean()),
+            "mixed_error_vs_fp64": _errors(mx[0], mx[1], f64[0], f64[1])}
+
+
+def tree_vs_direct(d, results, nsample, seed):
+    """Tree-vs-direct truncation error: the oracle's direct O(N^2) long-range
+    sum (same changeover split, float64) on nsample random targets against
+    each GPU result in `results` ({name: (acc, pot)})."""
+    import oracle
+    n = len(d["mass"])
+    tg = np.random.default_rng(seed).choice(n, min(nsample, n), replace=False)
+    t0 = time.perf_counter()
+    a_d, p_d = oracle.direct_force(d["pos"], d["mass"], 0.0003, 0.003, targets=tg)
+    rec = {"targets": int(len(tg)), "direct_s": time.perf_counter() - t0}
+    for name, (acc, pot) in results.items():
+        rec[name] = _errors(acc[tg], pot[tg], a_d, p_d)
+    return rec
+
+
 def cpu_oracle_sample(pos, mass, nsample, seed=11):
     """Oracle tree on the host cores: full build plus the tree force on
     nsample targets; returns the interactions/s it would sustain on the whole
@@ -462,6 +586,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--no-widened", action="store_true",
                     help="skip the orbit-neighbour and tidal-tensor legs")
+    ap.add_argument("--no-10m", action="store_true", help="skip the N = 10^7 leg")
+    ap.add_argument("--no-binaries", action="store_true", help="skip the primordial-binary leg")
+    ap.add_argument("--tvd-sample", type=int, default=10000,
+                    help="targets of the direct-sum reference at N = 2^20 (tree-vs-direct error)")
+    ap.add_argument("--tvd-sample-10m", type=int, default=1000,
+                    help="targets of the direct-sum reference at N = 10^7")
     ap.add_argument("--only-leg", choices=["orbit", "tidal"], default=None,
                     help="run one widened leg alone on the headline set and print its JSON (profiling)")
     args = ap.parse_args()
@@ -520,6 +650,7 @@ def main():
     clocks = clk.summary()
     acc_mx = out[0].cpu().numpy().copy()
     pot_mx = out[1].cpu().numpy().copy()
+    res_1m = {"mixed": (acc_mx, pot_mx)}
     nb_total = int(st["neighbours"])
     ms_step = statistics.mean(times)
     ms_max = max_over_ranks(ms_step, device="cuda")
@@ -551,17 +682,20 @@ def main():
         "gpu_launches": int((st["launches_build"] + st["launches_force"]) * args.steps),
         "clocks": clocks,
     }
-    line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK / 1e12,
-                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK,
+    sms = device_sm_count(local)
+    max_mhz = clocks.get("sm_max_mhz") or GB300_MAX_MHZ
+    peak = fp32_peak(sms, max_mhz)
+    line["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                        "unit": "TFLOP/s", "frac": achieved / peak,
                         "traffic": FORCE_MIXED_DRAM_BYTES,
                         "kernel": "k_force_mixed<2,true>",
                         "flops_per_interaction": {"cell_quadrupole": FLOPS[("mixed", "cell", 2)],
                                                   "pp_changeover": FLOPS[("mixed", "pp", None)],
                                                   "pp_newton": FLOPS[("mixed", "pp_newton", None)]},
-                        "peak_note": "FP32 CUDA-core peak at the 2070 MHz maximum SM clock "
-                                     "(152 SMs x 128 lanes x 2 flop)"}
+                        "peak_note": f"FP32 CUDA-core peak at the {max_mhz:.0f} MHz maximum SM clock "
+                                     f"({sms} SMs x 128 lanes x 2 flop; no tensor cores: not a contraction)"}
     if clocks.get("sm_mhz"):
-        line["roofline"]["frac_at_measured_clock"] = achieved / (SM_COUNT * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6)
+        line["roofline"]["frac_at_measured_clock"] = achieved / fp32_peak(sms, clocks["sm_mhz"])
     rc, probe = B.pt_probe_fp32_peak(ctx.h)
     if rc == B.PT_OK and probe > 0:
         line["roofline"]["fp32_fma_probe_tflops"] = probe
@@ -573,6 +707,7 @@ def main():
         t64, st64 = run_steps(ctx, holder, pos, mass, prm_64, out, max(3, args.steps // 2), flush)
         acc64 = out[0].cpu().numpy()
         pot64 = out[1].cpu().numpy()
+        res_1m["fp64"] = (acc64, pot64)
         ms64 = statistics.mean(t64)
         inter64 = st64["cell_interactions"] + st64["pp_interactions"]
         e = np.linalg.norm(acc_mx - acc64, axis=1) / np.linalg.norm(acc64, axis=1)
@@ -623,7 +758,19 @@ def main():
     if not args.no_widened and not args.only_mixed:
         line["orbit_neighbours"] = orbit_leg(ctx, d, args.steps)
         line["tidal"] = tidal_leg(ctx, d, max(3, args.steps // 2))
+    big = None
+    if not args.no_10m and not args.only_mixed:
+        line["c2_10m"], d10, big = c2_10m_leg(ctx, max(3, args.steps // 4), flush)
+    if not args.no_binaries and not args.only_mixed:
+        line["binaries_1m"] = binaries_leg(ctx, max(3, args.steps // 4), flush)
     if rank == 0 and not args.no_cpu_baseline:
+        # CPU oracle on the host cores: the direct-sum reference of the
+        # tree-vs-direct error on sampled targets, then the timed baseline
+        tvd = {"n_1m": tree_vs_direct(d, res_1m, args.tvd_sample, 21)}
+        if big is not None:
+            tvd["n_10m"] = tree_vs_direct(d10, big, args.tvd_sample_10m, 22)
+            del big, d10
+        line["tree_vs_direct"] = tvd
         v, secs, thr, si = cpu_oracle_sample(d["pos"], d["mass"], args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": "interactions/s", "cores": thr, "kind": "oracle",
                                 "sample": f"oracle tree build over all {n} particles + oracle tree force "

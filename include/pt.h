@@ -141,7 +141,10 @@ typedef struct {
  * *ctx receives the handle; destroy it with pt_ctx_destroy. */
 int pt_ctx_create(pt_ctx **ctx, int device, void *stream);
 
-/* Frees the context's workspace (waits for its stream first). */
+/* Frees the context's workspace (waits for its stream first).  Trees built
+ * in this context that are still alive lose their device memory and become
+ * empty handles: pass them to pt_tree_free (which then only releases the
+ * handle) or rebuild them with pt_tree_build in another context. */
 int pt_ctx_destroy(pt_ctx *ctx);
 
 /* Message of the last failing call on ctx (static storage in ctx). */
@@ -178,7 +181,8 @@ int pt_longrange_force(pt_ctx *ctx, pt_tree *tree, double *acc, double *pot,
                        int64_t *nb_offsets, int32_t *nb_idx, int64_t nb_capacity,
                        int64_t *nb_total, pt_stats *stats);
 
-/* Releases a tree. */
+/* Releases a tree (waits for its context's stream first, if the context
+ * still exists). */
 int pt_tree_free(pt_tree *tree);
 
 /* One independent particle set in a batch. */
@@ -422,9 +426,9 @@ int pt_probe_fp32_peak(pt_ctx *ctx, double *tflops);
  * order.  This is the same radix sort that orders the Morton keys inside
  * pt_tree_build, offered for callers that cannot allocate device memory: a
  * process whose GPU memory belongs to another allocator (a framework's
- * caching allocator or a fixed arena), a loop that must never allocate, or
- * work that will later be captured into a CUDA graph.  The paper has no
- * counterpart; it is a service of this library.
+ * caching allocator or a fixed arena, where a cudaMalloc of the library's
+ * own would fail or fragment it), or a loop that must never allocate.  The
+ * paper has no counterpart; it is a service of this library.
  *
  * It allocates nothing.  Its scratch space is a fixed array of about
  * 4.3 MiB inside the library image, which every GPU that loads the library
@@ -436,10 +440,13 @@ int pt_probe_fp32_peak(pt_ctx *ctx, double *tflops);
  *   stream: the cudaStream_t (as void*) on which the sort is ordered; the
  *     call returns without waiting for it.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  All calls share the one scratch array, so calls whose
- * work overlaps on the GPU (other streams, other host threads) race and
- * must be serialised by the caller.  Returns PT_OK, PT_ERR_ARG or
+ * (cudaGetSymbolAddress) for that device and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call
+ * this function on a device after cudaDeviceReset of that device (the kept
+ * address belonged to the reset context).  All calls share the one scratch
+ * array, which keeps the last call's contents (the call rewrites everything
+ * it reads from it), so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.  Returns PT_OK, PT_ERR_ARG or
  * PT_ERR_CUDA (launch failure). */
 int pt_sort_keys_noalloc(int64_t n, const uint64_t *keys, uint64_t *keys_sorted,
                          uint32_t *perm, void *stream);

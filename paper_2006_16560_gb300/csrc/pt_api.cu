@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -31,6 +32,10 @@ struct pt_ctx {
     Status *h_status = nullptr;      // pinned
     cudaEvent_t ev[8] = {};
     pt_tree *batch_tree = nullptr;   // reused by pt_batch_longrange_force
+    // trees built in this context and not yet freed: pt_ctx_destroy releases
+    // their device memory and detaches them, so a later pt_tree_free never
+    // touches the destroyed context
+    std::vector<pt_tree *> trees;
     struct TuneEntry {
         int nsets, nbucket, mbucket, order, precision;
         double theta;
@@ -289,7 +294,7 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->gr_co, (N + 1) * 8));
     TRY(ensure(ctx, t->gr_po, (N + 1) * 8));
     TRY(ensure(ctx, t->gpart, N * 32));
-    TRY(ensure(ctx, t->red_part, 256 * 48));     // reduction partials (152 blocks used)
+    TRY(ensure(ctx, t->red_part, (size_t)kRedBlocksMax * 48));     // reduction partials, one per block
     TRY(ensure(ctx, t->ssc, N * 8));
     TRY(ensure(ctx, t->set_mean, S * 8));
     if (t->prm.mass_dependent) {
@@ -475,6 +480,7 @@ ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
     ForceArgs A{};
     A.gr_r = t->gr_r.as<uint2>();
     A.gr_a = t->gr_a.as<uint4>();
+    A.gr_b = t->gr_b.as<uint4>();
     A.gr_nc = t->gr_nc.as<unsigned>();
     A.gr_np = t->gr_np.as<unsigned>();
     A.gr_co = t->gr_co.as<unsigned long long>();
@@ -503,7 +509,7 @@ ForceArgs force_args(pt_tree *t, double *acc, double *pot, bool want_nb) {
     A.pair_cap = t->cap_pairs;
     A.gpart = t->gpart.as<double4>();
     A.red_e = t->red_part.as<double4>();
-    A.red_c = reinterpret_cast<unsigned long long *>(t->red_part.as<double4>() + 256);
+    A.red_c = reinterpret_cast<unsigned long long *>(t->red_part.as<double4>() + kRedBlocksMax);
     A.st = t->status.as<Status>();
     return A;
 }
@@ -1131,6 +1137,26 @@ int autotune_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *base,
 
 }  // namespace
 
+namespace pt {
+int sm_count() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        (void)cudaGetLastError();
+        v = 152;      // grid sizing only: any positive count gives the same results
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+}  // namespace pt
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1166,7 +1192,7 @@ int pt_ctx_create(pt_ctx **out, int device, void *stream) {
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->out_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-        walk_init() != 0) {
+        walk_init() != 0 || sm_count() <= 0) {
         (void)cudaGetLastError();
         pt_ctx_destroy(ctx);
         return PT_ERR_CUDA;
@@ -1180,6 +1206,13 @@ int pt_ctx_destroy(pt_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->batch_tree) pt_tree_free(ctx->batch_tree);
+    for (pt_tree *t : ctx->trees) {      // still alive: free their memory, detach them
+        t->release();
+        t->built = false;
+        t->lists_valid = false;
+        t->ctx = nullptr;
+    }
+    ctx->trees.clear();
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1228,7 +1261,14 @@ int pt_tree_build_scaled(pt_ctx *ctx, int64_t n, const double *pos, const double
         if (!t) return fail(ctx, PT_ERR_OOM, "out of host memory");
         *tree = t;
     }
-    t->ctx = ctx;
+    if (t->ctx != ctx) {
+        if (t->ctx) {
+            auto &v = t->ctx->trees;
+            v.erase(std::remove(v.begin(), v.end(), t), v.end());
+        }
+        ctx->trees.push_back(t);
+        t->ctx = ctx;
+    }
     t->n = (unsigned)n;
     t->nsets = 1;
     t->prm = *params;
@@ -1449,6 +1489,8 @@ int pt_tree_free(pt_tree *t) {
     if (t->ctx) {
         cudaSetDevice(t->ctx->device);
         cudaStreamSynchronize(t->ctx->stream);
+        auto &v = t->ctx->trees;
+        v.erase(std::remove(v.begin(), v.end(), t), v.end());
     }
     t->release();
     delete t;

@@ -78,13 +78,13 @@ __global__ void k_batch_nb_split(const BatchTab *tab, const SetInfo *sets, int n
 
 int batch_gather_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
                         double *pos, double *mass, double *scale, cudaStream_t st) {
-    k_batch_gather<<<152 * 8, 256, 0, st>>>(tab, sets, nsets, n, pos, mass, scale);
+    k_batch_gather<<<sm_count() * 8, 256, 0, st>>>(tab, sets, nsets, n, pos, mass, scale);
     return 1;
 }
 
 int batch_scatter_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigned n,
                          const double *acc, const double *pot, cudaStream_t st) {
-    k_batch_scatter<<<152 * 8, 256, 0, st>>>(tab, sets, nsets, n, acc, pot);
+    k_batch_scatter<<<sm_count() * 8, 256, 0, st>>>(tab, sets, nsets, n, acc, pot);
     return 1;
 }
 
@@ -93,7 +93,7 @@ int batch_nb_launch(const BatchTab *tab, const SetInfo *sets, int nsets, unsigne
                     cudaStream_t st) {
     k_batch_nb_totals<<<(nsets + 255) / 256, 256, 0, st>>>(sets, nsets, off, totals);
     if (!split) return 1;
-    k_batch_nb_split<<<152 * 8, 256, 0, st>>>(tab, sets, nsets, n, off, idx, totals);
+    k_batch_nb_split<<<sm_count() * 8, 256, 0, st>>>(tab, sets, nsets, n, off, idx, totals);
     return 2;
 }
 

@@ -687,7 +687,7 @@ static inline int grid_for(unsigned long long n, int threads, int cap) {
 }
 
 int build_launch(const BuildArgs &A, cudaStream_t st) {
-    const int gmax = 152 * 8;
+    const int gmax = sm_count() * 8;
     const unsigned n = A.n;
     Status *S = A.status;
     int nk = 0;

@@ -28,8 +28,11 @@
 // forms dx = (hi_j - hi_i) + (lo_j - lo_i), accurate to ~2^-23 |dx| whatever
 // the offset from the origin; cells use float offsets from the group's
 // first particle.  Per tile the float sums are folded into float-float
-// accumulators (Knuth TwoSum).  A neighbour candidate (float r^2 within
-// 2^-10 of r_out^2) is confirmed with the exact float64 test.
+// accumulators (Knuth TwoSum).  A neighbour candidate (float r^2 below a
+// per-group bound that no pair within r_out can exceed, see vote_rout2) is
+// confirmed with the exact float64 test.
+#include <algorithm>
+
 #include "pt_kernels.cuh"
 
 namespace pt {
@@ -132,6 +135,32 @@ __device__ __forceinline__ Chg make_chg(const SetInfo &S) {
 struct ChgF {
     float invw, c0, c2, k0, w0, w1, w2, w3, tiny, rout2m;
 };
+
+// Near-vote bound of a group: a float32 r^2 at or above it proves that the
+// pair is at least r_out (r_out,ij = s_ij r_out for mass-dependent radii)
+// apart, so K = W = 0 and the pair cannot be a neighbour.  With u = 2^-24:
+// an offset o from the group's first particle, formed as
+// (hi_j - hi_g) + (lo_j - lo_g), is within 2u|o| + 2u^2 (|x_j| + |x_g|) of
+// the true offset; dx = o_j - o_i adds u|dx|.  Every member is within E of
+// the first particle (E = diagonal of the group's grid box, two cells added
+// for the rounding of the keys), and a partner j within r_out of member i is
+// within E + r_out of it, so |r_float - r| <= 4uE + 3ur + O(u^2 X).  r^2 in
+// float32 adds 3u relative, 1/s_ij and its square 4u more.  The bound takes
+// twice the E term and the relative terms many times over:
+//   r_v = r_out (1 + 2^-18) + 2^-21 E + 2^-40 X,  bound = r_v^2 (1 + 2^-20),
+// X = sum over the axes of |origin| + S (the largest coordinate sizes).  A
+// compact group (E ~ 10 r_out) gets a margin of ~2^-17 on r_out; a wide halo
+// group a proportionally larger one.
+__device__ __forceinline__ float vote_rout2(const uint4 ga, const uint4 gb, const SetInfo &S) {
+    const double cell = S.S * (1.0 / (double)kGrid);
+    const double ex = ((double)gb.x - (double)ga.x + 2.0) * cell;
+    const double ey = ((double)gb.y - (double)ga.y + 2.0) * cell;
+    const double ez = ((double)gb.z - (double)ga.z + 2.0) * cell;
+    const double E = sqrt(ex * ex + ey * ey + ez * ez);
+    const double X = fabs(S.origin[0]) + fabs(S.origin[1]) + fabs(S.origin[2]) + 3.0 * S.S;
+    const double rv = S.r_out * (1.0 + 0x1p-18) + 0x1p-21 * E + 0x1p-40 * X;
+    return (float)(rv * rv * (1.0 + 0x1p-20));
+}
 
 // Lane layout of one warp for a pass over up to NI * L targets: the warp's
 // lanes form J = 32 / L sub-streams of L lanes; lane (s, l) holds targets
@@ -259,7 +288,7 @@ __device__ __forceinline__ void pp_changeover_f(const ForceArgs &A, const float4
 // sI[2P + 1].  Every lane runs the same number of iterations (the tile is
 // padded to a multiple of 2J with massless entries far away), so the warp can
 // vote per iteration: when neither entry of any lane lies within r_out
-// (float r^2 below r_out^2 (1 + 2^-10)), K = W = 0 exactly and both plain
+// (float r^2 at or above the group's vote_rout2 bound), K = W = 0 exactly and both plain
 // Newtonian pairs are evaluated with packed f32x2 arithmetic on the offsets;
 // otherwise every lane takes the full changeover path for both entries on
 // float-float differences, with neighbour candidates confirmed in float64.
@@ -654,7 +683,7 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         C.w2 = (float)(20.0 * C64.lam);
         C.w3 = (float)(-5.0 * C64.lam);
         C.tiny = fmaxf((float)C64.tiny, 1e-36f);
-        C.rout2m = (float)(C64.rout2 * (1.0 + 1.0 / 1024.0));
+        C.rout2m = vote_rout2(A.gr_a[g], A.gr_b[g], A.sets[A.gr_a[g].w]);
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y;) {
             const unsigned slots =
@@ -899,10 +928,9 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
 // ===========================================================================
 
 // Energy / momentum sums and interaction counts over the groups, in two
-// launches with a fixed reduction order (the same sums every run): each of
-// kRedBlocks blocks reduces a contiguous range of groups, then one warp adds
-// the blocks' partials.
-constexpr int kRedBlocks = 152;
+// launches with a fixed reduction order (the same sums every run on a given
+// device): each of nb = min(SMs, kRedBlocksMax) blocks reduces a contiguous
+// range of groups, then one warp adds the blocks' partials in block order.
 constexpr int kRedThreads = 256;
 
 __global__ void __launch_bounds__(kRedThreads) k_force_partials(const double4 *gpart, const uint2 *gr_r,
@@ -951,11 +979,11 @@ __global__ void __launch_bounds__(kRedThreads) k_force_partials(const double4 *g
 }
 
 __global__ void __launch_bounds__(32) k_force_reduce(const double4 *red_e, const unsigned long long *red_c,
-                                                     Status *st) {
+                                                     int nb, Status *st) {
     const unsigned lane = threadIdx.x;
     double acc[4] = {0, 0, 0, 0};
     unsigned long long ci = 0, pi = 0;
-    for (int b = lane; b < kRedBlocks; b += 32) {
+    for (int b = lane; b < nb; b += 32) {
         const double4 p = red_e[b];
         acc[0] += p.x; acc[1] += p.y; acc[2] += p.z; acc[3] += p.w;
         ci += red_c[2 * b];
@@ -1053,7 +1081,7 @@ __global__ void __launch_bounds__(1024) k_group_order(const uint2 *gr_r, unsigne
 }
 
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
-    const int blocks = 152 * 8;
+    const int blocks = sm_count() * 8;
     const bool md = A.massdep != 0;
     if (precision == 1) {
         k_group_order<<<1, 1024, 0, st>>>(A.gr_r, A.gr_ord, A.st);
@@ -1077,9 +1105,10 @@ int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
 }
 
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st) {
-    k_force_partials<<<kRedBlocks, kRedThreads, 0, st>>>(A.gpart, A.gr_r, A.gr_nc, A.gr_np, A.gr_nf, A.red_e,
-                                                         A.red_c, A.st);
-    k_force_reduce<<<1, 32, 0, st>>>(A.red_e, A.red_c, A.st);
+    const int nb = std::min(sm_count(), kRedBlocksMax);
+    k_force_partials<<<nb, kRedThreads, 0, st>>>(A.gpart, A.gr_r, A.gr_nc, A.gr_np, A.gr_nf, A.red_e,
+                                                 A.red_c, A.st);
+    k_force_reduce<<<1, 32, 0, st>>>(A.red_e, A.red_c, nb, A.st);
     return 2;
 }
 
@@ -1115,10 +1144,10 @@ __global__ void k_nb_csr(NbArgs A) {
 }
 
 int nb_launch(const NbArgs &A, cudaStream_t st) {
-    k_nb_keys<<<152 * 4, 256, 0, st>>>(A);
+    k_nb_keys<<<sm_count() * 4, 256, 0, st>>>(A);
     int nk = radix_sort(A.keys, A.vals, A.keys_sorted, A.vals_sorted, A.npairs_dev,
                         (unsigned)A.pair_cap, 0, A.key_bits, nullptr, 0, A.sort_tmp, st);
-    k_nb_csr<<<152 * 4, 256, 0, st>>>(A);
+    k_nb_csr<<<sm_count() * 4, 256, 0, st>>>(A);
     return nk + 2;
 }
 

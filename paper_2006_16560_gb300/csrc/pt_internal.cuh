@@ -120,13 +120,18 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Streaming multiprocessors of the calling thread's current device
+// (cudaDevAttrMultiProcessorCount), queried once per device and cached; every
+// persistent or grid-stride launch is sized from it (152 on a GB300).
+int sm_count();
+
 // ---------------------------------------------------------------------------
 // Device-wide exclusive scan over a device-resident element count, with a
 // fixed grid (so the launch sequence never depends on data and can be
 // captured in a CUDA graph).  Three launches: per-block sums, scan of the
 // block sums, per-block scan with carry.
 // ---------------------------------------------------------------------------
-constexpr int kScanBlocks = 304;     // 2 x 152 SMs
+constexpr int kScanBlocks = 304;     // fixed partition of the scans (two per SM on a GB300)
 constexpr int kScanThreads = 512;
 
 struct ScanTmp {

@@ -84,7 +84,7 @@ struct WalkArgs {
 
 struct ForceArgs {
     const uint2 *gr_r;
-    const uint4 *gr_a;
+    const uint4 *gr_a, *gr_b;        // group grid boxes (qmin, set), (qmax, -)
     const unsigned *gr_nc, *gr_np;
     const unsigned long long *gr_co, *gr_po;
     const unsigned *gr_nf;           // far PP segment (no pair within r_out)
@@ -184,6 +184,7 @@ int walk_warps(unsigned stack_cap);   // warps of a walk launch with this stack 
 constexpr unsigned kWalkSpill = 4096;    // per-warp spill entries of the walk stack (global memory)
 int walk_launch(const WalkArgs &A, int phase, cudaStream_t st);    // 0 count+scan, 1 fill, 2 one pass
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st);
+constexpr int kRedBlocksMax = 256;    // partial-sum slots of the force's energy / momentum reduction
 int force_reduce_launch(const ForceArgs &A, cudaStream_t st);
 int nb_launch(const NbArgs &A, cudaStream_t st);
 

@@ -3,16 +3,18 @@
 //
 // Who needs it: code that must not call cudaMalloc -- a process whose device
 // memory is owned entirely by another allocator (a framework's caching
-// allocator or a fixed arena), a real-time loop that may not allocate, or a
-// caller preparing work that will later be captured into a CUDA graph.  The
-// regular entry points size their workspace with cudaMalloc on first use;
-// this one uses a fixed scratch array that lives in the library image.
+// allocator or a fixed arena), or a real-time loop that may not allocate.
+// The regular entry points size their workspace with cudaMalloc on first
+// use; this one uses a fixed scratch array that lives in the library image.
 //
 // The scratch is a file-scope __device__ array of kNoallocBytes (about
 // 4.3 MiB).  Every GPU on which the library is loaded holds it until the
 // process exits.  In host code the array's name is only a host-side
 // stand-in, so its device address is looked up with cudaGetSymbolAddress
-// once per device (on that device's first call) and cached.
+// once per device (on that device's first call, with that device current)
+// and cached for the life of the process; a cudaDeviceReset of the device
+// invalidates it, so the entry point must not be called on that device
+// afterwards.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -299,13 +299,13 @@ int orbit_launch(const OrbitArgs &A, cudaStream_t st) {
     const size_t smem = (size_t)kOrbWarps * A.stack_cap * sizeof(unsigned);
     if (cudaFuncSetAttribute(k_orbit_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
-    k_orbit_prep<<<152 * 8, 256, 0, st>>>(A);
+    k_orbit_prep<<<sm_count() * 8, 256, 0, st>>>(A);
     int nk = 1;
-    for (int l = kLevels - 1; l >= 0; l--, nk++) k_orbit_nodes<<<152 * 4, 256, 0, st>>>(A, l);
-    k_orbit_groups<<<152 * 4, 256, 0, st>>>(A);
+    for (int l = kLevels - 1; l >= 0; l--, nk++) k_orbit_nodes<<<sm_count() * 4, 256, 0, st>>>(A, l);
+    k_orbit_groups<<<sm_count() * 4, 256, 0, st>>>(A);
     int per_sm = (int)((200u * 1024u) / (smem + 24u * 1024u));
     per_sm = per_sm < 1 ? 1 : (per_sm > 12 ? 12 : per_sm);
-    k_orbit_search<<<152 * per_sm, kOrbThreads, smem, st>>>(A);
+    k_orbit_search<<<sm_count() * per_sm, kOrbThreads, smem, st>>>(A);
     return nk + 2;
 }
 

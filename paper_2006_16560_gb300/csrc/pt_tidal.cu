@@ -253,7 +253,8 @@ int report(pt_ctx *ctx, int rc, const char *what) {
     return pt::ctx_fail(ctx, rc, msg);
 }
 
-constexpr int kGrid = 152 * 4, kBlock = 256;
+constexpr int kBlock = 256;
+int tidal_grid() { return pt::sm_count() * 4; }
 
 }  // namespace
 
@@ -273,7 +274,7 @@ int pt_tidal_points(pt_ctx *ctx, int order, int64_t n, const double *r_cm, const
     const double *dc = (const double *)S.in(d_c, n * 8);
     double *pts = (double *)S.out(points, n * np * 24);
     if (S.rc != PT_OK) return report(ctx, S.rc, "pt_tidal_points");
-    k_tidal_points<<<kGrid, kBlock, 0, S.st>>>(order, n, cm, dc, pts);
+    k_tidal_points<<<tidal_grid(), kBlock, 0, S.st>>>(order, n, cm, dc, pts);
     return report(ctx, S.finish(), "pt_tidal_points");
 }
 
@@ -290,7 +291,7 @@ int pt_tidal_tensor(pt_ctx *ctx, int order, int64_t n, const double *acc, const 
     const double *dc = (const double *)S.in(d_c, n * 8);
     double *t = (double *)S.out(T, n * ne * 8);
     if (S.rc != PT_OK) return report(ctx, S.rc, "pt_tidal_tensor");
-    k_tidal_fit<<<kGrid, kBlock, 0, S.st>>>(order, n, a, dc, t);
+    k_tidal_fit<<<tidal_grid(), kBlock, 0, S.st>>>(order, n, a, dc, t);
     return report(ctx, S.finish(), "pt_tidal_tensor");
 }
 
@@ -309,7 +310,7 @@ int pt_tidal_eval(pt_ctx *ctx, int order, int64_t n_query, const int64_t *owner,
     const double *r = (const double *)S.in(rel, n_query * 24);
     double *o = (double *)S.out(acc_out, n_query * 24);
     if (S.rc != PT_OK) return report(ctx, S.rc, "pt_tidal_eval");
-    k_tidal_eval<<<kGrid, kBlock, 0, S.st>>>(order, n_query, n_binaries, ow, t, ac, r, o);
+    k_tidal_eval<<<tidal_grid(), kBlock, 0, S.st>>>(order, n_query, n_binaries, ow, t, ac, r, o);
     return report(ctx, S.finish(), "pt_tidal_eval");
 }
 

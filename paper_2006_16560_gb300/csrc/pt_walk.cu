@@ -282,7 +282,7 @@ static int walk_blocks(unsigned stack_cap) {
     const size_t smem = (size_t)kWalkWarps * stack_cap * sizeof(unsigned);
     int per_sm = (int)((200u * 1024u) / (smem + 2048));
     per_sm = per_sm < 1 ? 1 : (per_sm > 16 ? 16 : per_sm);   // 16 x 4 warps: the SM's limit
-    return 152 * per_sm;
+    return sm_count() * per_sm;
 }
 
 int walk_warps(unsigned stack_cap) { return walk_blocks(stack_cap) * kWalkWarps; }

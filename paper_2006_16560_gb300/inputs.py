@@ -25,6 +25,10 @@ generators here reproduce that structure:
                       [1, 8.43] days, thermal eccentricities, Kroupa masses
                       0.08-40 Msun, Kepler's third law for the semi-major axes.
 * ``cluster_ensemble`` -- many independent clusters with log-uniform sizes.
+* ``wide_sparse_groups`` -- an adversarial layout for the mixed-precision
+                      near/far decision: two sparse walk groups tens of
+                      thousands of r_out wide whose members pair up across
+                      the face between them at r_out (1 -+ 1e-4).
 
 Every array is float64; positions are (n, 3) row-major.
 """
@@ -255,3 +259,37 @@ def cluster_ensemble(n_clusters: int, nmin: int, nmax: int, seed: int,
         c["r_in"] = 0.1 * c["r_out"]
         out.append(c)
     return out
+
+
+def wide_sparse_groups(r_out: float, k_sites: int, n_decoys: int, seed: int) -> np.ndarray:
+    """Positions (n, 3) of two sparse groups, each spanning a 32-unit cube
+    of a 64-unit box (~2e4 r_out at r_out = 0.0016).
+
+    The box is fixed by particles at (0, 0, 0) and (64, 64, 64); a third at
+    (32.5, 0.5, 0.5) is the first particle (lowest key) of the cube
+    [32, 64) x [0, 32)^2.  k_sites sites along the face x = 32 each hold a
+    particle b just below the face and a partner j = b + rho v just above it,
+    v within ~17 degrees of +x, rho = r_out (1 - 1e-4) for three sites in
+    four and r_out (1 + 1e-4) for the fourth.  Each of b and j gets n_decoys
+    companions 0.01-0.01 n_decoys further from the face (well outside r_out
+    of every other particle), so with n_leaf = n_decoys + 1 every leaf near
+    the face holds exactly one of b, j and its decoys, and a walk group's PP
+    entries that could be neighbours are never next to one another in its
+    list.  With n_group >= 1 + k_sites (n_decoys + 1) each cube is one group
+    whose members sit up to ~45 units from its first particle."""
+    rng = rng_for(seed)
+    pts = [(0.0, 0.0, 0.0), (64.0, 64.0, 64.0), (32.5, 0.5, 0.5)]
+    for k in range(k_sites):
+        y = 8.0 + 22.0 * (k + rng.uniform(0.2, 0.8)) / k_sites
+        z = rng.uniform(8.0, 30.0)
+        b = np.array([32.0 - rng.uniform(0.1, 0.8) * r_out, y, z])
+        v = np.array([1.0, rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3)])
+        v /= np.linalg.norm(v)
+        j = b + r_out * (1.0 + 1e-4 if k % 4 == 3 else 1.0 - 1e-4) * v
+        pts += [tuple(b), tuple(j)]
+        for side, base in ((-1.0, b), (1.0, j)):
+            for q in range(n_decoys):
+                d = base + side * np.array([0.01 + 0.01 * q, rng.uniform(-0.01, 0.01),
+                                            rng.uniform(-0.01, 0.01)])
+                pts.append(tuple(d))
+    return np.array(pts, dtype=np.float64)

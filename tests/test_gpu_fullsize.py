@@ -83,7 +83,7 @@ def test_binaries_1m(ctx):
 
 def test_kroupa_plummer_10m(ctx):
     d = inputs.plummer(10_000_000, 2, masses="kroupa")
-    sampled_parity(ctx, d, c2_params(), 100, 9, check_mixed=False)
+    sampled_parity(ctx, d, c2_params(), 100, 9)
 
 
 def test_kroupa95_binaries_200k(ctx):

@@ -196,6 +196,35 @@ def test_lattice_at_the_r_out_boundary(ctx, spacing):
             assert np.percentile(e, 99) <= MIXED_P99 and e.max() <= MIXED_MAX
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+@pytest.mark.parametrize("n_group,n_leaf,k_sites", [(64, 4, 15), (96, 4, 23), (24, 8, 2)])
+def test_wide_sparse_groups_neighbours_exact(ctx, seed, n_group, n_leaf, k_sites):
+    """Two walk groups each ~2e4 r_out wide (r_out = 0.0016, the serving
+    radii's scale) whose members pair up across the face between them at
+    r_out (1 -+ 1e-4).  The mixed kernel votes near / far on float32 offsets
+    from the group's first particle, whose rounding here reaches ~1e-3 of
+    r_out: a fixed 2^-10 margin calls about one true neighbour in ten far.
+    The per-group bound must send every such pair to the exact float64 test,
+    so the neighbour sets equal brute force in both precisions; the float64
+    forces match the oracle tree."""
+    r_out = 0.0016
+    pos = inputs.wide_sparse_groups(r_out, k_sites, n_leaf - 1, seed)
+    mass = np.full(len(pos), 1.0 / len(pos))
+    p = c1_params(order=2, n_leaf=n_leaf, n_group=n_group, r_out=r_out, r_in=0.1 * r_out, theta=0.5)
+    T = oracle.Tree(pos, mass, n_leaf, n_group)
+    assert T.ngroups == 2
+    a, phi, _ = T.force(p.theta, p.r_in, p.r_out, order=2)
+    off, _ = oracle.neighbours(pos, r_out)
+    assert off[-1] == 2 * (k_sites - k_sites // 4)
+    for prec in (B.PT_FP64, B.PT_MIXED):
+        p.precision = prec
+        g = run_gpu(ctx, pos, mass, p)
+        check_neighbours(g, pos, r_out)
+        if prec == B.PT_FP64:
+            assert rel_err(g["acc"], a).max() <= FP64_TOL
+            np.testing.assert_allclose(g["pot"], phi, rtol=FP64_TOL)
+
+
 def test_theta0_equals_direct(ctx):
     d = inputs.plummer(1500, 5, masses="kroupa")
     p = c1_params(theta=0.0, order=2)
@@ -315,6 +344,30 @@ def test_errors(ctx):
     T = oracle.Tree(d["pos"], d["mass"], 8, 64)
     a, _, _ = T.force(0.5, 0.02, 0.2, order=0)
     assert rel_err(acc, a).max() <= FP64_TOL
+
+
+def test_tree_outlives_its_context():
+    """A tree still alive when its context is destroyed keeps an empty handle:
+    using it is an argument error, freeing it touches nothing of the destroyed
+    context, and rebuilding it in a new context works."""
+    d = inputs.plummer(500, 6)
+    c1 = B.Context(0)
+    rc, h = B.pt_tree_build(c1.h, 500, d["pos"].ctypes.data, d["mass"].ctypes.data, c1_params().c())
+    assert rc == B.PT_OK
+    c1.close()                                   # destroys the context first
+    c2 = B.Context(0)
+    acc, pot = np.zeros((500, 3)), np.zeros(500)
+    rc, _, _ = B.pt_longrange_force(c2.h, h, acc.ctypes.data, pot.ctypes.data, None, None, 0)
+    assert rc == B.PT_ERR_ARG
+    rc, h2 = B.pt_tree_build(c2.h, 500, d["pos"].ctypes.data, d["mass"].ctypes.data, c1_params().c(), h)
+    assert rc == B.PT_OK and h2.value == h.value
+    rc, _, _ = B.pt_longrange_force(c2.h, h, acc.ctypes.data, pot.ctypes.data, None, None, 0)
+    assert rc == B.PT_OK
+    T = oracle.Tree(d["pos"], d["mass"], 8, 64)
+    a, _, _ = T.force(0.5, 0.005, 0.05, order=0)
+    assert rel_err(acc, a).max() <= FP64_TOL
+    c2.close()
+    assert B.pt_tree_free(h) == B.PT_OK            # after its second context is gone too
 
 
 @pytest.mark.parametrize("precision", [B.PT_FP64, B.PT_MIXED])
