@@ -276,7 +276,7 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->nd_c, C * 32));
     TRY(ensure(ctx, t->nd_q, C * 64));
     TRY(ensure(ctx, t->nd_t, C * 64));
-    TRY(ensure(ctx, t->nd_f, C * 64));
+    TRY(ensure(ctx, t->nd_f, C * 48));
     TRY(ensure(ctx, t->nd_bnd, C * 32));
     TRY(ensure(ctx, t->lcp, N + 32));
     TRY(ensure(ctx, t->tmp_a, std::max(C, N) * 4));

@@ -558,14 +558,15 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
     bb.x = qmx[0]; bb.y = qmx[1]; bb.z = qmx[2];
     nd_a[v] = a;
     nd_b[v] = bb;
+    // float record of the mixed kernel: float-float COM, M and -Q without its
+    // zz element (Q is traceless: -Qzz = Qxx + Qyy)
     float hx = __double2float_rn(com[0]), hy = __double2float_rn(com[1]), hz = __double2float_rn(com[2]);
-    nd_f[4 * v] = make_float4(hx, hy, hz, __double2float_rn(M));
-    nd_f[4 * v + 1] = make_float4(__double2float_rn(com[0] - (double)hx),
+    nd_f[3 * v] = make_float4(hx, hy, hz, __double2float_rn(M));
+    nd_f[3 * v + 1] = make_float4(__double2float_rn(com[0] - (double)hx),
                                   __double2float_rn(com[1] - (double)hy),
-                                  __double2float_rn(com[2] - (double)hz), __double2float_rn(Q[0]));
-    nd_f[4 * v + 2] = make_float4(__double2float_rn(Q[1]), __double2float_rn(Q[2]),
-                                  __double2float_rn(Q[3]), __double2float_rn(Q[4]));
-    nd_f[4 * v + 3] = make_float4(__double2float_rn(Q[5]), 0.f, 0.f, 0.f);
+                                  __double2float_rn(com[2] - (double)hz), __double2float_rn(-Q[0]));
+    nd_f[3 * v + 2] = make_float4(__double2float_rn(-Q[1]), __double2float_rn(-Q[3]),
+                                  __double2float_rn(-Q[4]), __double2float_rn(-Q[5]));
 }
 
 // Multipoles bottom-up: every leaf at once (k_moments_leaves), then the

@@ -1,16 +1,18 @@
 // pt_force.cu -- the P3T long-range force kernels, fused neighbour
 // extraction, the energy / momentum sums and the neighbour CSR.
 //
-// One CTA (4 warps) evaluates one walk group at a time, taking groups from
-// an atomic work counter in the order k_group_order writes (largest pass
-// configuration first).  Every warp holds all of the group's targets (two or
-// three per lane) and streams its own quarter of the group's lists: it
-// gathers 64 list entries into shared memory, then every lane reads them by
-// broadcast and accumulates.  The four warps' partial sums are reduced in
-// float64 at the end of the group.  A group has one cell list and two PP
-// segments: near (leaves within r_out of the group's box: changeover and
-// neighbour tests) and far (every pair at least r_out apart: plain
-// Newtonian pairs).
+// Mixed precision: every warp evaluates one walk group at a time, taking
+// groups from an atomic work counter in the order k_group_order writes
+// (largest pass configuration first).  The warp holds all of the group's
+// targets (two or three per lane) and streams the group's whole lists: it
+// gathers 128 list entries into shared memory, then every lane reads them by
+// broadcast and accumulates; at the end of a pass the lanes write their
+// targets' results themselves (no block-wide barrier or cross-warp sum).
+// Float64: one CTA (4 warps) per group, each warp streaming a quarter of the
+// lists, the four partial sums added in float64.  A group has one cell list
+// and two PP segments: near (leaves within r_out of the group's box:
+// changeover and neighbour tests) and far (every pair at least r_out apart:
+// plain Newtonian pairs).
 //
 // Pair force (Sec. 5.1, Eq. 11; Sec. 6.1, Eqs. 15-17), for x_ij > 0:
 //   a_i += m_j (x_j - x_i) (1 - K(x)) / r^3,  P_i += m_j (1 - W(x)) / r
@@ -40,9 +42,10 @@ namespace pt {
 constexpr int kFWarps = 4;
 constexpr int kFThreads = 32 * kFWarps;
 #ifndef PT_FORCE_TILE
-#define PT_FORCE_TILE 64
+#define PT_FORCE_TILE 128
 #endif
-constexpr int kJ = PT_FORCE_TILE;   // list entries per warp tile
+constexpr int kJ = PT_FORCE_TILE;   // list entries per warp tile of the mixed kernel
+constexpr int kJD = 64;             // list entries per warp tile of the float64 kernel
 #ifndef PT_FORCE_UNROLL_PAIRS
 #define PT_FORCE_UNROLL_PAIRS 1
 #endif
@@ -385,8 +388,9 @@ __device__ __forceinline__ void pp_tile_far(const ulonglong2 (*sQ)[kJ / 2], int 
 
 template <int NI, int J, int ORDER, bool NB, bool MD>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                             const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
-                             unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
+                             const ChgF &C, double rout2, double rout, double c2,
+                             ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ], float2 (*sF)[3][4][32],
+                             double (*sE)[4][32]) {
     constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = lane / L, l = lane % L;
@@ -426,46 +430,45 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         }
         const unsigned nc = A.gr_nc[g];
         const unsigned long long co = A.gr_co[g];
-        constexpr int R = 4 * (kJ / 2);                 // floats per row of the pair layout
-        float *rows = reinterpret_cast<float *>(sP[w]);
-        for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
+        for (unsigned t = 0; t < nc; t += kJ) {
             const int cnt = (int)min((unsigned)kJ, nc - t);
             const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
+            // lane -> pairs P = lane, lane + 32, ..: entries a = (P / J) 2J + P mod J and
+            // b = a + J; each row of a pair is one 128-bit store
 #pragma unroll
-            for (int h = 0; h < kJ / 32; h++) {
-                const int e = lane + 32 * h;
-                if (e < cnt2) {
-                    // entry e -> pair P = (e / 2J) J + (e mod J), half (e mod 2J) / J
-                    const int m = e / (2 * J), r = e - m * 2 * J;
-                    const int half = r >= J ? 1 : 0;
-                    const int P = m * J + r - half * J;
-                    float x = 1e15f, y = 1e15f, z = 1e15f, ms = 0.0f;   // padding: massless, far away
-                    float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f, q4 = 0.0f, q5 = 0.0f;
-                    if (e < cnt) {
-                        const unsigned v = A.cells[co + t + e];
-                        const float4 f0 = A.nd_f[4 * v], f1 = A.nd_f[4 * v + 1];
-                        x = (f0.x - Hg.x) + (f1.x - Lg.x);
-                        y = (f0.y - Hg.y) + (f1.y - Lg.y);
-                        z = (f0.z - Hg.z) + (f1.z - Lg.z);
-                        ms = f0.w;
-                        if (ORDER == 2) {
-                            const float4 f2 = A.nd_f[4 * v + 2], f3 = A.nd_f[4 * v + 3];
-                            // stored negated: -Q d then feeds the acceleration directly
-                            q0 = -f1.w; q1 = -f2.x; q2 = -f2.y; q3 = -f2.z; q4 = -f2.w; q5 = -f3.x;
+            for (int h = 0; h < kJ / 64; h++) {
+                const int P = lane + 32 * h;
+                if (2 * P < cnt2) {
+                    const int ea = (P / J) * 2 * J + (P % J), eb = ea + J;
+                    float x[2], y[2], z[2], ms[2], q[2][6];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int e = u ? eb : ea;
+                        x[u] = 1e15f; y[u] = 1e15f; z[u] = 1e15f; ms[u] = 0.0f;   // padding: massless, far away
+#pragma unroll
+                        for (int c = 0; c < 6; c++) q[u][c] = 0.0f;
+                        if (e < cnt) {
+                            const unsigned v = A.cells[co + t + e];
+                            const float4 f0 = A.nd_f[3 * v], f1 = A.nd_f[3 * v + 1];
+                            x[u] = (f0.x - Hg.x) + (f1.x - Lg.x);
+                            y[u] = (f0.y - Hg.y) + (f1.y - Lg.y);
+                            z[u] = (f0.z - Hg.z) + (f1.z - Lg.z);
+                            ms[u] = f0.w;
+                            if (ORDER == 2) {
+                                // the record holds -Q (so -Q d feeds the acceleration
+                                // directly) without its zz element: -Qzz = Qxx + Qyy
+                                const float4 f2 = A.nd_f[3 * v + 2];
+                                q[u][0] = f1.w; q[u][1] = f2.x; q[u][2] = -(f1.w + f2.x);
+                                q[u][3] = f2.y; q[u][4] = f2.z; q[u][5] = f2.w;
+                            }
                         }
                     }
-                    float *b = rows + 4 * P + half;
-                    b[0] = x;
-                    b[2] = y;
-                    b[R] = z;
-                    b[R + 2] = ms;
-                    if (ORDER == 2) {        // (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz)
-                        b[2 * R] = q0;
-                        b[2 * R + 2] = q1;
-                        b[3 * R] = q2;
-                        b[3 * R + 2] = q3;
-                        b[4 * R] = q4;
-                        b[4 * R + 2] = q5;
+                    sP[w][0][P] = make_ulonglong2(pk2(x[0], x[1]), pk2(y[0], y[1]));
+                    sP[w][1][P] = make_ulonglong2(pk2(z[0], z[1]), pk2(ms[0], ms[1]));
+                    if (ORDER == 2) {        // (Qxx, Qyy), (Qzz, Qxy), (Qxz, Qyz), all negated
+                        sP[w][2][P] = make_ulonglong2(pk2(q[0][0], q[1][0]), pk2(q[0][1], q[1][1]));
+                        sP[w][3][P] = make_ulonglong2(pk2(q[0][2], q[1][2]), pk2(q[0][3], q[1][3]));
+                        sP[w][4][P] = make_ulonglong2(pk2(q[0][4], q[1][4]), pk2(q[0][5], q[1][5]));
                     }
                 }
             }
@@ -505,40 +508,40 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         for (int k = 0; k < NI; k++) nvalid += valid[k] ? 1 : 0;
         unsigned n_full = 0, n_fast = 0;
         const unsigned ntarg = min((unsigned)(NI * L), gr.y - i0);   // targets of this pass
-        constexpr int R = 4 * (kJ / 2);                 // floats per row of the pair layout
-        float *rows = reinterpret_cast<float *>(sP[w]);
         // the near segment (changeover test per iteration), then the far one
         for (int seg = 0; seg < 2; seg++) {
             const unsigned np = seg == 0 ? A.gr_np[g] : A.gr_nf[g];
             const unsigned long long po = seg == 0 ? A.gr_po[g] : A.gr_fo[g];
-            for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
+            for (unsigned t = 0; t < np; t += kJ) {
                 const int cnt = (int)min((unsigned)kJ, np - t);
                 const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
 #pragma unroll
-                for (int h = 0; h < kJ / 32; h++) {
-                    const int e = lane + 32 * h;
-                    if (e < cnt2) {
-                        const int m = e / (2 * J), r = e - m * 2 * J;
-                        const int half = r >= J ? 1 : 0;
-                        const int P = m * J + r - half * J;
-                        float ox = 1e15f, oy = 1e15f, oz = 1e15f, ms = 0.0f, wj = 1.0f;   // padding: massless, far away
-                        unsigned p = 0xffffffffu;
-                        if (e < cnt) {
-                            p = A.pp[po + t + e];
-                            const float4 H = A.spH[p], L = A.spL[p];
-                            ox = (H.x - Hg.x) + (L.x - Lg.x);
-                            oy = (H.y - Hg.y) + (L.y - Lg.y);
-                            oz = (H.z - Hg.z) + (L.z - Lg.z);
-                            ms = H.w;
-                            wj = L.w;
+                for (int h = 0; h < kJ / 64; h++) {
+                    const int P = lane + 32 * h;
+                    if (2 * P < cnt2) {
+                        const int ea = (P / J) * 2 * J + (P % J), eb = ea + J;
+                        float ox[2], oy[2], oz[2], ms[2], wj[2];
+                        unsigned id[2];
+#pragma unroll
+                        for (int u = 0; u < 2; u++) {
+                            const int e = u ? eb : ea;
+                            ox[u] = 1e15f; oy[u] = 1e15f; oz[u] = 1e15f; ms[u] = 0.0f; wj[u] = 1.0f;   // padding
+                            id[u] = 0xffffffffu;
+                            if (e < cnt) {
+                                const unsigned p = A.pp[po + t + e];
+                                const float4 H = A.spH[p], L = A.spL[p];
+                                ox[u] = (H.x - Hg.x) + (L.x - Lg.x);
+                                oy[u] = (H.y - Hg.y) + (L.y - Lg.y);
+                                oz[u] = (H.z - Hg.z) + (L.z - Lg.z);
+                                ms[u] = H.w;
+                                wj[u] = L.w;
+                                id[u] = p;
+                            }
                         }
-                        float *b = rows + 4 * P + half;
-                        b[0] = ox;
-                        b[2] = oy;
-                        b[R] = oz;
-                        b[R + 2] = ms;
-                        if (MD) b[2 * R] = wj;
-                        sI[w][2 * P + half] = p;
+                        sP[w][0][P] = make_ulonglong2(pk2(ox[0], ox[1]), pk2(oy[0], oy[1]));
+                        sP[w][1][P] = make_ulonglong2(pk2(oz[0], oz[1]), pk2(ms[0], ms[1]));
+                        if (MD) sP[w][2][P].x = pk2(wj[0], wj[1]);
+                        reinterpret_cast<uint2 *>(sI[w])[P] = make_uint2(id[0], id[1]);
                     }
                 }
                 __syncwarp();
@@ -573,17 +576,35 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
             atomicAdd(&A.st->pp_fast, (unsigned long long)n_fast);
         }
     }
-    // ---- sum the J sub-streams of each target, then hand over to the block
+    // ---- sum the J sub-streams of each target (fixed order) and write it:
+    // the self entry m_i 2 / (s_i (r_out + r_in)) removed, caller's order
 #pragma unroll
-    for (int k = 0; k < NI; k++)
+    for (int k = 0; k < NI; k++) {
+        double v[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const float2 a = acc[k][c][lane];
-            double v = (double)a.x + (double)a.y;
+            v[c] = (double)a.x + (double)a.y;
 #pragma unroll
-            for (int o = L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (s == 0) red[w][l + L * k][c] = v;
+            for (int o = L; o < 32; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
         }
+        if (s == 0 && valid[k]) {
+            const unsigned p = pid[k];
+            const double m = A.sp64[p].w;
+            const double P = v[3] - (MD ? m * c2 / A.ssc[p] : m * c2);
+            const unsigned i = A.perm[p];
+            const double ax = A.G * v[0], ay = A.G * v[1], az = A.G * v[2], phi = -A.G * P;
+            A.acc[3ull * i] = ax;
+            A.acc[3ull * i + 1] = ay;
+            A.acc[3ull * i + 2] = az;
+            A.pot[i] = phi;
+            double *e = &sE[w][0][lane];      // this lane's energy / momentum partials
+            e[0] += 0.5 * m * phi;
+            e[32] += m * ax;
+            e[64] += m * ay;
+            e[96] += m * az;
+        }
+    }
 }
 
 // Final per-target sums (threads 0..slots-1): fixed-order float64 reduction
@@ -641,15 +662,16 @@ constexpr int kPassClasses = 6;
 // runs the matching instantiation.
 template <int ORDER, bool NB, bool MD>
 __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                               const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
-                               unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
+                               const ChgF &C, double rout2, double rout, double c2,
+                               ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ], float2 (*sF)[3][4][32],
+                               double (*ep)[4][32]) {
     const unsigned rem = gr.y - i0;
-    if (rem <= 16) { group_pass_f<2, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 16; }
-    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 24; }
-    if (rem <= 32) { group_pass_f<2, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 32; }
-    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 48; }
-    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 64; }
-    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red);
+    if (rem <= 16) { group_pass_f<2, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 16; }
+    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 24; }
+    if (rem <= 32) { group_pass_f<2, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 32; }
+    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 48; }
+    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 64; }
+    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep);
     return 96;
 }
 
@@ -658,19 +680,18 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
     __shared__ ulonglong2 sP[kFWarps][5][kJ / 2];
     __shared__ float2 sF[kFWarps][3][4][32];
     __shared__ unsigned sI[kFWarps][kJ];
-    __shared__ double red[kFWarps][kSlotMax][4];
-    __shared__ double ered[kFWarps][4];
-    __shared__ unsigned gsh;
+    __shared__ double sE[kFWarps][4][32];    // per lane: sum m phi / 2, sum m a
     // lists left unusable by the walk (one-pass arrays exhausted, stack
     // overflow): do nothing, the host re-runs the walk and the force
     if (A.st->flags & (kErrListCap | kErrStack)) return;
     const unsigned ng = A.st->ngroups;
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
-        __syncthreads();
-        if (gsh >= ng) break;
-        const unsigned g = A.gr_ord[gsh];
+        unsigned gi = 0;
+        if (lane == 0) gi = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= ng) break;
+        const unsigned g = A.gr_ord[gi];
         const uint2 gr = A.gr_r[g];
         const Chg C64 = make_chg(A.sets[A.gr_a[g].w]);
         ChgF C;
@@ -684,16 +705,15 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         C.w3 = (float)(-5.0 * C64.lam);
         C.tiny = fmaxf((float)C64.tiny, 1e-36f);
         C.rout2m = vote_rout2(A.gr_a[g], A.gr_b[g], A.sets[A.gr_a[g].w]);
-        double ep[4] = {0, 0, 0, 0};
-        for (unsigned i0 = 0; i0 < gr.y;) {
-            const unsigned slots =
-                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sP, sI, sF, red);
-            __syncthreads();
-            write_targets(A, gr, i0, slots, C64.c2, red, ep);
-            __syncthreads();
-            i0 += slots;
-        }
-        group_partials(A, g, ep, ered);
+#pragma unroll
+        for (int c = 0; c < 4; c++) sE[w][c][lane] = 0.0;
+        for (unsigned i0 = 0; i0 < gr.y;)
+            i0 += mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, C64.c2, sP, sI, sF, sE);
+        __syncwarp();
+        double ep[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) ep[c] = warp_sum(sE[w][c][lane]);
+        if (lane == 0) A.gpart[g] = make_double4(ep[0], ep[1], ep[2], ep[3]);
     }
 }
 
@@ -812,8 +832,8 @@ __device__ __forceinline__ void pp_tile_d_far(const double4 *sP, int cnt, const 
 
 template <int NI, int ORDER, bool NB, bool MD>
 __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                             const Chg &C, double4 (*sA)[kJ], double4 (*sB)[kJ],
-                             double2 (*sC)[kJ], unsigned (*sI)[kJ], double (*sS)[kJ],
+                             const Chg &C, double4 (*sA)[kJD], double4 (*sB)[kJD],
+                             double2 (*sC)[kJD], unsigned (*sI)[kJD], double (*sS)[kJD],
                              double (*red)[kSlotMax][4]) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double xx[2], xy[2], xz[2], st[2];
@@ -835,10 +855,10 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
         for (int c = 0; c < 4; c++) pa[s][c] = 0.0;
     const unsigned nc = A.gr_nc[g];
     const unsigned long long co = A.gr_co[g];
-    for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
-        const int cnt = (int)min((unsigned)kJ, nc - t);
+    for (unsigned t = w * kJD; t < nc; t += kFWarps * kJD) {
+        const int cnt = (int)min((unsigned)kJD, nc - t);
 #pragma unroll
-        for (int h = 0; h < kJ / 32; h++) {
+        for (int h = 0; h < kJD / 32; h++) {
             const int e = lane + 32 * h;
             if (e < cnt) {
                 const unsigned v = A.cells[co + t + e];
@@ -859,10 +879,10 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
     for (int seg = 0; seg < 2; seg++) {
         const unsigned np = seg == 0 ? A.gr_np[g] : A.gr_nf[g];
         const unsigned long long po = seg == 0 ? A.gr_po[g] : A.gr_fo[g];
-        for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
-            const int cnt = (int)min((unsigned)kJ, np - t);
+        for (unsigned t = w * kJD; t < np; t += kFWarps * kJD) {
+            const int cnt = (int)min((unsigned)kJD, np - t);
 #pragma unroll
-            for (int h = 0; h < kJ / 32; h++) {
+            for (int h = 0; h < kJD / 32; h++) {
                 const int e = lane + 32 * h;
                 if (e < cnt) {
                     const unsigned p = A.pp[po + t + e];
@@ -889,11 +909,11 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
 
 template <int ORDER, bool NB, bool MD>
 __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
-    __shared__ double4 sA[kFWarps][kJ];
-    __shared__ double4 sB[kFWarps][kJ];
-    __shared__ double2 sC[kFWarps][kJ];
-    __shared__ unsigned sI[kFWarps][kJ];
-    __shared__ double sS[kFWarps][MD ? kJ : 1];
+    __shared__ double4 sA[kFWarps][kJD];
+    __shared__ double4 sB[kFWarps][kJD];
+    __shared__ double2 sC[kFWarps][kJD];
+    __shared__ unsigned sI[kFWarps][kJD];
+    __shared__ double sS[kFWarps][MD ? kJD : 1];
     __shared__ double red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
@@ -912,9 +932,9 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y; i0 += kIB) {
             if (gr.y - i0 > 32)
-                group_pass_d<2, ORDER, NB, MD>(A, g, gr, i0, C, sA, sB, sC, sI, (double (*)[kJ])sS, red);
+                group_pass_d<2, ORDER, NB, MD>(A, g, gr, i0, C, sA, sB, sC, sI, (double (*)[kJD])sS, red);
             else
-                group_pass_d<1, ORDER, NB, MD>(A, g, gr, i0, C, sA, sB, sC, sI, (double (*)[kJ])sS, red);
+                group_pass_d<1, ORDER, NB, MD>(A, g, gr, i0, C, sA, sB, sC, sI, (double (*)[kJD])sS, red);
             __syncthreads();
             write_targets(A, gr, i0, kIB, C.c2, red, ep);
             __syncthreads();

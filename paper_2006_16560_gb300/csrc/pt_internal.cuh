@@ -12,7 +12,7 @@
 //              nd_b  uint4 (qmax xyz, first child)
 //              nd_r  uint2 (begin, count)
 //              nd_c  double4 (com xyz, M);  nd_q double4 x 2 (Q xx yy zz xy, xz yz T-trace 0)
-//              nd_f  float4 x 4 (hi(com) M | lo(com) Qxx | Qyy Qzz Qxy Qxz | Qyz 0 0 0)
+//              nd_f  float4 x 3 (hi(com) M | lo(com) -Qxx | -Qyy -Qxy -Qxz -Qyz), 48 B
 //   groups     gr_r  uint2 (begin, count); gr_a uint4 (qmin, set); gr_b uint4 (qmax, root)
 //              gr_nc, gr_np u32 list lengths; gr_co, gr_po u64 list offsets;
 //              gr_nf u32, gr_fo u64: far PP segment (leaves opened for the
