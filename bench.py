@@ -288,7 +288,10 @@ def serve_leg(ctx, duration_s):
     """Serving workload: 64 resident Kroupa Plummer simulations, N log-uniform
     in 2,000-2,000,000 (seed 5), theta 0.4, leaf 16, FP32-mixed, neighbour lists
     on, HBM budget 150 GB; Poisson arrivals at 200 requests/s, each request a
-    drift + long-range force + kick of one simulation."""
+    drift + long-range force + kick of one simulation.  The server's defaults:
+    4 workers, simulations of 2^20 particles or more on two low-priority
+    workers, the rest on two high-priority ones, batches of up to 2^22
+    particles."""
     import torch
     from paper_2006_16560_gb300 import binding as B
     from paper_2006_16560_gb300 import inputs
@@ -308,12 +311,13 @@ def serve_leg(ctx, duration_s):
     # warm the pipeline's buffers with one request per simulation
     for t in [srv.submit(i, 0.0, 0.0) for i in ids]:
         srv.wait(t)
-    r = poisson_load(srv, ids, rate=200.0, duration_s=duration_s, seed=6, dt_drift=1e-5, dt_kick=1e-5)
+    r = poisson_load(srv, ids, rate=200.0, duration_s=duration_s, seed=6, dt_drift=1e-5, dt_kick=1e-5,
+                     timeout=120.0)
     st = srv.stats()
     srv.close()
     r.update({"workload": "64 resident Kroupa Plummer simulations, N log-uniform 2e3-2e6 (seed 5), "
                           "theta 0.4, leaf 16, FP32-mixed, neighbour lists on, budget 150 GB, "
-                          "Poisson arrivals 200/s (seed 6)",
+                          "Poisson arrivals 200/s (seed 6); 4 workers (2 for sims >= 2^20 particles)",
               "resident_particles": int(sizes.sum()), "resident_bytes": st["resident_bytes"],
               "max_batch_particles": st["max_batch_particles"], "setup_s": setup_s})
     return r
@@ -583,7 +587,7 @@ def main():
     ap.add_argument("--only-mixed", action="store_true", help="skip the FP64, e2e and batch legs (profiling)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-cluster batch leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--no-widened", action="store_true",
                     help="skip the orbit-neighbour and tidal-tensor legs")
     ap.add_argument("--no-10m", action="store_true", help="skip the N = 10^7 leg")

@@ -231,13 +231,19 @@ int pt_autotune(pt_ctx *ctx, int n_clusters, pt_cluster_desc *desc, const pt_par
 
 /* A server keeps the particle state of many simulations resident on the
  * device and serves "drift, long-range force, kick" requests for them with
- * continuous batching: a worker thread takes the queued requests in arrival
- * order (at most one per simulation, up to max_batch_particles particles) and
- * evaluates them in one pass of the pipeline (pt_batch_longrange_force), so
- * requests that arrive while a batch runs are served by the next batch.
+ * continuous batching: `workers` worker threads, each with its own context and
+ * stream, take the queued requests in arrival order (at most one per
+ * simulation, none for a simulation another worker has on the GPU, up to
+ * max_batch_particles particles) and evaluate them in one pass of the
+ * pipeline (pt_batch_longrange_force).  Requests that arrive while batches run
+ * are taken by the next free worker, and the workers' batches overlap on the
+ * device: with two or more workers, half of them serve the large simulations
+ * on low-priority streams and the others the small ones on high-priority
+ * streams, so small requests do not wait for a large simulation's batch.  A
+ * simulation's requests run one after the other, in submission order.
  * Admission is checked against hbm_budget_bytes: the resident state of every
  * simulation (about 100 bytes plus neighbour capacity per particle) plus a
- * workspace reserve of 1,536 bytes per batch particle must fit.
+ * workspace reserve of 1,536 bytes per batch particle and worker must fit.
  * A request on simulation s does x += v dt_drift (a free drift standing in for
  * the short-range integrator, out of scope here), computes the long-range
  * acceleration and potential (and neighbour lists if requested) of s, and
@@ -252,6 +258,11 @@ typedef struct {
     int neighbours;               /* 1: keep r_out neighbour lists per sim     */
     pt_params params;             /* theta, G, n_leaf, n_group, order,
                                      precision (r_in / r_out come per sim)     */
+    int workers;                  /* concurrent batch pipelines, 0 = 4, <= 16  */
+    int64_t large_sim_particles;  /* with 2+ workers: simulations of at least
+                                     this size go to the first half of the
+                                     workers (low stream priority), the rest
+                                     to the other half; 0 = 2^20             */
 } pt_server_config;
 
 typedef struct {
@@ -269,8 +280,9 @@ typedef struct {
     int64_t resident_bytes, max_batch_particles, queued;
 } pt_server_stats_t;
 
-/* Starts a server (and its worker thread) on the calling thread's current
- * device, with its own stream and context.  `ctx` must be a valid context (its
+/* Starts a server (and its worker threads) on the calling thread's current
+ * device, each worker with its own stream and context; max_batch_particles
+ * 0 means min(2^22, the budget's share).  `ctx` must be a valid context (its
  * device is used for checks only).  Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
 int pt_server_create(pt_ctx *ctx, const pt_server_config *cfg, pt_server **srv);
 /* Finishes the queued requests, stops the worker and frees all state. */
@@ -292,6 +304,8 @@ int pt_server_wait(pt_server *srv, int64_t ticket, double timeout_s, pt_request_
 int pt_server_read_sim(pt_server *srv, int sim_id, double *pos, double *vel, double *acc, double *pot);
 /* Totals since the server started. */
 int pt_server_stats(pt_server *srv, pt_server_stats_t *stats);
+/* Message of the last batch that failed (empty if none); static storage in srv. */
+const char *pt_server_last_error(pt_server *srv);
 
 /* ---- introspection (copies to HOST buffers; for tests and tools) ---- */
 

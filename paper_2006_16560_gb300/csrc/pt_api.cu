@@ -36,6 +36,12 @@ struct pt_ctx {
     // their device memory and detaches them, so a later pt_tree_free never
     // touches the destroyed context
     std::vector<pt_tree *> trees;
+    // device and pinned host blocks given up by buffers that grew: freed when
+    // the context is destroyed (or once they pass kRetiredMax), because a
+    // cudaFree / cudaFreeHost waits for the whole device, which would stall
+    // the streams of every other context (a server's other workers)
+    std::vector<void *> retired_dev, retired_host;
+    size_t retired_bytes = 0;
     struct TuneEntry {
         int nsets, nbucket, mbucket, order, precision;
         double theta;
@@ -84,10 +90,34 @@ struct Buf {
     T *as() const { return static_cast<T *>(p); }
 };
 
+constexpr size_t kRetiredMax = 2ull << 30;
+
+void free_retired(pt_ctx *ctx) {
+    for (void *q : ctx->retired_dev) cudaFree(q);
+    for (void *q : ctx->retired_host) cudaFreeHost(q);
+    ctx->retired_dev.clear();
+    ctx->retired_host.clear();
+    ctx->retired_bytes = 0;
+}
+
+void retire(pt_ctx *ctx, void *p, size_t bytes, bool host) {
+    if (!p) return;
+    (host ? ctx->retired_host : ctx->retired_dev).push_back(p);
+    ctx->retired_bytes += bytes;
+    if (ctx->retired_bytes > kRetiredMax) free_retired(ctx);
+}
+
+// A buffer that has to grow keeps a quarter of head room, and its old block
+// is retired rather than freed (see pt_ctx::retired_dev).
 int ensure(pt_ctx *ctx, Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return PT_OK;
-    b.release();
+    if (b.p) {
+        bytes = std::max(bytes, b.bytes + b.bytes / 4);
+        retire(ctx, b.p, b.bytes, false);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -248,10 +278,14 @@ SortTmp sort_tmp_of(pt_tree *t) {
 
 int alloc_build(pt_tree *t, unsigned n, int nsets) {
     pt_ctx *ctx = t->ctx;
-    if (t->cap_nodes == 0) {
-        unsigned long long c = 2ull * n / (unsigned)std::max(1, std::min(t->prm.n_leaf, 8)) +
-                               (unsigned long long)kLevels * nsets + 1024;
-        t->cap_nodes = (unsigned)std::min<unsigned long long>(c, 0x7fffffffull);
+    // node capacity: at least the estimate for this build's size (a tree
+    // reused for a larger set, e.g. a batch tree, grows here; overflows of
+    // the estimate double it in run_build)
+    {
+        const unsigned long long c = 2ull * n / (unsigned)std::max(1, std::min(t->prm.n_leaf, 8)) +
+                                     (unsigned long long)kLevels * nsets + 1024;
+        const unsigned est = (unsigned)std::min<unsigned long long>(c, 0x7fffffffull);
+        if (t->cap_nodes < est) t->cap_nodes = est;
     }
     if (t->cap_nodes < (unsigned)nsets + 1024) t->cap_nodes = nsets + 1024;
     const size_t N = n, C = t->cap_nodes, S = nsets;
@@ -431,9 +465,7 @@ int run_build(pt_tree *t, const double *pos, const double *mass) {
             unsigned long long c = 2ull * t->cap_nodes;
             if (c > 0x7fffffffull) return fail(ctx, PT_ERR_INTERNAL, "tree node count exceeds 2^31");
             t->cap_nodes = (unsigned)c;
-            t->nd_a.release();   // force re-allocation of node arrays
-            t->nd_b.release(); t->nd_r.release(); t->nd_c.release(); t->nd_q.release();
-            t->nd_t.release(); t->nd_f.release(); t->nd_bnd.release(); t->tmp_a.release(); t->tmp_b.release();
+            // node arrays are re-allocated for the new capacity by alloc_build
             continue;
         }
         t->built = true;
@@ -643,6 +675,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
             int nk = walk_launch(W, 2, st);
             CK(cudaEventRecord(ctx->ev[3], st));
             ForceArgs F = force_args(t, acc, pot, want_nb);
+            F.direct_groups = t->h.ngroups;           // known since the build's status read
             nk += force_launch(F, t->prm.precision, st);
             CK(cudaEventRecord(ctx->ev[4], st));
             TRY(copy_out());
@@ -691,6 +724,7 @@ int run_force(pt_tree *t, double *acc, double *pot, bool want_nb, unsigned long 
         nk += walk_launch(W, 1, st);
         CK(cudaEventRecord(ctx->ev[3], st));
         ForceArgs F = force_args(t, acc, pot, want_nb);
+        F.direct_groups = t->h.ngroups;
         nk += force_launch(F, t->prm.precision, st);
         CK(cudaEventRecord(ctx->ev[4], st));
         TRY(copy_out());
@@ -755,7 +789,10 @@ void fill_stats(pt_tree *t, pt_stats *s, const float *ms) {
 template <typename T>
 int ensure_pinned(pt_ctx *ctx, T *&p, size_t &cap, size_t n) {
     if (n <= cap && p) return PT_OK;
-    if (p) cudaFreeHost(p);
+    if (p) {
+        n = std::max(n, cap + cap / 4);
+        retire(ctx, p, cap * sizeof(T), true);
+    }
     p = nullptr;
     cap = 0;
     if (cudaMallocHost((void **)&p, n * sizeof(T)) != cudaSuccess) {
@@ -769,9 +806,10 @@ int ensure_pinned(pt_ctx *ctx, T *&p, size_t &cap, size_t n) {
 int batch_tables(pt_tree *t, int nsets) {
     pt_ctx *ctx = t->ctx;
     if (t->cap_tab < nsets) {
-        if (t->h_tab) cudaFreeHost(t->h_tab);
-        if (t->h_sets_pin) cudaFreeHost(t->h_sets_pin);
-        if (t->h_totals) cudaFreeHost(t->h_totals);
+        retire(ctx, t->h_tab, t->cap_tab * sizeof(BatchTab), true);
+        retire(ctx, t->h_sets_pin, t->cap_tab * sizeof(SetInfo), true);
+        retire(ctx, t->h_totals, t->cap_tab * sizeof(long long), true);
+        if (t->cap_tab > 0) nsets = std::max(nsets, t->cap_tab + t->cap_tab / 4);
         t->h_tab = nullptr; t->h_sets_pin = nullptr; t->h_totals = nullptr; t->cap_tab = 0;
         if (cudaMallocHost((void **)&t->h_tab, nsets * sizeof(BatchTab)) != cudaSuccess ||
             cudaMallocHost((void **)&t->h_sets_pin, nsets * sizeof(SetInfo)) != cudaSuccess ||
@@ -995,8 +1033,6 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
             TRY(size_onepass(t));
             if (t->h.nnodes + t->h.nnodes / 4 > t->cap_nodes) {
                 t->cap_nodes = t->h.nnodes + t->h.nnodes / 4 + 1024;
-                t->nd_a.release(); t->nd_b.release(); t->nd_r.release(); t->nd_c.release();
-                t->nd_q.release(); t->nd_t.release(); t->nd_f.release(); t->nd_bnd.release(); t->tmp_a.release(); t->tmp_b.release();
                 TRY(alloc_build(t, n, C));
             }
             if (want_nb) TRY(alloc_pairs(t, std::max<unsigned long long>(t->cap_pairs, t->h.npairs * 2 + 1024)));
@@ -1219,6 +1255,7 @@ int pt_ctx_destroy(pt_ctx *ctx) {
     if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    free_retired(ctx);
     delete ctx;
     return PT_OK;
 }

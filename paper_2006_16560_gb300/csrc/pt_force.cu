@@ -1,18 +1,18 @@
 // pt_force.cu -- the P3T long-range force kernels, fused neighbour
 // extraction, the energy / momentum sums and the neighbour CSR.
 //
-// Mixed precision: every warp evaluates one walk group at a time, taking
-// groups from an atomic work counter in the order k_group_order writes
-// (largest pass configuration first).  The warp holds all of the group's
-// targets (two or three per lane) and streams the group's whole lists: it
-// gathers 128 list entries into shared memory, then every lane reads them by
-// broadcast and accumulates; at the end of a pass the lanes write their
-// targets' results themselves (no block-wide barrier or cross-warp sum).
-// Float64: one CTA (4 warps) per group, each warp streaming a quarter of the
-// lists, the four partial sums added in float64.  A group has one cell list
-// and two PP segments: near (leaves within r_out of the group's box:
-// changeover and neighbour tests) and far (every pair at least r_out apart:
-// plain Newtonian pairs).
+// One CTA (4 warps) evaluates one walk group at a time, taking groups from
+// an atomic work counter in the order k_group_order writes (largest pass
+// configuration first).  Every warp holds all of the group's targets (two or
+// three per lane) and streams its own quarter of the group's lists: it
+// gathers a tile of list entries into shared memory (128 in the mixed
+// kernel, 64 in the float64 one), then every lane reads them by broadcast and
+// accumulates.  The four warps' partial sums are reduced in float64 at the
+// end of the group, in a fixed order.  Four warps per group rather than one
+// keep small sets (a few thousand particles, a few hundred groups) spread
+// over the whole GPU.  A group has one cell list and two PP segments: near
+// (leaves within r_out of the group's box: changeover and neighbour tests)
+// and far (every pair at least r_out apart: plain Newtonian pairs).
 //
 // Pair force (Sec. 5.1, Eq. 11; Sec. 6.1, Eqs. 15-17), for x_ij > 0:
 //   a_i += m_j (x_j - x_i) (1 - K(x)) / r^3,  P_i += m_j (1 - W(x)) / r
@@ -388,9 +388,8 @@ __device__ __forceinline__ void pp_tile_far(const ulonglong2 (*sQ)[kJ / 2], int 
 
 template <int NI, int J, int ORDER, bool NB, bool MD>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                             const ChgF &C, double rout2, double rout, double c2,
-                             ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ], float2 (*sF)[3][4][32],
-                             double (*sE)[4][32]) {
+                             const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
+                             unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = lane / L, l = lane % L;
@@ -430,7 +429,7 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         }
         const unsigned nc = A.gr_nc[g];
         const unsigned long long co = A.gr_co[g];
-        for (unsigned t = 0; t < nc; t += kJ) {
+        for (unsigned t = w * kJ; t < nc; t += kFWarps * kJ) {
             const int cnt = (int)min((unsigned)kJ, nc - t);
             const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
             // lane -> pairs P = lane, lane + 32, ..: entries a = (P / J) 2J + P mod J and
@@ -512,7 +511,7 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
         for (int seg = 0; seg < 2; seg++) {
             const unsigned np = seg == 0 ? A.gr_np[g] : A.gr_nf[g];
             const unsigned long long po = seg == 0 ? A.gr_po[g] : A.gr_fo[g];
-            for (unsigned t = 0; t < np; t += kJ) {
+            for (unsigned t = w * kJ; t < np; t += kFWarps * kJ) {
                 const int cnt = (int)min((unsigned)kJ, np - t);
                 const int cnt2 = (cnt + 2 * J - 1) / (2 * J) * (2 * J);   // <= kJ: kJ is a multiple of 2J
 #pragma unroll
@@ -576,35 +575,17 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
             atomicAdd(&A.st->pp_fast, (unsigned long long)n_fast);
         }
     }
-    // ---- sum the J sub-streams of each target (fixed order) and write it:
-    // the self entry m_i 2 / (s_i (r_out + r_in)) removed, caller's order
+    // ---- sum the J sub-streams of each target, then hand over to the block
 #pragma unroll
-    for (int k = 0; k < NI; k++) {
-        double v[4];
+    for (int k = 0; k < NI; k++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const float2 a = acc[k][c][lane];
-            v[c] = (double)a.x + (double)a.y;
+            double v = (double)a.x + (double)a.y;
 #pragma unroll
-            for (int o = L; o < 32; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+            for (int o = L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (s == 0) red[w][l + L * k][c] = v;
         }
-        if (s == 0 && valid[k]) {
-            const unsigned p = pid[k];
-            const double m = A.sp64[p].w;
-            const double P = v[3] - (MD ? m * c2 / A.ssc[p] : m * c2);
-            const unsigned i = A.perm[p];
-            const double ax = A.G * v[0], ay = A.G * v[1], az = A.G * v[2], phi = -A.G * P;
-            A.acc[3ull * i] = ax;
-            A.acc[3ull * i + 1] = ay;
-            A.acc[3ull * i + 2] = az;
-            A.pot[i] = phi;
-            double *e = &sE[w][0][lane];      // this lane's energy / momentum partials
-            e[0] += 0.5 * m * phi;
-            e[32] += m * ax;
-            e[64] += m * ay;
-            e[96] += m * az;
-        }
-    }
 }
 
 // Final per-target sums (threads 0..slots-1): fixed-order float64 reduction
@@ -662,16 +643,15 @@ constexpr int kPassClasses = 6;
 // runs the matching instantiation.
 template <int ORDER, bool NB, bool MD>
 __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
-                               const ChgF &C, double rout2, double rout, double c2,
-                               ulonglong2 (*sP)[5][kJ / 2], unsigned (*sI)[kJ], float2 (*sF)[3][4][32],
-                               double (*ep)[4][32]) {
+                               const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
+                               unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
-    if (rem <= 16) { group_pass_f<2, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 16; }
-    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 24; }
-    if (rem <= 32) { group_pass_f<2, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 32; }
-    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 48; }
-    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep); return 64; }
-    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, c2, sP, sI, sF, ep);
+    if (rem <= 16) { group_pass_f<2, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 16; }
+    if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 24; }
+    if (rem <= 32) { group_pass_f<2, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 32; }
+    if (rem <= 48) { group_pass_f<3, 2, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 48; }
+    if (rem <= 64) { group_pass_f<2, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 64; }
+    group_pass_f<3, 1, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red);
     return 96;
 }
 
@@ -680,17 +660,25 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
     __shared__ ulonglong2 sP[kFWarps][5][kJ / 2];
     __shared__ float2 sF[kFWarps][3][4][32];
     __shared__ unsigned sI[kFWarps][kJ];
-    __shared__ double sE[kFWarps][4][32];    // per lane: sum m phi / 2, sum m a
+    __shared__ double red[kFWarps][kSlotMax][4];
+    __shared__ double ered[kFWarps][4];
+    __shared__ unsigned gsh;
     // lists left unusable by the walk (one-pass arrays exhausted, stack
     // overflow): do nothing, the host re-runs the walk and the force
     if (A.st->flags & (kErrListCap | kErrStack)) return;
     const unsigned ng = A.st->ngroups;
-    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (;;) {
-        unsigned gi = 0;
-        if (lane == 0) gi = (unsigned)atomicAdd(&A.st->work[2], 1ull);
-        gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= ng) break;
+    for (unsigned it = 0;; it++) {
+        unsigned gi;
+        if (A.direct_groups) {                   // one group per CTA, in group order
+            if (it > 0 || blockIdx.x >= ng) break;
+            gi = blockIdx.x;
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+            __syncthreads();
+            gi = gsh;
+            if (gi >= ng) break;
+        }
         const unsigned g = A.gr_ord[gi];
         const uint2 gr = A.gr_r[g];
         const Chg C64 = make_chg(A.sets[A.gr_a[g].w]);
@@ -705,15 +693,16 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         C.w3 = (float)(-5.0 * C64.lam);
         C.tiny = fmaxf((float)C64.tiny, 1e-36f);
         C.rout2m = vote_rout2(A.gr_a[g], A.gr_b[g], A.sets[A.gr_a[g].w]);
-#pragma unroll
-        for (int c = 0; c < 4; c++) sE[w][c][lane] = 0.0;
-        for (unsigned i0 = 0; i0 < gr.y;)
-            i0 += mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, C64.c2, sP, sI, sF, sE);
-        __syncwarp();
-        double ep[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) ep[c] = warp_sum(sE[w][c][lane]);
-        if (lane == 0) A.gpart[g] = make_double4(ep[0], ep[1], ep[2], ep[3]);
+        double ep[4] = {0, 0, 0, 0};
+        for (unsigned i0 = 0; i0 < gr.y;) {
+            const unsigned slots =
+                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sP, sI, sF, red);
+            __syncthreads();
+            write_targets(A, gr, i0, slots, C64.c2, red, ep);
+            __syncthreads();
+            i0 += slots;
+        }
+        group_partials(A, g, ep, ered);
     }
 }
 
@@ -921,12 +910,18 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     // overflow): do nothing, the host re-runs the walk and the force
     if (A.st->flags & (kErrListCap | kErrStack)) return;
     const unsigned ng = A.st->ngroups;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
-        __syncthreads();
-        const unsigned g = gsh;
-        if (g >= ng) break;
+    for (unsigned it = 0;; it++) {
+        unsigned g;
+        if (A.direct_groups) {                   // one group per CTA
+            if (it > 0 || blockIdx.x >= ng) break;
+            g = blockIdx.x;
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+            __syncthreads();
+            g = gsh;
+            if (g >= ng) break;
+        }
         const uint2 gr = A.gr_r[g];
         const Chg C = make_chg(A.sets[A.gr_a[g].w]);
         double ep[4] = {0, 0, 0, 0};
@@ -1100,8 +1095,12 @@ __global__ void __launch_bounds__(1024) k_group_order(const uint2 *gr_r, unsigne
     }
 }
 
+// One CTA per group when the host knows the group count (CTAs then retire
+// group by group, so kernels of other streams -- other batches of a server --
+// get SMs within a group's time instead of waiting for the whole launch),
+// else a persistent grid that takes groups from an atomic counter.
 int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
-    const int blocks = sm_count() * 8;
+    const int blocks = A.direct_groups ? (int)A.direct_groups : sm_count() * 8;
     const bool md = A.massdep != 0;
     if (precision == 1) {
         k_group_order<<<1, 1024, 0, st>>>(A.gr_r, A.gr_ord, A.st);

@@ -105,6 +105,10 @@ struct ForceArgs {
     int want_nb;
     uint2 *pairs;                    // (sorted i, sorted j)
     unsigned long long pair_cap;
+    // groups of the launch when it is one CTA per group (known to the host
+    // after the build), 0 for a persistent launch that takes groups from an
+    // atomic counter (graph-captured batches, where the count is on the device)
+    unsigned direct_groups;
     double4 *gpart;                  // per group: sum m phi / 2, sum m a
     double4 *red_e;                  // per reduction block: partial sums of gpart
     unsigned long long *red_c;       // per reduction block: cell and PP interaction counts

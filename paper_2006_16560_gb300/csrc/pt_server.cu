@@ -3,20 +3,28 @@
 //
 // Each simulation's particle state (positions, velocities, masses, last
 // accelerations, potentials and neighbour lists) stays resident in device
-// memory between requests.  A worker thread forms batches from the queued
-// requests -- at most one request per simulation per batch, within a particle
-// cap derived from the HBM budget -- and runs each batch as one pass of the
-// pipeline (pt_batch_longrange_force over the batch's simulations) between a
-// drift and a kick kernel.  Requests that arrive while a batch is on the GPU
-// join the next batch as soon as it forms, so the device stays busy while the
-// queue is non-empty.  A request's result does not depend on the other
-// requests of its batch: every set keeps its own tree, lists and summation
-// order.
+// memory between requests.  Several worker threads, each with its own context
+// and stream, form batches from the queued requests -- in arrival order, at
+// most one request per simulation, skipping simulations that another worker
+// has on the GPU (so a simulation's requests run one after the other), within
+// a particle cap -- and run each batch as one pass of the pipeline
+// (pt_batch_longrange_force over the batch's simulations) between a drift and
+// a kick kernel.  Requests that arrive while batches are on the GPU are taken
+// by the next worker to become free, and the batches of different workers
+// overlap on the device, so a small request does not wait for a large
+// simulation's batch to finish.  With two or more workers, half of them
+// serve the large simulations on low-priority streams and the others serve
+// the rest on high-priority streams: the force kernels run one CTA per group,
+// so as the CTAs of a large batch retire the block scheduler starts those of
+// the small batches first.  A request's result does not depend on the
+// other requests of its batch or on the worker that ran it: every set keeps
+// its own tree, lists and summation order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -31,6 +39,9 @@ namespace {
 
 constexpr double kWorkspaceBytesPerParticle = 1536.0;   // tree, groups and lists per batch particle
 constexpr int kNbPerParticle = 16;                       // neighbour capacity per particle
+constexpr int kDefaultWorkers = 4;                       // concurrent batch pipelines
+constexpr long long kDefaultLarge = 1ll << 20;           // particles of a "large" simulation
+constexpr long long kDefaultBatchCap = 1ll << 22;        // particles per batch (default cap)
 
 struct KickEntry {
     double *pos, *vel;
@@ -54,6 +65,7 @@ __global__ void k_drift_kick(const KickEntry *tab, int kick) {
 
 struct Sim {
     bool live = false;
+    bool running = false;           // a worker has one of its requests on the GPU
     long long n = 0;
     double r_in = 0, r_out = 0;
     double *pos = nullptr, *vel = nullptr, *mass = nullptr, *acc = nullptr, *pot = nullptr;
@@ -89,9 +101,19 @@ bool is_dev(const void *p) {
 
 }  // namespace
 
-struct pt_server {
-    pt_ctx *ctx = nullptr;                 // the worker's own context and stream
+// One batch pipeline: its own context (batch tree, workspace) and stream,
+// and the drift / kick tables of its batch (pinned and device copies; drift
+// entries first, kick entries after them, uploaded once per batch).
+struct Worker {
+    int lane = 0;                   // 0: every simulation, 1: large ones, 2: the others
+    pt_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
+    KickEntry *h_tab = nullptr, *d_tab = nullptr;   // 2 x max_sims entries
+    std::thread th;
+};
+
+struct pt_server {
+    std::vector<Worker> workers;
     int device = 0;
     pt_server_config cfg{};
     long long max_batch = 0;
@@ -105,40 +127,59 @@ struct pt_server {
     std::thread worker;
     bool stop = false;
     std::chrono::steady_clock::time_point t0;
-    KickEntry *h_tab = nullptr, *d_tab = nullptr;   // pinned / device, one per simulation
     int tab_cap = 0;
     // totals
     long long batches = 0, served = 0, particles = 0, interactions = 0;
-    double busy_s = 0;
+    double busy_s = 0;              // time with at least one batch on the device
+    int active = 0;                 // batches on the device
+    double busy_since = 0;
     char err[256] = {0};
 
-    void run();
+    long long large = kDefaultLarge;
+    bool in_lane(int lane, const Sim &m) const {
+        return lane == 0 || (lane == 1) == (m.n >= large);
+    }
+    bool runnable(int lane) const {   // a queued request of the lane whose simulation is idle (lock held)
+        for (long long k : pending) {
+            const Sim &m = sims[reqs.at(k).sim];
+            if (!m.running && in_lane(lane, m)) return true;
+        }
+        return false;
+    }
+    void run(int w);
 };
 
-void pt_server::run() {
+void pt_server::run(int w) {
     cudaSetDevice(device);
+    Worker &W = workers[w];
     for (;;) {
         std::vector<long long> batch;
         std::vector<Sim> bs;                      // snapshots: the tables may grow meanwhile
         std::vector<double> dtd, dtk;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+            cv_work.wait(lk, [&] { return (stop && pending.empty()) || runnable(W.lane); });
             if (stop && pending.empty()) return;
-            // continuous batching: FIFO, one request per simulation, particle cap
+            // continuous batching: arrival order, one request per simulation,
+            // simulations on the GPU with another worker skipped (with all of
+            // their later requests: each simulation's requests stay in order),
+            // and a particle cap; a request that does not fit stays queued for
+            // the next batch
             std::vector<char> taken(sims.size(), 0);
             long long np = 0;
             for (auto it = pending.begin(); it != pending.end();) {
                 Req &r = reqs[*it];
-                const long long n = sims[r.sim].n;
-                if (taken[r.sim]) { ++it; continue; }
-                if (!batch.empty() && np + n > max_batch) break;
+                Sim &m = sims[r.sim];
+                if (taken[r.sim] || m.running || !in_lane(W.lane, m)) { ++it; continue; }
                 taken[r.sim] = 1;
-                np += n;
+                if (!batch.empty() && np + m.n > max_batch) { ++it; continue; }
+                np += m.n;
+                m.running = true;
                 batch.push_back(*it);
                 it = pending.erase(it);
             }
             const double t = now_s(t0);
+            if (active++ == 0) busy_since = t;
             for (long long k : batch) {
                 Req &r = reqs[k];
                 r.t_start = t;
@@ -165,25 +206,32 @@ void pt_server::run() {
             d[k].nb_offsets = cfg.neighbours ? s.nb_off : nullptr;
             d[k].nb_idx = cfg.neighbours ? s.nb_idx : nullptr;
             d[k].nb_capacity = cfg.neighbours ? s.nb_cap : 0;
-            h_tab[k] = KickEntry{s.pos, s.vel, s.acc, s.n, dtd[k]};
+            W.h_tab[k] = KickEntry{s.pos, s.vel, s.acc, s.n, dtd[k]};
             np += s.n;
         }
-        const double tb = now_s(t0);
-        cudaMemcpyAsync(d_tab, h_tab, B * sizeof(KickEntry), cudaMemcpyHostToDevice, stream);
-        k_drift_kick<<<dim3(64, B), 256, 0, stream>>>(d_tab, 0);
+        // drift entries [0, B), kick entries [B, 2B): one upload; the pinned
+        // table is rewritten only after the stream synchronisation below
+        for (int k = 0; k < B; k++) {
+            W.h_tab[B + k] = W.h_tab[k];
+            W.h_tab[B + k].dt = dtk[k];
+        }
+        cudaMemcpyAsync(W.d_tab, W.h_tab, 2 * B * sizeof(KickEntry), cudaMemcpyHostToDevice, W.stream);
+        k_drift_kick<<<dim3(64, B), 256, 0, W.stream>>>(W.d_tab, 0);
         pt_stats st{};
-        status = pt_batch_longrange_force(ctx, B, d.data(), &cfg.params, 0, &st);
-        for (int k = 0; k < B; k++) h_tab[k].dt = dtk[k];
-        cudaMemcpyAsync(d_tab, h_tab, B * sizeof(KickEntry), cudaMemcpyHostToDevice, stream);
-        k_drift_kick<<<dim3(64, B), 256, 0, stream>>>(d_tab, 1);
-        if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        status = pt_batch_longrange_force(W.ctx, B, d.data(), &cfg.params, 0, &st);
+        if (status != PT_OK && status != PT_ERR_CAPACITY) {
+            std::lock_guard<std::mutex> lk(mu);
+            snprintf(err, sizeof err, "worker %d: %s", w, pt_last_error(W.ctx));
+        }
+        k_drift_kick<<<dim3(64, B), 256, 0, W.stream>>>(W.d_tab + B, 1);
+        if (cudaStreamSynchronize(W.stream) != cudaSuccess) {
             (void)cudaGetLastError();
             status = PT_ERR_CUDA;
         }
         {
             std::lock_guard<std::mutex> lk(mu);
             const double t = now_s(t0);
-            busy_s += t - tb;
+            if (--active == 0) busy_s += t - busy_since;
             batches++;
             served += B;
             particles += np;
@@ -196,9 +244,11 @@ void pt_server::run() {
                 r.status = status;
                 r.done = true;
                 sims[r.sim].inflight--;
+                sims[r.sim].running = false;
             }
         }
         cv_done.notify_all();
+        cv_work.notify_all();     // the finished simulations' later requests may run now
     }
 }
 
@@ -207,7 +257,7 @@ extern "C" {
 int pt_server_create(pt_ctx *ctx, const pt_server_config *cfg, pt_server **out) {
     if (!ctx || !cfg || !out) return PT_ERR_ARG;
     *out = nullptr;
-    if (cfg->hbm_budget_bytes == 0 || cfg->max_sims < 1) return PT_ERR_ARG;
+    if (cfg->hbm_budget_bytes == 0 || cfg->max_sims < 1 || cfg->workers < 0 || cfg->workers > 16) return PT_ERR_ARG;
     pt_server *s = new (std::nothrow) pt_server;
     if (!s) return PT_ERR_OOM;
     s->cfg = *cfg;
@@ -215,27 +265,38 @@ int pt_server_create(pt_ctx *ctx, const pt_server_config *cfg, pt_server **out) 
         delete s;
         return PT_ERR_CUDA;
     }
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete s;
-        return PT_ERR_CUDA;
-    }
-    int rc = pt_ctx_create(&s->ctx, s->device, s->stream);
-    if (rc != PT_OK) {
-        cudaStreamDestroy(s->stream);
-        delete s;
-        return rc;
-    }
-    const double room = (double)cfg->hbm_budget_bytes / 2.0 / kWorkspaceBytesPerParticle;
-    s->max_batch = cfg->max_batch_particles > 0 ? cfg->max_batch_particles : (long long)std::min(room, 6.0e7);
+    const int nw = cfg->workers > 0 ? cfg->workers : kDefaultWorkers;
+    // every worker keeps a batch workspace: half the budget is theirs
+    const double room = (double)cfg->hbm_budget_bytes / 2.0 / nw / kWorkspaceBytesPerParticle;
+    s->max_batch = cfg->max_batch_particles > 0 ? cfg->max_batch_particles
+                                                : (long long)std::min(room, (double)kDefaultBatchCap);
     s->tab_cap = cfg->max_sims;
-    if (cudaMallocHost((void **)&s->h_tab, s->tab_cap * sizeof(KickEntry)) != cudaSuccess ||
-        cudaMalloc((void **)&s->d_tab, s->tab_cap * sizeof(KickEntry)) != cudaSuccess) {
+    s->large = cfg->large_sim_particles > 0 ? cfg->large_sim_particles : kDefaultLarge;
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
         (void)cudaGetLastError();
-        pt_server_destroy(s);
-        return PT_ERR_OOM;
+        prio_low = prio_high = 0;
+    }
+    s->workers.resize(nw);
+    for (int w = 0; w < nw; w++) {
+        Worker &W = s->workers[w];
+        W.lane = nw == 1 ? 0 : (w < nw / 2 ? 1 : 2);
+        if (cudaStreamCreateWithPriority(&W.stream, cudaStreamNonBlocking, W.lane == 1 ? prio_low : prio_high) !=
+                cudaSuccess ||
+            cudaMallocHost((void **)&W.h_tab, 2 * s->tab_cap * sizeof(KickEntry)) != cudaSuccess ||
+            cudaMalloc((void **)&W.d_tab, 2 * s->tab_cap * sizeof(KickEntry)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            pt_server_destroy(s);
+            return PT_ERR_OOM;
+        }
+        const int rc = pt_ctx_create(&W.ctx, s->device, W.stream);
+        if (rc != PT_OK) {
+            pt_server_destroy(s);
+            return rc;
+        }
     }
     s->t0 = std::chrono::steady_clock::now();
-    s->worker = std::thread([s] { s->run(); });
+    for (int w = 0; w < nw; w++) s->workers[w].th = std::thread([s, w] { s->run(w); });
     *out = s;
     return PT_OK;
 }
@@ -247,17 +308,20 @@ int pt_server_destroy(pt_server *s) {
         s->stop = true;
     }
     s->cv_work.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    for (Worker &W : s->workers)
+        if (W.th.joinable()) W.th.join();
     cudaSetDevice(s->device);
     for (Sim &m : s->sims)
         if (m.live) {
             cudaFree(m.pos); cudaFree(m.vel); cudaFree(m.mass); cudaFree(m.acc); cudaFree(m.pot);
             cudaFree(m.nb_off); cudaFree(m.nb_idx);
         }
-    if (s->h_tab) cudaFreeHost(s->h_tab);
-    if (s->d_tab) cudaFree(s->d_tab);
-    if (s->ctx) pt_ctx_destroy(s->ctx);
-    if (s->stream) cudaStreamDestroy(s->stream);
+    for (Worker &W : s->workers) {
+        if (W.h_tab) cudaFreeHost(W.h_tab);
+        if (W.d_tab) cudaFree(W.d_tab);
+        if (W.ctx) pt_ctx_destroy(W.ctx);
+        if (W.stream) cudaStreamDestroy(W.stream);
+    }
     delete s;
     return PT_OK;
 }
@@ -270,7 +334,7 @@ int pt_server_add_sim(pt_server *s, int64_t n, const double *pos, const double *
     const long long nbc = kNbPerParticle * n + 64;
     const size_t bytes = (size_t)n * (24 + 24 + 8 + 24 + 8 + 8) + 8 + (size_t)nbc * 4;
     std::lock_guard<std::mutex> lk(s->mu);
-    const double reserve = kWorkspaceBytesPerParticle * (double)s->max_batch;
+    const double reserve = kWorkspaceBytesPerParticle * (double)s->max_batch * (double)s->workers.size();
     if ((double)(s->resident + bytes) + reserve > (double)s->cfg.hbm_budget_bytes) return PT_ERR_CAPACITY;
     int id = -1;
     for (size_t k = 0; k < s->sims.size(); k++)
@@ -342,7 +406,7 @@ int pt_server_submit(pt_server *s, int sim_id, double dt_drift, double dt_kick, 
         s->sims[sim_id].inflight++;
         *ticket = t;
     }
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();      // workers of different lanes wait on this variable
     return PT_OK;
 }
 
@@ -387,6 +451,8 @@ int pt_server_read_sim(pt_server *s, int sim_id, double *pos, double *vel, doubl
         }
     return PT_OK;
 }
+
+const char *pt_server_last_error(pt_server *s) { return s ? s->err : "no server"; }
 
 int pt_server_stats(pt_server *s, pt_server_stats_t *out) {
     if (!s || !out) return PT_ERR_ARG;

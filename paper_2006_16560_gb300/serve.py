@@ -18,7 +18,8 @@ from . import binding as B
 
 class pt_server_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_batch_particles", C.c_int64),
-                ("max_sims", C.c_int), ("neighbours", C.c_int), ("params", B.pt_params)]
+                ("max_sims", C.c_int), ("neighbours", C.c_int), ("params", B.pt_params),
+                ("workers", C.c_int), ("large_sim_particles", C.c_int64)]
 
 
 class pt_request_info(C.Structure):
@@ -50,6 +51,7 @@ def _lib():
             ("pt_server_wait", I, [P, I64, D, C.POINTER(pt_request_info)]),
             ("pt_server_read_sim", I, [P, I, P, P, P, P]),
             ("pt_server_stats", I, [P, C.POINTER(pt_server_stats_t)]),
+            ("pt_server_last_error", C.c_char_p, [P]),
         ]:
             fn = getattr(L, name)
             fn.restype = res
@@ -62,10 +64,11 @@ class Server:
     """Resident-state serving loop for long-range kick requests."""
 
     def __init__(self, ctx: B.Context, params: B.Params, hbm_budget_bytes: float = 150e9,
-                 max_sims: int = 64, neighbours: bool = True, max_batch_particles: int = 0):
+                 max_sims: int = 64, neighbours: bool = True, max_batch_particles: int = 0,
+                 workers: int = 0, large_sim_particles: int = 0):
         self.ctx = ctx
         cfg = pt_server_config(int(hbm_budget_bytes), int(max_batch_particles), int(max_sims),
-                               1 if neighbours else 0, params.c())
+                               1 if neighbours else 0, params.c(), int(workers), int(large_sim_particles))
         h = C.c_void_p()
         rc = _lib().pt_server_create(ctx.h, C.byref(cfg), C.byref(h))
         if rc != B.PT_OK:
@@ -107,7 +110,7 @@ class Server:
         info = pt_request_info()
         rc = _lib().pt_server_wait(self.h, ticket, float(timeout), C.byref(info))
         if rc != B.PT_OK:
-            raise B.PTError(rc, "pt_server_wait")
+            raise B.PTError(rc, "pt_server_wait: " + self.last_error())
         return {k: getattr(info, k) for k, _ in info._fields_}
 
     def read(self, sid: int):
@@ -119,6 +122,9 @@ class Server:
         if rc != B.PT_OK:
             raise B.PTError(rc, "pt_server_read_sim")
         return pos, vel, acc, pot
+
+    def last_error(self) -> str:
+        return (_lib().pt_server_last_error(self.h) or b"").decode()
 
     def stats(self) -> dict:
         s = pt_server_stats_t()
@@ -138,7 +144,7 @@ class Server:
 
 
 def poisson_load(server: Server, sims: list[int], rate: float, duration_s: float, seed: int,
-                 dt_drift: float = 1e-4, dt_kick: float = 1e-4) -> dict:
+                 dt_drift: float = 1e-4, dt_kick: float = 1e-4, timeout: float = -1.0) -> dict:
     """Submit requests at Poisson arrival times (rate per second) for
     duration_s, each on a uniformly chosen simulation; wait for all of them.
     Returns latency percentiles (submit -> done, server clock), throughput and
@@ -166,7 +172,7 @@ def poisson_load(server: Server, sims: list[int], rate: float, duration_s: float
     t_start = time.perf_counter()
     th.start()
     th.join()
-    infos = [server.wait(t) for t in tickets]
+    infos = [server.wait(t, timeout) for t in tickets]
     wall = time.perf_counter() - t_start
     s1 = server.stats()
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3

@@ -370,6 +370,29 @@ def test_tree_outlives_its_context():
     assert B.pt_tree_free(h) == B.PT_OK            # after its second context is gone too
 
 
+def test_rebuild_with_a_much_larger_set(ctx):
+    """A tree first built over 1,000 particles and then rebuilt in place over
+    600,000 needs 600 times its node capacity: the rebuild sizes it for the
+    new set, and the result equals a fresh tree's (keys, forces, neighbours)."""
+    small = inputs.plummer(1000, 8, masses="kroupa")
+    big = inputs.plummer(600_000, 9, masses="kroupa")
+    p = B.Params(theta=0.4, r_in=0.0004, r_out=0.004, n_leaf=16, n_group=64, order=2,
+                 precision=B.PT_MIXED)
+    t = B.Tree(ctx, small["pos"], small["mass"], p)
+    n = len(big["mass"])
+    t.rebuild(big["pos"], big["mass"], p)
+    a1, p1 = np.zeros((n, 3)), np.zeros(n)
+    off1, idx1 = np.zeros(n + 1, dtype=np.int64), np.zeros(8 * n, dtype=np.int32)
+    tot1, _, _ = t.force(a1, p1, off1, idx1, 8 * n)
+    k1, _ = t.keys()
+    t.free()
+    g = run_gpu(ctx, big["pos"], big["mass"], p, device_buffers=False)
+    k2, _ = g["tree"].keys()
+    assert np.array_equal(k1, k2)
+    assert np.array_equal(a1, g["acc"]) and np.array_equal(p1, g["pot"])
+    assert np.array_equal(off1, g["nb_off"]) and np.array_equal(idx1[:tot1], g["nb_idx"])
+
+
 @pytest.mark.parametrize("precision", [B.PT_FP64, B.PT_MIXED])
 def test_one_pass_walk_matches_two_pass(ctx, precision):
     """A tree's first force call walks in two passes (count, scan, fill); later

@@ -12,6 +12,7 @@ from gpu_helpers import rel_err
 pytestmark = pytest.mark.gpu
 
 DT_DRIFT, DT_KICK = 2e-4, 1e-4
+WAIT_S = 60.0     # a request not served within this fails the test instead of hanging it
 
 
 @pytest.fixture(scope="module")
@@ -44,19 +45,43 @@ def test_result_is_the_same_alone_and_in_the_mix(ctx):
     alone = []
     for c in sims:                      # one request, nothing else queued
         s, (sid,) = _server(ctx, [c])
-        info = s.wait(s.submit(sid, DT_DRIFT, DT_KICK))
+        info = s.wait(s.submit(sid, DT_DRIFT, DT_KICK), timeout=WAIT_S)
         assert info["batch_size"] == 1
         alone.append(s.read(sid))
         s.close()
-    s, ids = _server(ctx, sims)         # all requests queued together
-    tickets = [s.submit(i, DT_DRIFT, DT_KICK) for i in ids]
-    infos = [s.wait(t) for t in tickets]
-    assert max(i["batch_size"] for i in infos) > 1
-    for sid, a in zip(ids, alone):
-        mixed = s.read(sid)
-        for x, y in zip(a, mixed):
+    # all requests queued together: one worker batches them; three workers
+    # run them in overlapping batches on separate streams
+    for workers in (1, 3):
+        s = Server(ctx, _params(), workers=workers, max_batch_particles=1 << 20)
+        ids = [s.add_sim(c["pos"], c["vel"], c["mass"], c["r_in"], c["r_out"]) for c in sims]
+        tickets = [s.submit(i, DT_DRIFT, DT_KICK) for i in ids]
+        infos = [s.wait(t, timeout=WAIT_S) for t in tickets]
+        if workers == 1:
+            assert max(i["batch_size"] for i in infos) > 1
+        for sid, a in zip(ids, alone):
+            mixed = s.read(sid)
+            for x, y in zip(a, mixed):
+                assert np.array_equal(x, y)
+        s.close()
+
+
+def test_concurrent_workers_keep_each_simulations_order(ctx):
+    """Several requests per simulation submitted at once: with three workers
+    a simulation's requests still run one after the other, in order, so the
+    state after k requests equals that of one worker serving them."""
+    sims = _sims(60, [4000, 9000, 2500])
+    out = {}
+    for workers in (1, 3):
+        s = Server(ctx, _params(), workers=workers)
+        ids = [s.add_sim(c["pos"], c["vel"], c["mass"], c["r_in"], c["r_out"]) for c in sims]
+        tickets = [s.submit(i, DT_DRIFT * (1 + k), DT_KICK) for k in range(3) for i in ids]
+        for t in tickets:
+            s.wait(t, timeout=WAIT_S)
+        out[workers] = [s.read(i) for i in ids]
+        s.close()
+    for a, b in zip(out[1], out[3]):
+        for x, y in zip(a, b):
             assert np.array_equal(x, y)
-    s.close()
 
 
 def test_request_is_drift_force_kick(ctx):
@@ -64,7 +89,7 @@ def test_request_is_drift_force_kick(ctx):
     (c,) = _sims(70, [6000])
     s, (sid,) = _server(ctx, [c])
     for _ in range(2):
-        s.wait(s.submit(sid, DT_DRIFT, DT_KICK))
+        s.wait(s.submit(sid, DT_DRIFT, DT_KICK), timeout=WAIT_S)
     pos, vel, acc, pot = s.read(sid)
     s.close()
     x, v = c["pos"].copy(), c["vel"].copy()
@@ -86,7 +111,7 @@ def test_request_is_drift_force_kick(ctx):
 
 def test_admission_by_budget(ctx):
     (c,) = _sims(90, [20000])
-    s = Server(ctx, _params(), hbm_budget_bytes=40e6, max_batch_particles=10000)
+    s = Server(ctx, _params(), hbm_budget_bytes=40e6, max_batch_particles=10000, workers=1)
     rc, _ = s.try_add_sim(c["pos"], c["vel"], c["mass"], c["r_in"], c["r_out"])
     assert rc == B.PT_ERR_CAPACITY          # larger than a batch may hold
     small = _sims(91, [5000])[0]
@@ -108,7 +133,7 @@ def test_admission_by_budget(ctx):
 def test_poisson_load_smoke(ctx):
     sims = _sims(120, [2000, 4000, 8000, 16000])
     s, ids = _server(ctx, sims)
-    r = poisson_load(s, ids, rate=200.0, duration_s=0.5, seed=3)
+    r = poisson_load(s, ids, rate=200.0, duration_s=0.5, seed=3, timeout=WAIT_S)
     assert r["requests"] > 0 and r["errors"] == 0
     assert r["latency_ms"]["p99"] >= r["latency_ms"]["p50"] > 0
     s.close()
