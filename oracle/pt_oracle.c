@@ -420,9 +420,15 @@ static void build_node(orc_tree *t, int64_t vi)
 
 /* Groups (this project's reading of "group-wise walk"): going down from the
  * root, a node with at most n_group particles, or a leaf, is one group;
- * otherwise its children are taken in key order, each child with more than
- * n_group particles is handled recursively, and consecutive smaller children
- * are packed greedily into groups of at most n_group particles. */
+ * otherwise its children are taken in key order and each child with more
+ * than n_group particles is handled recursively (a leaf that large is a
+ * group of its own).  The smaller children of a node with at most
+ * 8 n_group particles form runs of consecutive children, each cut in key
+ * order into groups of exactly n_group particles (the last one of a run
+ * smaller); those of a larger node are packed whole and greedily into
+ * groups of at most n_group (cutting there could join sparse children of a
+ * wide node into one group whose box reaches far).  A group's box is the
+ * tight box of its particles' grid cells. */
 static void group_emit(orc_tree *t, int64_t begin, int64_t count,
                        const uint32_t *qmin, const uint32_t *qmax, double smax)
 {
@@ -437,6 +443,30 @@ static void group_emit(orc_tree *t, int64_t begin, int64_t count,
     g->smax = smax;
 }
 
+/* one group over sorted particles [b, b + c): box and largest radius scale
+ * straight from the particles */
+static void group_of_range(orc_tree *t, int64_t b, int64_t c)
+{
+    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0, 0, 0};
+    double sm = 0.0;
+    for (int64_t i = b; i < b + c; i++) {
+        for (int d = 0; d < 3; d++) {
+            uint32_t q = t->sq[3 * i + d];
+            if (q < mn[d]) mn[d] = q;
+            if (q > mx[d]) mx[d] = q;
+        }
+        if (t->sscale[i] > sm) sm = t->sscale[i];
+    }
+    group_emit(t, b, c, mn, mx, sm);
+}
+
+/* a run of consecutive small children, [b, b + c): cut into n_group pieces */
+static void group_run(orc_tree *t, int64_t b, int64_t c)
+{
+    for (int64_t o = 0; o < c; o += t->n_group)
+        group_of_range(t, b + o, c - o < t->n_group ? c - o : t->n_group);
+}
+
 static void build_groups(orc_tree *t, int64_t vi)
 {
     const orc_node *v = &t->node[vi];
@@ -444,35 +474,24 @@ static void build_groups(orc_tree *t, int64_t vi)
         group_emit(t, v->begin, v->count, v->qmin, v->qmax, v->smax);
         return;
     }
-    int64_t pb = 0, pc = 0;
-    uint32_t pmin[3], pmax[3];
-    double psmax = 0.0;
+    const int cut = v->count <= 8 * (int64_t)t->n_group;   /* cut runs, else pack children */
+    int64_t rb = 0, rc = 0;                 /* the current run (or pack) of small children */
     for (int k = 0; k < v->nchild; k++) {
         const orc_node *c = &t->node[v->first_child + k];
         if (c->count > t->n_group) {
-            if (pc) group_emit(t, pb, pc, pmin, pmax, psmax);
-            pc = 0;
+            if (rc) { if (cut) group_run(t, rb, rc); else group_of_range(t, rb, rc); }
+            rc = 0;
             build_groups(t, v->first_child + k);
             continue;
         }
-        if (pc && pc + c->count > t->n_group) {
-            group_emit(t, pb, pc, pmin, pmax, psmax);
-            pc = 0;
+        if (!cut && rc && rc + c->count > t->n_group) {
+            group_of_range(t, rb, rc);
+            rc = 0;
         }
-        if (pc == 0) {
-            pb = c->begin;
-            psmax = c->smax;
-            for (int d = 0; d < 3; d++) { pmin[d] = c->qmin[d]; pmax[d] = c->qmax[d]; }
-        } else {
-            if (c->smax > psmax) psmax = c->smax;
-            for (int d = 0; d < 3; d++) {
-                if (c->qmin[d] < pmin[d]) pmin[d] = c->qmin[d];
-                if (c->qmax[d] > pmax[d]) pmax[d] = c->qmax[d];
-            }
-        }
-        pc += c->count;
+        if (rc == 0) rb = c->begin;
+        rc += c->count;
     }
-    if (pc) group_emit(t, pb, pc, pmin, pmax, psmax);
+    if (rc) { if (cut) group_run(t, rb, rc); else group_of_range(t, rb, rc); }
 }
 
 static int cmp_group_begin(const void *a, const void *b)

@@ -601,6 +601,15 @@ __global__ void __launch_bounds__(kT) k_moments_level(int l, const double4 *sp64
 
 // ---------------------------------------------------------------------------
 // Groups: mark the first particle of every group, compact, then describe.
+// A node with at most n_group particles (or a leaf) is a group; a larger
+// node's children are taken in key order, each larger child on its own (its
+// thread marks its children; a leaf that large is a group).  The smaller
+// children of a node with at most 8 n_group particles form runs of
+// consecutive children, each cut into groups of exactly n_group particles
+// (the last one of a run smaller), so most groups fill the force kernel's
+// 64-target pass; those of a larger node are packed whole and greedily into
+// groups of at most n_group (cutting there could join sparse children of a
+// wide node into one group whose box reaches far).
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kT) k_group_mark(const uint4 *nd_a, const uint4 *nd_b,
@@ -616,23 +625,26 @@ __global__ void __launch_bounds__(kT) k_group_mark(const uint4 *nd_a, const uint
         if (r.y <= G || leaf) continue;
         const unsigned fc = nd_b[v].w, nc = meta_nchild(a.w);
         if (fc >= nn || nc > nn - fc) continue;         // truncated build (capacity flag is set)
-        unsigned pb = 0, pc = 0;
+        // cut: the run is marked every G particles; else a pack of whole
+        // children is marked at its start
+        const bool cut = (unsigned long long)r.y <= 8ull * G;
+        unsigned rb = 0, rc = 0;                        // the current run (or pack) of small children
         for (unsigned c = fc; c < fc + nc; c++) {
             uint2 cr = nd_r[c];
             if (cr.y > G) {
-                if (pc) gflag[pb] = 1u;
-                pc = 0;
+                for (unsigned o = 0; o < rc; o += cut ? G : rc) gflag[rb + o] = 1u;
+                rc = 0;
                 if (meta_leaf(nd_a[c].w)) gflag[cr.x] = 1u;
                 continue;
             }
-            if (pc && pc + cr.y > G) {
-                gflag[pb] = 1u;
-                pc = 0;
+            if (!cut && rc && rc + cr.y > G) {
+                gflag[rb] = 1u;
+                rc = 0;
             }
-            if (pc == 0) pb = cr.x;
-            pc += cr.y;
+            if (rc == 0) rb = cr.x;
+            rc += cr.y;
         }
-        if (pc) gflag[pb] = 1u;
+        for (unsigned o = 0; o < rc; o += cut ? G : rc) gflag[rb + o] = 1u;
     }
 }
 

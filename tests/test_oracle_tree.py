@@ -191,6 +191,61 @@ def test_groups_partition():
             assert (b, c) in leaves
 
 
+@pytest.mark.parametrize("n_group,n_leaf", [(64, 16), (24, 8), (7, 4)])
+def test_groups_follow_the_rule(n_group, n_leaf):
+    """The group partition restated in Python from the node list: top-down, a
+    node with at most n_group particles (or a leaf) is a group; a larger node's
+    children in key order, each larger child recursively; the smaller
+    children of a node with at most 8 n_group particles in runs of
+    consecutive children cut into pieces of exactly n_group (the last piece of
+    a run smaller), those of a larger node packed whole and greedily into
+    groups of at most n_group; boxes are the tight boxes of the particles'
+    grid cells."""
+    d = inputs.plummer(6000, 9, masses="kroupa")
+    T = oracle.Tree(d["pos"], d["mass"], n_leaf, n_group)
+    nd = T.nodes()
+    key, q, perm = T.keys()
+    sq = q[perm]
+    want = []
+
+    def visit(v):
+        if nd["count"][v] <= n_group or nd["leaf"][v]:
+            want.append((nd["begin"][v], nd["count"][v]))
+            return
+        cut = nd["count"][v] <= 8 * n_group
+
+        def close(b, c):
+            if cut:
+                for o in range(0, c, n_group):
+                    want.append((b + o, min(n_group, c - o)))
+            elif c:
+                want.append((b, c))
+
+        run_b, run_c = 0, 0
+        for c in range(nd["first_child"][v], nd["first_child"][v] + nd["nchild"][v]):
+            if nd["count"][c] > n_group:
+                close(run_b, run_c)
+                run_c = 0
+                visit(c)
+                continue
+            if not cut and run_c and run_c + nd["count"][c] > n_group:
+                close(run_b, run_c)
+                run_c = 0
+            if run_c == 0:
+                run_b = nd["begin"][c]
+            run_c += nd["count"][c]
+        close(run_b, run_c)
+
+    root = int(np.argmin(nd["level"]))
+    visit(root)
+    g = T.groups()
+    assert sorted(want) == list(zip(g["begin"].tolist(), g["count"].tolist()))
+    for b, c, mn, mx in zip(g["begin"], g["count"], g["qmin"], g["qmax"]):
+        assert np.array_equal(mn, sq[b:b + c].min(0)) and np.array_equal(mx, sq[b:b + c].max(0))
+    if n_group == 64:
+        assert np.mean(g["count"] == 64) > 0.3
+
+
 def _brute_min_dist2(A, B):
     return float(((A[:, None, :] - B[None, :, :]) ** 2).sum(2).min())
 
