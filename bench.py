@@ -77,8 +77,8 @@ def device_sm_count(local: int) -> int:
 
 # DRAM bytes per launch of the mixed force kernel from one ncu capture of the
 # same kernel build on this workload (dram__bytes_read.sum + dram__bytes_write.sum,
-# 1.442 GB + 0.086 GB); None when the kernel changed after the capture.
-FORCE_MIXED_DRAM_BYTES = 1.528e9
+# 1.339 GB + 0.081 GB); None when the kernel changed after the capture.
+FORCE_MIXED_DRAM_BYTES = 1.420e9
 
 
 def rank_env():

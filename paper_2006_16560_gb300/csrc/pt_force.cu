@@ -53,7 +53,11 @@ constexpr int kUnrollPairs = PT_FORCE_UNROLL_PAIRS;   // unroll of the packed ce
 #ifndef PT_FORCE_UNROLL_PP
 #define PT_FORCE_UNROLL_PP 1
 #endif
-constexpr int kUnrollPP = PT_FORCE_UNROLL_PP;   // unroll of the packed PP-pair loop
+constexpr int kUnrollPP = PT_FORCE_UNROLL_PP;   // unroll of the near-segment PP-pair loop
+#ifndef PT_FORCE_UNROLL_FAR
+#define PT_FORCE_UNROLL_FAR 4
+#endif
+constexpr int kUnrollFar = PT_FORCE_UNROLL_FAR;   // unroll of the far-segment PP-pair loop
 constexpr int kIB = 64;       // targets per pass of the float64 kernel (two per lane)
 constexpr int kSlotMax = 96;  // largest pass of the mixed kernel
 #ifndef PT_FORCE_MIN_BLOCKS
@@ -359,13 +363,14 @@ __device__ __forceinline__ void pp_tile_f2(const ForceArgs &A, const ulonglong2 
 
 // Far PP entries (the walk guarantees every pair at least r_out apart, so
 // K = W = 0): plain Newtonian pairs, two list entries per f32x2 operation,
-// with no per-iteration test; unrolled twice (the loop is short enough to
-// keep two iterations in flight).
+// with no per-iteration test; unrolled four times (the loop is short enough
+// to keep four iterations in flight: 12.20 -> 11.86 ms for the kernel at
+// N = 2^20; two, eight: slower).
 template <int NI, int J>
 __device__ __forceinline__ void pp_tile_far(const ulonglong2 (*sQ)[kJ / 2], int s, int npairs,
                                             const f2x (&OX)[NI], const f2x (&OY)[NI],
                                             const f2x (&OZ)[NI], f2x (&PA)[NI][4]) {
-#pragma unroll 2
+#pragma unroll kUnrollFar
     for (int P = s; P < npairs; P += J) {
         const ulonglong2 q0 = sQ[0][P], q1 = sQ[1][P];
 #pragma unroll
@@ -386,10 +391,21 @@ __device__ __forceinline__ void pp_tile_far(const ulonglong2 (*sQ)[kJ / 2], int 
 // Per-lane float-float accumulators live in shared memory (touched once per
 // tile), which keeps their 8 NI registers free for the inner loops.
 
+// Float-float sum of two float-float values (Knuth TwoSum of the high parts,
+// low parts added): about 2^-44 relative, all on the FP32 pipe.
+__device__ __forceinline__ float2 ff_sum(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bp = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bp)), __fsub_rn(b.x, bp));
+    const float lo = __fadd_rn(__fadd_rn(a.y, b.y), e);
+    const float hi = __fadd_rn(s, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+
 template <int NI, int J, int ORDER, bool NB, bool MD>
 __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                              const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
-                             unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
+                             unsigned (*sI)[kJ], float2 (*sF)[3][4][32], float2 (*red)[kSlotMax][4]) {
     constexpr int L = 32 / J;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = lane / L, l = lane % L;
@@ -575,21 +591,56 @@ __device__ void group_pass_f(const ForceArgs &A, unsigned g, const uint2 gr, uns
             atomicAdd(&A.st->pp_fast, (unsigned long long)n_fast);
         }
     }
-    // ---- sum the J sub-streams of each target, then hand over to the block
+    // ---- sum the J sub-streams of each target (float-float, fixed order),
+    // then hand over to the block
 #pragma unroll
     for (int k = 0; k < NI; k++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            const float2 a = acc[k][c][lane];
-            double v = (double)a.x + (double)a.y;
+            float2 v = acc[k][c][lane];
 #pragma unroll
-            for (int o = L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o = L; o < 32; o <<= 1) {
+                const float2 u = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
+                                             __shfl_xor_sync(0xffffffffu, v.y, o));
+                v = (lane & o) ? ff_sum(u, v) : ff_sum(v, u);   // the same order on both lanes
+            }
             if (s == 0) red[w][l + L * k][c] = v;
         }
 }
 
-// Final per-target sums (threads 0..slots-1): fixed-order float64 reduction
-// over the warps, removal of the self entry, output in caller order.
+// Final per-target sums of the mixed kernel (threads 0..slots-1): the warps'
+// float-float partials added in a fixed order, converted to float64 once;
+// removal of the self entry, output in caller order.
+__device__ __forceinline__ void write_targets_ff(const ForceArgs &A, const uint2 gr, unsigned i0,
+                                                 unsigned slots, double c2, float2 (*red)[kSlotMax][4],
+                                                 double (&ep)[4]) {
+    const unsigned t = threadIdx.x;
+    if (t < slots && i0 + t < gr.y) {
+        double s[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            float2 v = red[0][t][c];
+            for (int w = 1; w < kFWarps; w++) v = ff_sum(v, red[w][t][c]);
+            s[c] = (double)v.x + (double)v.y;
+        }
+        const unsigned p = gr.x + i0 + t;
+        const double m = A.sp64[p].w;
+        const double P = s[3] - (A.massdep ? m * c2 / A.ssc[p] : m * c2);
+        const unsigned i = A.perm[p];
+        const double ax = A.G * s[0], ay = A.G * s[1], az = A.G * s[2], phi = -A.G * P;
+        A.acc[3ull * i] = ax;
+        A.acc[3ull * i + 1] = ay;
+        A.acc[3ull * i + 2] = az;
+        A.pot[i] = phi;
+        ep[0] += 0.5 * m * phi;
+        ep[1] += m * ax;
+        ep[2] += m * ay;
+        ep[3] += m * az;
+    }
+}
+
+// Final per-target sums of the float64 kernel (threads 0..slots-1): fixed-order
+// float64 reduction over the warps, removal of the self entry, output in caller order.
 __device__ __forceinline__ void write_targets(const ForceArgs &A, const uint2 gr, unsigned i0,
                                               unsigned slots, double c2, double (*red)[kSlotMax][4],
                                               double (&ep)[4]) {
@@ -644,7 +695,7 @@ constexpr int kPassClasses = 6;
 template <int ORDER, bool NB, bool MD>
 __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, unsigned i0,
                                const ChgF &C, double rout2, double rout, ulonglong2 (*sP)[5][kJ / 2],
-                               unsigned (*sI)[kJ], float2 (*sF)[3][4][32], double (*red)[kSlotMax][4]) {
+                               unsigned (*sI)[kJ], float2 (*sF)[3][4][32], float2 (*red)[kSlotMax][4]) {
     const unsigned rem = gr.y - i0;
     if (rem <= 16) { group_pass_f<2, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 16; }
     if (rem <= 24) { group_pass_f<3, 4, ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red); return 24; }
@@ -660,9 +711,13 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
     __shared__ ulonglong2 sP[kFWarps][5][kJ / 2];
     __shared__ float2 sF[kFWarps][3][4][32];
     __shared__ unsigned sI[kFWarps][kJ];
-    __shared__ double red[kFWarps][kSlotMax][4];
+    __shared__ float2 red[kFWarps][kSlotMax][4];
     __shared__ double ered[kFWarps][4];
     __shared__ unsigned gsh;
+    // the group's changeover constants, formed once per group by thread 0
+    // (float64 divisions and a square root: slow on this part's FP64 pipe)
+    __shared__ ChgF sC;
+    __shared__ double sRout2, sRout, sC2;
     // lists left unusable by the walk (one-pass arrays exhausted, stack
     // overflow): do nothing, the host re-runs the walk and the force
     if (A.st->flags & (kErrListCap | kErrStack)) return;
@@ -681,24 +736,32 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
         }
         const unsigned g = A.gr_ord[gi];
         const uint2 gr = A.gr_r[g];
-        const Chg C64 = make_chg(A.sets[A.gr_a[g].w]);
-        ChgF C;
-        C.invw = (float)C64.invw;
-        C.c0 = (float)C64.c0;
-        C.c2 = (float)C64.c2;
-        C.k0 = (float)(70.0 * C64.ri / (C64.ro + C64.ri));   // 35 (1 - Lambda), no cancellation
-        C.w0 = (float)(14.0 * C64.lam);
-        C.w1 = (float)(-28.0 * C64.lam);
-        C.w2 = (float)(20.0 * C64.lam);
-        C.w3 = (float)(-5.0 * C64.lam);
-        C.tiny = fmaxf((float)C64.tiny, 1e-36f);
-        C.rout2m = vote_rout2(A.gr_a[g], A.gr_b[g], A.sets[A.gr_a[g].w]);
+        if (threadIdx.x == 0) {
+            const Chg C64 = make_chg(A.sets[A.gr_a[g].w]);
+            ChgF C;
+            C.invw = (float)C64.invw;
+            C.c0 = (float)C64.c0;
+            C.c2 = (float)C64.c2;
+            C.k0 = (float)(70.0 * C64.ri / (C64.ro + C64.ri));   // 35 (1 - Lambda), no cancellation
+            C.w0 = (float)(14.0 * C64.lam);
+            C.w1 = (float)(-28.0 * C64.lam);
+            C.w2 = (float)(20.0 * C64.lam);
+            C.w3 = (float)(-5.0 * C64.lam);
+            C.tiny = fmaxf((float)C64.tiny, 1e-36f);
+            C.rout2m = vote_rout2(A.gr_a[g], A.gr_b[g], A.sets[A.gr_a[g].w]);
+            sC = C;
+            sRout2 = C64.rout2;
+            sRout = C64.ro;
+            sC2 = C64.c2;
+        }
+        __syncthreads();
+        const ChgF C = sC;
+        const double rout2 = sRout2, rout = sRout, c2 = sC2;
         double ep[4] = {0, 0, 0, 0};
         for (unsigned i0 = 0; i0 < gr.y;) {
-            const unsigned slots =
-                mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, C64.rout2, C64.ro, sP, sI, sF, red);
+            const unsigned slots = mixed_pass<ORDER, NB, MD>(A, g, gr, i0, C, rout2, rout, sP, sI, sF, red);
             __syncthreads();
-            write_targets(A, gr, i0, slots, C64.c2, red, ep);
+            write_targets_ff(A, gr, i0, slots, c2, red, ep);
             __syncthreads();
             i0 += slots;
         }
