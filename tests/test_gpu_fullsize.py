@@ -101,3 +101,41 @@ def test_kroupa95_binaries_200k(ctx):
     rows = np.repeat(np.arange(n), np.diff(g["nb_off"]))
     have = set((rows.astype(np.int64) * n + g["nb_idx"]).tolist())
     assert all((2 * k) * n + 2 * k + 1 in have for k in close[::13])
+
+
+def test_kroupa_plummer_36m_lists_past_2_32(ctx):
+    """N = 3.6*10^7: the cell list holds more than 2^32 entries (the near and
+    far PP lists more than 2^31), so every list offset of the walk, the force
+    kernel and the CSR must be 64-bit.  The mixed path only (the FP64 path
+    would add half a minute): key order, node and group counts, sampled forces
+    against the oracle tree, exact neighbour rows of the sampled targets and a
+    symmetric CSR."""
+    d = inputs.plummer(36_000_000, 2, masses="kroupa")
+    n = len(d["mass"])
+    p = c2_params(B.PT_MIXED)
+    g = run_gpu(ctx, d["pos"], d["mass"], p)
+    st = g["stats"]
+    assert st["cell_list_total"] > 2**32 and st["pp_list_total"] > 2**31
+    T = oracle.Tree(d["pos"], d["mass"], p.n_leaf, p.n_group)
+    key, _, perm = T.keys()
+    gk, gperm = g["tree"].keys()
+    assert np.array_equal(gperm.astype(np.int64), perm) and np.array_equal(gk, key[perm])
+    info, _ = g["tree"].info()
+    assert info[1] == T.nnodes and info[2] == T.ngroups
+    del key, perm, gk, gperm
+    rng = np.random.default_rng(10)
+    tg = np.unique(np.concatenate([rng.choice(n, 60, replace=False), [0, n - 1]]))
+    a, phi, _ = T.force(p.theta, p.r_in, p.r_out, order=p.order, targets=tg)
+    e = rel_err(g["acc"][tg], a)
+    ep = np.abs(g["pot"][tg] - phi) / np.abs(phi)
+    assert np.percentile(e, 99) <= 1e-6 and np.percentile(ep, 99) <= 1e-6
+    off, idx = oracle.neighbours(d["pos"], p.r_out, tg)
+    nb_off, nb_idx = g["nb_off"], g["nb_idx"]
+    for t, i in enumerate(tg):
+        assert np.array_equal(nb_idx[nb_off[i]:nb_off[i + 1]], idx[off[t]:off[t + 1]])
+    assert nb_off[0] == 0 and nb_off[-1] == len(nb_idx) and np.all(np.diff(nb_off) >= 0)
+    rows = np.repeat(np.arange(n), np.diff(nb_off))
+    assert np.all(nb_idx != rows)
+    fwd = rows.astype(np.int64) * n + nb_idx
+    bwd = nb_idx.astype(np.int64) * n + rows
+    assert np.array_equal(np.sort(fwd), np.sort(bwd))
