@@ -162,7 +162,8 @@ int pt_tree_build(pt_ctx *ctx, int64_t n, const double *pos, const double *mass,
  * particle i has radii s_i (r_in, r_out) and a pair uses the larger pair
  * (Eq. 16), so the changeover, the walk's r_out gap and the neighbour lists all
  * use s_ij = max(s_i, s_j).  params->mass_dependent must be 1.  radius_scale
- * (n doubles, host or device, each >= 1 in the paper's use) gives s_i; if it
+ * (n doubles, host or device, each >= 1 in the paper's use; a factor that is
+ * not finite and positive returns PT_ERR_ARG) gives s_i; if it
  * is NULL the library computes Eq. 12, s_i = max(1, m_i / <m>)^(1/3) with <m>
  * the mean mass, on the device (CUDA cbrt: within 1 ulp of a host cbrt, so
  * pass the factors explicitly when neighbour lists must match a host
@@ -197,7 +198,8 @@ typedef struct {
     int32_t *nb_idx;         /* out: nb_capacity entries (cluster-local ids)  */
     int64_t nb_capacity;
     int64_t nb_total;        /* out: entries needed                           */
-    const double *radius_scale;  /* n radius factors (mass_dependent) or NULL */
+    const double *radius_scale;  /* n radius factors (mass_dependent) or NULL;
+                                    each finite and > 0, else PT_ERR_ARG     */
 } pt_cluster_desc;
 
 /* Evaluates n_clusters independent sets in one pass of the pipeline: every

@@ -461,6 +461,7 @@ int run_build(pt_tree *t, const double *pos, const double *mass) {
         const unsigned f = t->h.flags;
         if (f & kErrNonFinite) return fail(ctx, PT_ERR_ARG, "non-finite position or mass in the input");
         if (f & kErrNegMass) return fail(ctx, PT_ERR_ARG, "negative mass in the input");
+        if (f & kErrBadScale) return fail(ctx, PT_ERR_ARG, "radius factor not finite and positive");
         if (f & kErrNodeCap) {
             unsigned long long c = 2ull * t->cap_nodes;
             if (c > 0x7fffffffull) return fail(ctx, PT_ERR_INTERNAL, "tree node count exceeds 2^31");
@@ -987,7 +988,8 @@ int batch_impl(pt_ctx *ctx, int C, pt_cluster_desc *d, const pt_params *params, 
         t->h = *ctx->h_status;
         const unsigned f = t->h.flags;
         const bool pair_short = want_nb && t->h.npairs > t->cap_pairs && t->h.npairs <= nb_hint;
-        if (f & (kErrNonFinite | kErrNegMass)) return fail(ctx, PT_ERR_ARG, "non-finite position or negative mass");
+        if (f & (kErrNonFinite | kErrNegMass | kErrBadScale))
+            return fail(ctx, PT_ERR_ARG, "non-finite position, negative mass or radius factor not finite and positive");
         if (!(f & (kErrNodeCap | kErrStack | kErrListCap)) && !pair_short) {
             done = true;
             cudaEventElapsedTime(&ms[2], ctx->ev[6], ctx->ev[7]);

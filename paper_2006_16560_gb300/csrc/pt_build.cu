@@ -192,10 +192,12 @@ __global__ void __launch_bounds__(kT) k_keys(const double *pos, unsigned n, cons
 __global__ void __launch_bounds__(kT) k_gather(const double *pos, const double *mass, unsigned n,
                                                const unsigned *perm, const uint4 *qbuf,
                                                const double *scale, double *ssc,
-                                               double4 *sp64, float4 *spH, float4 *spL, uint4 *sq) {
+                                               double4 *sp64, float4 *spH, float4 *spL, uint4 *sq,
+                                               Status *st) {
     for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         unsigned i = perm[p];
         const double sc = scale ? scale[i] : 1.0;
+        if (!(sc > 0.0 && isfinite(sc))) atomicOr(&st->flags, kErrBadScale);   // rare: no aggregation
         const float inv_sc = scale ? __double2float_rn(1.0 / sc) : 1.0f;
         ssc[p] = sc;
         double x = pos[3ull * i], y = pos[3ull * i + 1], z = pos[3ull * i + 2], m = mass[i];
@@ -472,6 +474,12 @@ __global__ void k_topo_finish(Status *st, unsigned cap) {
 // stored quadrupole is Q = 3T - tr(T) I (twice the traceless A' of Eq. 31).
 // ---------------------------------------------------------------------------
 
+// max of two non-negative doubles on the integer pipe (their bit patterns
+// order like their values); GB300's float64 pipe is the build's slow unit
+__device__ __forceinline__ double dmax_pos(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+
 // Moments of node v: leaves sum their particles about the first particle,
 // internal nodes combine their children (complete: a deeper level or a leaf,
 // from an earlier launch) with the parallel-axis shift.
@@ -484,10 +492,15 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
     double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3], smax = 0.0;
     unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
     if (meta_leaf(a.w)) {
-        double4 p0 = sp64[r.x];
+        // sums about the first particle, whose own offset is zero
+        const double4 p0 = sp64[r.x];
+        const uint4 q0 = sq[r.x];
         double x0[3] = {p0.x, p0.y, p0.z};
         double s2[6] = {0, 0, 0, 0, 0, 0};
-        for (unsigned p = r.x; p < r.x + r.y; p++) {
+        M = p0.w;
+        smax = ssc[r.x];
+        qmn[0] = qmx[0] = q0.x; qmn[1] = qmx[1] = q0.y; qmn[2] = qmx[2] = q0.z;
+        for (unsigned p = r.x + 1; p < r.x + r.y; p++) {
             double4 P = sp64[p];
             uint4 q = sq[p];
             double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
@@ -499,17 +512,19 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
             s2[3] = fma(md0, d1, s2[3]); s2[4] = fma(md0, d2, s2[4]); s2[5] = fma(md1, d2, s2[5]);
             qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
             qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
-            smax = fmax(smax, ssc[p]);
+            smax = dmax_pos(smax, ssc[p]);
         }
         if (M > 0.0) {
-            double dc[3] = {s1[0] / M, s1[1] / M, s1[2] / M};
+            // one reciprocal for the three offsets; T = S2 - s1 dc^T (s1 = M dc)
+            const double iM = 1.0 / M;
+            const double dc[3] = {s1[0] * iM, s1[1] * iM, s1[2] * iM};
             for (int d = 0; d < 3; d++) com[d] = x0[d] + dc[d];
-            T[0] = s2[0] - M * dc[0] * dc[0];
-            T[1] = s2[1] - M * dc[1] * dc[1];
-            T[2] = s2[2] - M * dc[2] * dc[2];
-            T[3] = s2[3] - M * dc[0] * dc[1];
-            T[4] = s2[4] - M * dc[0] * dc[2];
-            T[5] = s2[5] - M * dc[1] * dc[2];
+            T[0] = fma(-s1[0], dc[0], s2[0]);
+            T[1] = fma(-s1[1], dc[1], s2[1]);
+            T[2] = fma(-s1[2], dc[2], s2[2]);
+            T[3] = fma(-s1[0], dc[1], s2[3]);
+            T[4] = fma(-s1[0], dc[2], s2[4]);
+            T[5] = fma(-s1[1], dc[2], s2[5]);
         } else {
             for (int d = 0; d < 3; d++) com[d] = x0[d];
         }
@@ -525,22 +540,24 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
             s1[1] += C.w * (C.y - x0[1]);
             s1[2] += C.w * (C.z - x0[2]);
             uint4 ca = nd_a[c], cb = nd_b[c];
-            smax = fmax(smax, nd_t[2 * c + 1].z);
+            smax = dmax_pos(smax, nd_t[2 * c + 1].z);
             qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
             qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
         }
         if (M > 0.0) {
-            for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] / M;
+            const double iM = 1.0 / M;
+            for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] * iM;
             for (unsigned c = fc; c < fc + nc; c++) {
                 double4 C = nd_c[c];
                 double4 t0 = nd_t[2 * c], t1 = nd_t[2 * c + 1];
                 double e0 = C.x - com[0], e1 = C.y - com[1], e2 = C.z - com[2], m = C.w;
-                T[0] += t0.x + m * e0 * e0;
-                T[1] += t0.y + m * e1 * e1;
-                T[2] += t0.z + m * e2 * e2;
-                T[3] += t0.w + m * e0 * e1;
-                T[4] += t1.x + m * e0 * e2;
-                T[5] += t1.y + m * e1 * e2;
+                const double me0 = m * e0, me1 = m * e1, me2 = m * e2;
+                T[0] += fma(me0, e0, t0.x);
+                T[1] += fma(me1, e1, t0.y);
+                T[2] += fma(me2, e2, t0.z);
+                T[3] += fma(me0, e1, t0.w);
+                T[4] += fma(me0, e2, t1.x);
+                T[5] += fma(me1, e2, t1.y);
             }
         } else {
             for (int d = 0; d < 3; d++) com[d] = x0[d];
@@ -728,7 +745,7 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     nk += radix_sort(A.keys_in, A.vals_in, A.skey, A.perm, A.n_dev, n, 0, 3 * kBits, set_of,
                      set_bits, A.sort_tmp, st);
     k_gather<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.pos, A.mass, n, A.perm, A.qbuf, scale, A.ssc,
-                                                   A.sp64, A.spH, A.spL, A.sq);
+                                                   A.sp64, A.spH, A.spL, A.sq, S);
     // topology
     k_lcp<<<grid_for(n, kT, gmax), kT, 0, st>>>(A.skey, A.n_dev, A.lcp);
     nk++;

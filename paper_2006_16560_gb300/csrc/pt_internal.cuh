@@ -38,6 +38,7 @@ enum : unsigned {
     kErrNonFinite = 1u << 4,  // NaN / Inf position or mass
     kErrNegMass = 1u << 5,    // negative mass
     kErrGroupCap = 1u << 6,   // group arrays too small
+    kErrBadScale = 1u << 7,   // radius factor not finite and positive
 };
 
 // Per-set (cluster) table entry.

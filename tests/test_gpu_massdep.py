@@ -108,3 +108,20 @@ def test_scaled_batch_equals_single(ctx):
     for k, g in enumerate(singles):
         assert np.array_equal(bt.acc[k].cpu().numpy(), g["acc"])
         assert np.array_equal(bt.pot[k].cpu().numpy(), g["pot"])
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.5, float("nan"), float("inf")])
+def test_bad_radius_factor_is_an_argument_error(ctx, bad):
+    """A radius factor that is not finite and positive is rejected by the build
+    (PT_ERR_ARG), and the context stays usable."""
+    import torch
+    d = inputs.plummer(2000, 61, masses="kroupa")
+    sc = oracle.radius_scale(d["mass"])
+    sc[1234] = bad
+    pos, mass = torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["mass"]).cuda()
+    with pytest.raises(B.PTError) as e:
+        B.Tree(ctx, pos, mass, _params(), scale=torch.from_numpy(sc).cuda())
+    assert e.value.code == B.PT_ERR_ARG and "radius factor" in str(e.value)
+    sc[1234] = 1.0
+    g = _run(ctx, d, _params(), sc)
+    assert np.all(np.isfinite(g["acc"]))
