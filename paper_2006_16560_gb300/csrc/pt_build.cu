@@ -272,6 +272,7 @@ __global__ void k_topo_roots(const SetInfo *sets, int nsets, uint4 *nd_a, uint4 
             st->lvl_begin[l] = 0;
             st->lvl_count[l] = 0;
         }
+        for (int l = 0; l <= kLevels; l++) st->lvl_int[l] = 0;
     }
 }
 
@@ -414,10 +415,14 @@ __global__ void __launch_bounds__(kT) k_topo_count_big(int l, const unsigned lon
     }
 }
 
+// Creates the children of level l's split nodes (at next + choff) and lists
+// the split nodes themselves, in any order, in nd_int from lvl_begin[l] on:
+// the multipole pass then takes one internal node per thread with no leaves
+// in between (float64 instructions cost the same for a warp with few lanes).
 __global__ void __launch_bounds__(kT) k_topo_emit(int l, const uint4 *bnd,
                                                   uint4 *nd_a, uint4 *nd_b, uint2 *nd_r,
                                                   const unsigned *nch, const unsigned *choff,
-                                                  unsigned cap, Status *st) {
+                                                  unsigned *nd_int, unsigned cap, Status *st) {
     unsigned b0, cnt;
     level_range(st, l, cap, b0, cnt);
     const unsigned next = st->lvl_begin[l] + st->lvl_count[l];
@@ -431,9 +436,21 @@ __global__ void __launch_bounds__(kT) k_topo_emit(int l, const uint4 *bnd,
             st->lvl_count[l + 1] = next < cap ? cap - next : 0u;
         }
     }
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        if (nch[k] == 0) continue;
+    // grid-stride rounds over whole warps, so that the list slots are taken
+    // with one atomic per warp
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned k0 = blockIdx.x * blockDim.x; k0 < cnt; k0 += gridDim.x * blockDim.x) {
+        const unsigned k = k0 + threadIdx.x;
+        const bool split = k < cnt && nch[k] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, split);
+        unsigned slot = 0;
+        if (m) {
+            if (lane == 0) slot = atomicAdd(&st->lvl_int[l], (unsigned)__popc(m));
+            slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
+        }
+        if (!split) continue;
         unsigned v = b0 + k;
+        if (b0 + slot < cap) nd_int[b0 + slot] = v;
         uint2 r = nd_r[v];
         const uint4 b1 = bnd[2 * v], b2 = bnd[2 * v + 1];
         const unsigned B[9] = {b1.x, b1.y, b1.z, b1.w, b2.x, b2.y, b2.z, b2.w, r.x + r.y};
@@ -480,89 +497,15 @@ __device__ __forceinline__ double dmax_pos(double a, double b) {
     return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
 }
 
-// Moments of node v: leaves sum their particles about the first particle,
-// internal nodes combine their children (complete: a deeper level or a leaf,
-// from an earlier launch) with the parallel-axis shift.
-__device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, const uint4 *sq, uint4 *nd_a,
-                                             uint4 *nd_b, const uint2 *nd_r, double4 *nd_c, double4 *nd_q,
-                                             double4 *nd_t, float4 *nd_f, const double *ssc,
-                                             const SetInfo *sets, long long *nd_thr, unsigned cap) {
-    uint4 a = nd_a[v], bb = nd_b[v];
-    uint2 r = nd_r[v];
-    double M = 0, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3], smax = 0.0;
-    unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
-    if (meta_leaf(a.w)) {
-        // sums about the first particle, whose own offset is zero
-        const double4 p0 = sp64[r.x];
-        const uint4 q0 = sq[r.x];
-        double x0[3] = {p0.x, p0.y, p0.z};
-        double s2[6] = {0, 0, 0, 0, 0, 0};
-        M = p0.w;
-        smax = ssc[r.x];
-        qmn[0] = qmx[0] = q0.x; qmn[1] = qmx[1] = q0.y; qmn[2] = qmx[2] = q0.z;
-        for (unsigned p = r.x + 1; p < r.x + r.y; p++) {
-            double4 P = sp64[p];
-            uint4 q = sq[p];
-            double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
-            // float64 is GB300's slow pipe: m d formed once, reused by both sums
-            const double md0 = m * d0, md1 = m * d1, md2 = m * d2;
-            M += m;
-            s1[0] += md0; s1[1] += md1; s1[2] += md2;
-            s2[0] = fma(md0, d0, s2[0]); s2[1] = fma(md1, d1, s2[1]); s2[2] = fma(md2, d2, s2[2]);
-            s2[3] = fma(md0, d1, s2[3]); s2[4] = fma(md0, d2, s2[4]); s2[5] = fma(md1, d2, s2[5]);
-            qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
-            qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
-            smax = dmax_pos(smax, ssc[p]);
-        }
-        if (M > 0.0) {
-            // one reciprocal for the three offsets; T = S2 - s1 dc^T (s1 = M dc)
-            const double iM = 1.0 / M;
-            const double dc[3] = {s1[0] * iM, s1[1] * iM, s1[2] * iM};
-            for (int d = 0; d < 3; d++) com[d] = x0[d] + dc[d];
-            T[0] = fma(-s1[0], dc[0], s2[0]);
-            T[1] = fma(-s1[1], dc[1], s2[1]);
-            T[2] = fma(-s1[2], dc[2], s2[2]);
-            T[3] = fma(-s1[0], dc[1], s2[3]);
-            T[4] = fma(-s1[0], dc[2], s2[4]);
-            T[5] = fma(-s1[1], dc[2], s2[5]);
-        } else {
-            for (int d = 0; d < 3; d++) com[d] = x0[d];
-        }
-    } else {
-        const unsigned fc = bb.w, nc = meta_nchild(a.w);
-        if (fc >= cap || nc > cap - fc) return;     // truncated build (capacity flag is set)
-        double4 c0 = nd_c[fc];
-        double x0[3] = {c0.x, c0.y, c0.z};
-        for (unsigned c = fc; c < fc + nc; c++) {
-            double4 C = nd_c[c];
-            M += C.w;
-            s1[0] += C.w * (C.x - x0[0]);
-            s1[1] += C.w * (C.y - x0[1]);
-            s1[2] += C.w * (C.z - x0[2]);
-            uint4 ca = nd_a[c], cb = nd_b[c];
-            smax = dmax_pos(smax, nd_t[2 * c + 1].z);
-            qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
-            qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
-        }
-        if (M > 0.0) {
-            const double iM = 1.0 / M;
-            for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] * iM;
-            for (unsigned c = fc; c < fc + nc; c++) {
-                double4 C = nd_c[c];
-                double4 t0 = nd_t[2 * c], t1 = nd_t[2 * c + 1];
-                double e0 = C.x - com[0], e1 = C.y - com[1], e2 = C.z - com[2], m = C.w;
-                const double me0 = m * e0, me1 = m * e1, me2 = m * e2;
-                T[0] += fma(me0, e0, t0.x);
-                T[1] += fma(me1, e1, t0.y);
-                T[2] += fma(me2, e2, t0.z);
-                T[3] += fma(me0, e1, t0.w);
-                T[4] += fma(me0, e2, t1.x);
-                T[5] += fma(me1, e2, t1.y);
-            }
-        } else {
-            for (int d = 0; d < 3; d++) com[d] = x0[d];
-        }
-    }
+// Writes node v's multipole records: COM and mass, Q = 3T - tr(T) I, T with
+// the largest radius factor, the grid box, the walk's gap threshold (f1) and
+// the float record of the mixed kernel.
+__device__ __forceinline__ void store_moments(unsigned v, uint4 a, uint4 bb, unsigned p0, double M,
+                                              const double com[3], const double T[6], double smax,
+                                              const unsigned qmn[3], const unsigned qmx[3],
+                                              const uint4 *sq, uint4 *nd_a, uint4 *nd_b, double4 *nd_c,
+                                              double4 *nd_q, double4 *nd_t, float4 *nd_f,
+                                              const SetInfo *sets, long long *nd_thr) {
     double tr = T[0] + T[1] + T[2];
     double Q[6] = {3 * T[0] - tr, 3 * T[1] - tr, 3 * T[2] - tr, 3 * T[3], 3 * T[4], 3 * T[5]};
     nd_c[v] = make_double4(com[0], com[1], com[2], M);
@@ -570,7 +513,7 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
     nd_q[2 * v + 1] = make_double4(Q[4], Q[5], 0.0, 0.0);
     nd_t[2 * v] = make_double4(T[0], T[1], T[2], T[3]);
     nd_t[2 * v + 1] = make_double4(T[4], T[5], smax, 0.0);
-    if (nd_thr) nd_thr[v] = gap_threshold(sets[sq[r.x].w], smax);
+    if (nd_thr) nd_thr[v] = gap_threshold(sets[sq[p0].w], smax);
     a.x = qmn[0]; a.y = qmn[1]; a.z = qmn[2];
     bb.x = qmx[0]; bb.y = qmx[1]; bb.z = qmx[2];
     nd_a[v] = a;
@@ -586,6 +529,108 @@ __device__ __forceinline__ void node_moments(unsigned v, const double4 *sp64, co
                                   __double2float_rn(-Q[4]), __double2float_rn(-Q[5]));
 }
 
+// Moments of leaf v: its particles summed about the first particle (whose own
+// offset is zero).
+__device__ __forceinline__ void leaf_moments(unsigned v, const double4 *sp64, const uint4 *sq, uint4 *nd_a,
+                                             uint4 *nd_b, const uint2 *nd_r, double4 *nd_c, double4 *nd_q,
+                                             double4 *nd_t, float4 *nd_f, const double *ssc,
+                                             const SetInfo *sets, long long *nd_thr) {
+    const uint4 a = nd_a[v], bb = nd_b[v];
+    const uint2 r = nd_r[v];
+    double s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3];
+    const double4 p0 = sp64[r.x];
+    const uint4 q0 = sq[r.x];
+    const double x0[3] = {p0.x, p0.y, p0.z};
+    double M = p0.w, smax = ssc[r.x];
+    unsigned qmn[3] = {q0.x, q0.y, q0.z}, qmx[3] = {q0.x, q0.y, q0.z};
+    for (unsigned p = r.x + 1; p < r.x + r.y; p++) {
+        const double4 P = sp64[p];
+        const uint4 q = sq[p];
+        const double d0 = P.x - x0[0], d1 = P.y - x0[1], d2 = P.z - x0[2], m = P.w;
+        // float64 is GB300's slow pipe: m d formed once, reused by both sums
+        const double md0 = m * d0, md1 = m * d1, md2 = m * d2;
+        M += m;
+        s1[0] += md0; s1[1] += md1; s1[2] += md2;
+        s2[0] = fma(md0, d0, s2[0]); s2[1] = fma(md1, d1, s2[1]); s2[2] = fma(md2, d2, s2[2]);
+        s2[3] = fma(md0, d1, s2[3]); s2[4] = fma(md0, d2, s2[4]); s2[5] = fma(md1, d2, s2[5]);
+        qmn[0] = min(qmn[0], q.x); qmn[1] = min(qmn[1], q.y); qmn[2] = min(qmn[2], q.z);
+        qmx[0] = max(qmx[0], q.x); qmx[1] = max(qmx[1], q.y); qmx[2] = max(qmx[2], q.z);
+        smax = dmax_pos(smax, ssc[p]);
+    }
+    if (M > 0.0) {
+        // one reciprocal for the three offsets; T = S2 - s1 dc^T (s1 = M dc)
+        const double iM = 1.0 / M;
+        const double dc[3] = {s1[0] * iM, s1[1] * iM, s1[2] * iM};
+        for (int d = 0; d < 3; d++) com[d] = x0[d] + dc[d];
+        T[0] = fma(-s1[0], dc[0], s2[0]);
+        T[1] = fma(-s1[1], dc[1], s2[1]);
+        T[2] = fma(-s1[2], dc[2], s2[2]);
+        T[3] = fma(-s1[0], dc[1], s2[3]);
+        T[4] = fma(-s1[0], dc[2], s2[4]);
+        T[5] = fma(-s1[1], dc[2], s2[5]);
+    } else {
+        for (int d = 0; d < 3; d++) com[d] = x0[d];
+    }
+    store_moments(v, a, bb, r.x, M, com, T, smax, qmn, qmx, sq, nd_a, nd_b, nd_c, nd_q, nd_t, nd_f, sets,
+                  nd_thr);
+}
+
+// Moments of internal node v from its (complete) children: mass and COM about
+// the first child's COM, then T = sum of the children's T shifted to the COM
+// (parallel axes).  The child loops are unrolled over the at most eight
+// children, so their loads are issued together.
+__device__ __forceinline__ void internal_moments(unsigned v, const uint4 *sq, uint4 *nd_a, uint4 *nd_b,
+                                                 const uint2 *nd_r, double4 *nd_c, double4 *nd_q,
+                                                 double4 *nd_t, float4 *nd_f, const SetInfo *sets,
+                                                 long long *nd_thr, unsigned cap) {
+    const uint4 a = nd_a[v], bb = nd_b[v];
+    const unsigned fc = bb.w, nc = meta_nchild(a.w);
+    if (nc < 1 || nc > 8 || fc >= cap || nc > cap - fc) return;   // truncated build (flag is set)
+    double4 C[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) C[j] = j < (int)nc ? nd_c[fc + j] : make_double4(0.0, 0.0, 0.0, 0.0);
+    const double x0[3] = {C[0].x, C[0].y, C[0].z};
+    double M = C[0].w, s1[3] = {0, 0, 0}, T[6] = {0, 0, 0, 0, 0, 0}, com[3], smax = 0.0;
+    unsigned qmn[3] = {kGrid, kGrid, kGrid}, qmx[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        if (j >= (int)nc) break;
+        const unsigned c = fc + j;
+        if (j > 0) {
+            M += C[j].w;
+            s1[0] += C[j].w * (C[j].x - x0[0]);
+            s1[1] += C[j].w * (C[j].y - x0[1]);
+            s1[2] += C[j].w * (C[j].z - x0[2]);
+        }
+        const uint4 ca = nd_a[c], cb = nd_b[c];
+        smax = dmax_pos(smax, nd_t[2 * c + 1].z);
+        qmn[0] = min(qmn[0], ca.x); qmn[1] = min(qmn[1], ca.y); qmn[2] = min(qmn[2], ca.z);
+        qmx[0] = max(qmx[0], cb.x); qmx[1] = max(qmx[1], cb.y); qmx[2] = max(qmx[2], cb.z);
+    }
+    if (M > 0.0) {
+        const double iM = 1.0 / M;
+        for (int d = 0; d < 3; d++) com[d] = x0[d] + s1[d] * iM;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (j >= (int)nc) break;
+            const unsigned c = fc + j;
+            const double4 t0 = nd_t[2 * c], t1 = nd_t[2 * c + 1];
+            const double e0 = C[j].x - com[0], e1 = C[j].y - com[1], e2 = C[j].z - com[2], m = C[j].w;
+            const double me0 = m * e0, me1 = m * e1, me2 = m * e2;
+            T[0] += fma(me0, e0, t0.x);
+            T[1] += fma(me1, e1, t0.y);
+            T[2] += fma(me2, e2, t0.z);
+            T[3] += fma(me0, e1, t0.w);
+            T[4] += fma(me0, e2, t1.x);
+            T[5] += fma(me1, e2, t1.y);
+        }
+    } else {
+        for (int d = 0; d < 3; d++) com[d] = x0[d];
+    }
+    store_moments(v, a, bb, nd_r[v].x, M, com, T, smax, qmn, qmx, sq, nd_a, nd_b, nd_c, nd_q, nd_t, nd_f,
+                  sets, nd_thr);
+}
+
 // Multipoles bottom-up: every leaf at once (k_moments_leaves), then the
 // internal nodes one level at a time, deepest first (k_moments_level), so
 // that each level finds its children complete.  (A single launch in which
@@ -598,22 +643,20 @@ __global__ void __launch_bounds__(kT) k_moments_leaves(const double4 *sp64, cons
                                                        long long *nd_thr, unsigned cap, const Status *st) {
     const unsigned nn = min(st->nnodes, cap);
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x)
-        if (meta_leaf(nd_a[v].w))
-            node_moments(v, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr, cap);
+        if (meta_leaf(nd_a[v].w)) leaf_moments(v, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr);
 }
 
-__global__ void __launch_bounds__(kT) k_moments_level(int l, const double4 *sp64, const uint4 *sq,
-                                                      uint4 *nd_a, uint4 *nd_b, const uint2 *nd_r,
-                                                      double4 *nd_c, double4 *nd_q, double4 *nd_t,
-                                                      float4 *nd_f, const double *ssc, const SetInfo *sets,
-                                                      long long *nd_thr, unsigned cap, const Status *st) {
+// The internal nodes of level l, from the list the topology pass wrote.
+__global__ void __launch_bounds__(kT) k_moments_level(int l, const uint4 *sq, uint4 *nd_a, uint4 *nd_b,
+                                                      const uint2 *nd_r, double4 *nd_c, double4 *nd_q,
+                                                      double4 *nd_t, float4 *nd_f, const SetInfo *sets,
+                                                      long long *nd_thr, const unsigned *nd_int, unsigned cap,
+                                                      const Status *st) {
     unsigned b0, cnt;
     level_range(st, l, cap, b0, cnt);
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        const unsigned v = b0 + k;
-        if (!meta_leaf(nd_a[v].w))
-            node_moments(v, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr, cap);
-    }
+    const unsigned ni = min(st->lvl_int[l], cnt);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < ni; k += gridDim.x * blockDim.x)
+        internal_moments(nd_int[b0 + k], sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, sets, nd_thr, cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -761,7 +804,7 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
         nk += scan_exclusive<unsigned>(A.tmp_u32a, A.tmp_u32b, &S->lvl_count[l], nullptr,
                                        &S->lvl_count[l + 1], A.scan_tmp, st);
         k_topo_emit<<<gmax, kT, 0, st>>>(l, A.nd_bnd, A.nd_a, A.nd_b, A.nd_r, A.tmp_u32a, A.tmp_u32b,
-                                         A.cap_nodes, S);
+                                         A.nd_int, A.cap_nodes, S);
         nk++;
     }
     k_topo_finish<<<1, 1, 0, st>>>(S, A.cap_nodes);
@@ -771,8 +814,8 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
                                           A.nd_f, A.ssc, A.sets, thr, A.cap_nodes, S);
     nk++;
     for (int l = kMaxLevel - 1; l >= 0; l--, nk++)
-        k_moments_level<<<gmax, kT, 0, st>>>(l, A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q,
-                                             A.nd_t, A.nd_f, A.ssc, A.sets, thr, A.cap_nodes, S);
+        k_moments_level<<<gmax, kT, 0, st>>>(l, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,
+                                             A.nd_f, A.sets, thr, A.nd_int, A.cap_nodes, S);
     // groups
     cudaMemsetAsync(A.gflag, 0, (size_t)n * sizeof(unsigned), st);
     k_group_mark<<<gmax, kT, 0, st>>>(A.nd_a, A.nd_b, A.nd_r, A.gflag, A.n_group, S);

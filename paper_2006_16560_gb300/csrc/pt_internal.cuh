@@ -67,6 +67,7 @@ struct Status {
     double energy, mom[3];
     unsigned lvl_begin[kLevels + 1];
     unsigned lvl_count[kLevels + 1];
+    unsigned lvl_int[kLevels + 1];   // internal nodes per level (build only)
 };
 
 // Walk thresholds shared by every group.
