@@ -273,6 +273,7 @@ __global__ void k_topo_roots(const SetInfo *sets, int nsets, uint4 *nd_a, uint4 
             st->lvl_count[l] = 0;
         }
         for (int l = 0; l <= kLevels; l++) st->lvl_int[l] = 0;
+        for (int b = 0; b < kLeafBuckets; b++) st->leaf_hist[b] = st->leaf_fill[b] = 0;
     }
 }
 
@@ -631,6 +632,63 @@ __device__ __forceinline__ void internal_moments(unsigned v, const uint4 *sq, ui
                   sets, nd_thr);
 }
 
+// Leaves in order of their particle count, so that the threads of a warp in
+// the leaf multipole pass loop over leaves of one size (in node order a warp
+// runs as many float64 iterations as its largest leaf, ~3x the mean).  The
+// order within a size class is the atomics' and does not matter: each leaf
+// is still summed by one thread, particle by particle.
+__device__ __forceinline__ unsigned leaf_bucket(unsigned count) {
+    return count < (unsigned)kLeafBuckets - 1 ? count : (unsigned)kLeafBuckets - 1;
+}
+
+__global__ void __launch_bounds__(kT) k_leaf_hist(const uint4 *nd_a, const uint2 *nd_r, unsigned cap,
+                                                  Status *st) {
+    __shared__ unsigned h[kLeafBuckets];
+    for (int b = threadIdx.x; b < kLeafBuckets; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned nn = min(st->nnodes, cap);
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x)
+        if (meta_leaf(nd_a[v].w)) atomicAdd(&h[leaf_bucket(nd_r[v].y)], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kLeafBuckets; b += blockDim.x)
+        if (h[b]) atomicAdd(&st->leaf_hist[b], h[b]);
+}
+
+// list[off[b] ..] = the leaves of class b; each block round takes its
+// classes' slots with one global atomic per class.
+__global__ void __launch_bounds__(kT) k_leaf_scatter(const uint4 *nd_a, const uint2 *nd_r, unsigned cap,
+                                                     unsigned *list, Status *st) {
+    __shared__ unsigned off[kLeafBuckets], cnt[kLeafBuckets], base[kLeafBuckets];
+    if (threadIdx.x == 0) {
+        unsigned o = 0;
+        for (int b = 0; b < kLeafBuckets; b++) {
+            off[b] = o;
+            o += st->leaf_hist[b];
+        }
+    }
+    const unsigned nn = min(st->nnodes, cap);
+    for (unsigned r0 = blockIdx.x * blockDim.x; r0 < nn; r0 += gridDim.x * blockDim.x) {
+        for (int b = threadIdx.x; b < kLeafBuckets; b += blockDim.x) cnt[b] = 0;
+        __syncthreads();
+        const unsigned v = r0 + threadIdx.x;
+        const bool leaf = v < nn && meta_leaf(nd_a[v].w);
+        unsigned b = 0, local = 0;
+        if (leaf) {
+            b = leaf_bucket(nd_r[v].y);
+            local = atomicAdd(&cnt[b], 1u);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < kLeafBuckets; c += blockDim.x)
+            if (cnt[c]) base[c] = atomicAdd(&st->leaf_fill[c], cnt[c]);
+        __syncthreads();
+        if (leaf) {
+            const unsigned at = off[b] + base[b] + local;
+            if (at < cap) list[at] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // Multipoles bottom-up: every leaf at once (k_moments_leaves), then the
 // internal nodes one level at a time, deepest first (k_moments_level), so
 // that each level finds its children complete.  (A single launch in which
@@ -640,10 +698,17 @@ __global__ void __launch_bounds__(kT) k_moments_leaves(const double4 *sp64, cons
                                                        uint4 *nd_b, const uint2 *nd_r, double4 *nd_c,
                                                        double4 *nd_q, double4 *nd_t, float4 *nd_f,
                                                        const double *ssc, const SetInfo *sets,
-                                                       long long *nd_thr, unsigned cap, const Status *st) {
-    const unsigned nn = min(st->nnodes, cap);
-    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x)
-        if (meta_leaf(nd_a[v].w)) leaf_moments(v, sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr);
+                                                       long long *nd_thr, const unsigned *list, unsigned cap,
+                                                       const Status *st) {
+    __shared__ unsigned nl;
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int b = 0; b < kLeafBuckets; b++) t += st->leaf_hist[b];
+        nl = min(t, cap);
+    }
+    __syncthreads();
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x)
+        leaf_moments(list[k], sp64, sq, nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, ssc, sets, nd_thr);
 }
 
 // The internal nodes of level l, from the list the topology pass wrote.
@@ -810,8 +875,11 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     k_topo_finish<<<1, 1, 0, st>>>(S, A.cap_nodes);
     nk++;
     long long *thr = A.massdep ? A.nd_thr : nullptr;
+    k_leaf_hist<<<gmax, kT, 0, st>>>(A.nd_a, A.nd_r, A.cap_nodes, S);
+    k_leaf_scatter<<<gmax, kT, 0, st>>>(A.nd_a, A.nd_r, A.cap_nodes, A.tmp_u32a, S);
+    nk += 2;
     k_moments_leaves<<<gmax, kT, 0, st>>>(A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,
-                                          A.nd_f, A.ssc, A.sets, thr, A.cap_nodes, S);
+                                          A.nd_f, A.ssc, A.sets, thr, A.tmp_u32a, A.cap_nodes, S);
     nk++;
     for (int l = kMaxLevel - 1; l >= 0; l--, nk++)
         k_moments_level<<<gmax, kT, 0, st>>>(l, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,

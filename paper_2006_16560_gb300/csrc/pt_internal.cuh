@@ -28,6 +28,7 @@ constexpr int kBits = 21;            // grid bits per dimension
 constexpr int kMaxLevel = 21;        // deepest node level
 constexpr int kLevels = 22;          // levels 0..21
 constexpr unsigned kGrid = 1u << kBits;
+constexpr int kLeafBuckets = 64;     // leaf size classes of the multipole pass (the last: >= 63)
 
 // status flags (Status::flags)
 enum : unsigned {
@@ -68,6 +69,8 @@ struct Status {
     unsigned lvl_begin[kLevels + 1];
     unsigned lvl_count[kLevels + 1];
     unsigned lvl_int[kLevels + 1];   // internal nodes per level (build only)
+    unsigned leaf_hist[kLeafBuckets];   // leaves by particle count (build only)
+    unsigned leaf_fill[kLeafBuckets];
 };
 
 // Walk thresholds shared by every group.
