@@ -158,7 +158,7 @@ struct pt_tree {
     Buf status, sets, set_of, bmin, bmax, n_dev;
     Buf in_pos, in_mass;                                   // staging for host inputs
     Buf keys_in, vals_in, qbuf, skey, perm, sp64, spH, spL, sq;
-    Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, nd_int, tmp_a, tmp_b, lcp;
+    Buf nd_a, nd_b, nd_r, nd_c, nd_q, nd_t, nd_f, nd_bnd, nd_int, topo_bs, tmp_a, tmp_b, lcp;
     Buf gflag, gbegin, gr_r, gr_a, gr_b, gr_nc, gr_np, gr_co, gr_po, gr_nf, gr_fo, gr_ord, gpart, red_part;
     Buf cells, pp;
     Buf pairs, nb_keys, nb_keys_s, nb_vals, nb_vals_s, nb_off, nb_idx, npairs_dev;
@@ -204,7 +204,7 @@ struct pt_tree {
     void release() {
         Buf *all[] = {&status, &sets, &set_of, &bmin, &bmax, &n_dev, &in_pos, &in_mass, &keys_in,
                       &vals_in, &qbuf, &skey, &perm, &sp64, &spH, &spL, &sq, &nd_a, &nd_b, &nd_r,
-                      &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &nd_int, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
+                      &nd_c, &nd_q, &nd_t, &nd_f, &nd_bnd, &nd_int, &topo_bs, &tmp_a, &tmp_b, &lcp, &gflag, &gbegin, &gr_r, &gr_a,
                       &gr_b, &gr_nc, &gr_np, &gr_co, &gr_po, &gr_nf, &gr_fo, &gr_ord, &gpart, &red_part, &cells, &pp, &pairs,
                       &nb_keys, &nb_keys_s, &nb_vals, &nb_vals_s, &nb_off, &nb_idx, &npairs_dev,
                       &sort_k2, &sort_v2, &sort_counts, &scan_sums, &out_acc, &out_pot,
@@ -313,6 +313,7 @@ int alloc_build(pt_tree *t, unsigned n, int nsets) {
     TRY(ensure(ctx, t->nd_f, C * 48));
     TRY(ensure(ctx, t->nd_bnd, C * 32));
     TRY(ensure(ctx, t->nd_int, C * 4));
+    TRY(ensure(ctx, t->topo_bs, (size_t)sm_count() * 8 * 4));   // one per block of the topology grid
     TRY(ensure(ctx, t->lcp, N + 32));
     TRY(ensure(ctx, t->tmp_a, std::max(C, N) * 4));
     TRY(ensure(ctx, t->tmp_b, std::max(C, N) * 4));
@@ -378,6 +379,7 @@ BuildArgs build_args(pt_tree *t, const double *pos, const double *mass) {
     A.nd_f = t->nd_f.as<float4>();
     A.nd_bnd = t->nd_bnd.as<uint4>();
     A.nd_int = t->nd_int.as<unsigned>();
+    A.topo_bsum = t->topo_bs.as<unsigned>();
     A.lcp = t->lcp.as<unsigned char>();
     A.tmp_u32a = t->tmp_a.as<unsigned>();
     A.tmp_u32b = t->tmp_b.as<unsigned>();

@@ -343,20 +343,66 @@ __device__ __forceinline__ void child_bounds(const unsigned long long *skey, con
     }
 }
 
-// Number of children of every node of level l (0 for a leaf); writes meta
-// and keeps the child boundaries of split nodes for k_topo_emit.
+// Block sum and exclusive block scan (kT threads, every thread calls).
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned *sh) {
+    v = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned t = 0;
+#pragma unroll
+    for (int i = 0; i < kT / 32; i++) t += sh[i];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *sh, unsigned &total) {
+    const unsigned inc = warp_incl_scan(v);
+    const unsigned w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 31) sh[w] = inc;
+    __syncthreads();
+    unsigned before = 0, t = 0;
+#pragma unroll
+    for (int i = 0; i < kT / 32; i++) {
+        const unsigned x = sh[i];
+        before += (unsigned)i < w ? x : 0u;
+        t += x;
+    }
+    __syncthreads();
+    total = t;
+    return before + inc - v;
+}
+
+// The level's nodes in even contiguous chunks, one per block (the same
+// partition in k_topo_count and k_topo_emit: both run on the same grid).
+__device__ __forceinline__ void topo_chunk(unsigned cnt, unsigned &k0, unsigned &k1) {
+    const unsigned C = (cnt + gridDim.x - 1) / gridDim.x;
+    k0 = min(blockIdx.x * C, cnt);
+    k1 = min(k0 + C, cnt);
+}
+
+// Number of children of every node of level l (0 for a leaf); writes meta,
+// keeps the child boundaries of split nodes for k_topo_emit and the block's
+// total of children in bsum.  Nodes of up to kTopoBig particles take a
+// thread; larger ones a warp, whose lanes 1..7 bisect for the seven digit
+// boundaries at once (a thread doing them one after another waits on ~140
+// dependent loads at the top levels).
 __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long long *skey,
                                                    const unsigned char *lcp, uint4 *nd_a,
                                                    const uint2 *nd_r, unsigned *nch, uint4 *bnd,
-                                                   int n_leaf, unsigned cap, const Status *st) {
-    unsigned b0, cnt;
+                                                   unsigned *bsum, int n_leaf, unsigned cap,
+                                                   const Status *st) {
+    __shared__ unsigned sh[kT / 32];
+    unsigned b0, cnt, k0, k1;
     level_range(st, l, cap, b0, cnt);
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        unsigned v = b0 + k;
-        uint2 r = nd_r[v];
-        if (r.y > kTopoBig && (int)r.y > n_leaf && l < kMaxLevel) continue;   // k_topo_count_big's
+    topo_chunk(cnt, k0, k1);
+    const bool can_split = l < kMaxLevel;
+    for (unsigned k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const unsigned v = b0 + k;
+        const uint2 r = nd_r[v];
+        const bool split = can_split && (int)r.y > n_leaf;
+        if (split && r.y > kTopoBig) continue;            // a warp's, below
         unsigned nc = 0;
-        if ((int)r.y > n_leaf && l < kMaxLevel) {
+        if (split) {
             unsigned B[9];
             child_bounds(skey, lcp, r.x, r.y, l, B);
             for (int j = 0; j < 8; j++) nc += (B[j + 1] > B[j]) ? 1u : 0u;
@@ -368,106 +414,112 @@ __global__ void __launch_bounds__(kT) k_topo_count(int l, const unsigned long lo
         a.w = make_meta((unsigned)l, nc == 0 ? 1u : 0u, nc);
         nd_a[v] = a;
     }
-}
-
-// The same for nodes of more than kTopoBig particles, one warp per node:
-// lanes 1..7 bisect for the seven digit boundaries at once (a thread doing
-// them one after another waits on ~140 dependent loads at the top levels).
-__global__ void __launch_bounds__(kT) k_topo_count_big(int l, const unsigned long long *skey,
-                                                       uint4 *nd_a, const uint2 *nd_r, unsigned *nch,
-                                                       uint4 *bnd, int n_leaf, unsigned cap,
-                                                       const Status *st) {
-    unsigned b0, cnt;
-    level_range(st, l, cap, b0, cnt);
-    if (l >= kMaxLevel) return;
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int sh = 3 * (kBits - 1 - l);
-    for (unsigned k = warp; k < cnt; k += nwarps) {
-        const unsigned v = b0 + k;
-        const uint2 r = nd_r[v];
-        if (r.y <= kTopoBig || (int)r.y <= n_leaf) continue;   // uniform across the warp
-        const unsigned e = r.x + r.y;
-        unsigned pos = r.x;                              // lane 0: B[0]
-        if (lane >= 1 && lane < 8) {                     // first p with digit >= lane
-            unsigned lo = r.x, hi = e;
-            while (lo < hi) {
-                const unsigned mid = lo + ((hi - lo) >> 1);
-                const unsigned dg = (unsigned)(skey[mid] >> sh) & 7u;
-                if (dg >= lane) hi = mid; else lo = mid + 1;
+    if (can_split) {
+        const unsigned lane = threadIdx.x & 31;
+        const int sh3 = 3 * (kBits - 1 - l);
+        for (unsigned k = k0 + (threadIdx.x >> 5); k < k1; k += kT / 32) {
+            const unsigned v = b0 + k;
+            const uint2 r = nd_r[v];
+            if (r.y <= kTopoBig || (int)r.y <= n_leaf) continue;   // uniform across the warp
+            const unsigned e = r.x + r.y;
+            unsigned pos = r.x;                              // lane 0: B[0]
+            if (lane >= 1 && lane < 8) {                     // first p with digit >= lane
+                unsigned lo = r.x, hi = e;
+                while (lo < hi) {
+                    const unsigned mid = lo + ((hi - lo) >> 1);
+                    const unsigned dg = (unsigned)(skey[mid] >> sh3) & 7u;
+                    if (dg >= lane) hi = mid; else lo = mid + 1;
+                }
+                pos = lo;
             }
-            pos = lo;
-        }
-        unsigned B[9];
+            unsigned B[9];
 #pragma unroll
-        for (int j = 0; j < 8; j++) B[j] = __shfl_sync(0xffffffffu, pos, j);
-        B[8] = e;
-        if (lane == 0) {
-            unsigned nc = 0;
-            for (int j = 0; j < 8; j++) nc += (B[j + 1] > B[j]) ? 1u : 0u;
-            bnd[2 * v] = make_uint4(B[0], B[1], B[2], B[3]);
-            bnd[2 * v + 1] = make_uint4(B[4], B[5], B[6], B[7]);
-            nch[k] = nc;
-            uint4 a = nd_a[v];
-            a.w = make_meta((unsigned)l, nc == 0 ? 1u : 0u, nc);
-            nd_a[v] = a;
+            for (int j = 0; j < 8; j++) B[j] = __shfl_sync(0xffffffffu, pos, j);
+            B[8] = e;
+            if (lane == 0) {
+                unsigned nc = 0;
+                for (int j = 0; j < 8; j++) nc += (B[j + 1] > B[j]) ? 1u : 0u;
+                bnd[2 * v] = make_uint4(B[0], B[1], B[2], B[3]);
+                bnd[2 * v + 1] = make_uint4(B[4], B[5], B[6], B[7]);
+                nch[k] = nc;
+                uint4 a = nd_a[v];
+                a.w = make_meta((unsigned)l, nc == 0 ? 1u : 0u, nc);
+                nd_a[v] = a;
+            }
         }
     }
+    __syncthreads();                  // the block's nch entries are in place
+    unsigned s = 0;
+    for (unsigned k = k0 + threadIdx.x; k < k1; k += blockDim.x) s += nch[k];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = s;
 }
 
-// Creates the children of level l's split nodes (at next + choff) and lists
-// the split nodes themselves, in any order, in nd_int from lvl_begin[l] on:
-// the multipole pass then takes one internal node per thread with no leaves
-// in between (float64 instructions cost the same for a warp with few lanes).
+// Creates the children of level l's split nodes and lists the split nodes
+// themselves, in any order, in nd_int from lvl_begin[l] on (the multipole
+// pass then takes one internal node per thread with no leaves in between:
+// float64 instructions cost the same for a warp with few lanes).  A block's
+// children follow those of the blocks before it (the sum of their bsum) in
+// the order of its chunk (a block scan), so level l+1 is in key order.
 __global__ void __launch_bounds__(kT) k_topo_emit(int l, const uint4 *bnd,
                                                   uint4 *nd_a, uint4 *nd_b, uint2 *nd_r,
-                                                  const unsigned *nch, const unsigned *choff,
+                                                  const unsigned *nch, const unsigned *bsum,
                                                   unsigned *nd_int, unsigned cap, Status *st) {
-    unsigned b0, cnt;
+    __shared__ unsigned sh[kT / 32];
+    unsigned b0, cnt, k0, k1;
     level_range(st, l, cap, b0, cnt);
+    topo_chunk(cnt, k0, k1);
     const unsigned next = st->lvl_begin[l] + st->lvl_count[l];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned s = 0;
+    for (unsigned i = threadIdx.x; i < blockIdx.x; i += blockDim.x) s += bsum[i];
+    const unsigned base = block_sum(s, sh);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         // only this thread touches level l+1's entries; the kernels that
         // read them are later launches
+        const unsigned total = base + bsum[blockIdx.x];
         st->lvl_begin[l + 1] = next;
-        unsigned long long end = (unsigned long long)next + st->lvl_count[l + 1];
-        if (end > cap) {
+        unsigned c = total;
+        if ((unsigned long long)next + total > cap) {
             atomicOr(&st->flags, kErrNodeCap);
-            st->lvl_count[l + 1] = next < cap ? cap - next : 0u;
+            c = next < cap ? cap - next : 0u;
         }
+        st->lvl_count[l + 1] = c;
     }
-    // grid-stride rounds over whole warps, so that the list slots are taken
-    // with one atomic per warp
     const unsigned lane = threadIdx.x & 31;
-    for (unsigned k0 = blockIdx.x * blockDim.x; k0 < cnt; k0 += gridDim.x * blockDim.x) {
-        const unsigned k = k0 + threadIdx.x;
-        const bool split = k < cnt && nch[k] != 0;
-        const unsigned m = __ballot_sync(0xffffffffu, split);
+    unsigned carry = 0;
+    for (unsigned r0 = k0; r0 < k1; r0 += blockDim.x) {      // uniform across the block
+        const unsigned k = r0 + threadIdx.x;
+        const unsigned nc = k < k1 ? nch[k] : 0u;
+        unsigned tot;
+        const unsigned excl = block_excl_scan(nc, sh, tot);
+        const unsigned m = __ballot_sync(0xffffffffu, nc != 0);
         unsigned slot = 0;
-        if (m) {
+        if (m) {                      // list slots: one atomic per warp
             if (lane == 0) slot = atomicAdd(&st->lvl_int[l], (unsigned)__popc(m));
-            slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
+            slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & lanemask_lt());
         }
-        if (!split) continue;
-        unsigned v = b0 + k;
-        if (b0 + slot < cap) nd_int[b0 + slot] = v;
-        uint2 r = nd_r[v];
-        const uint4 b1 = bnd[2 * v], b2 = bnd[2 * v + 1];
-        const unsigned B[9] = {b1.x, b1.y, b1.z, b1.w, b2.x, b2.y, b2.z, b2.w, r.x + r.y};
-        unsigned first = next + choff[k], c = first;
-        for (int j = 0; j < 8; j++) {
-            if (B[j + 1] == B[j]) continue;
-            if (c < cap) {
-                nd_r[c] = make_uint2(B[j], B[j + 1] - B[j]);
-                nd_a[c] = make_uint4(0, 0, 0, make_meta((unsigned)l + 1, 1, 0));
-                nd_b[c] = make_uint4(0, 0, 0, 0);
+        if (nc) {
+            const unsigned v = b0 + k;
+            if (b0 + slot < cap) nd_int[b0 + slot] = v;
+            const uint2 r = nd_r[v];
+            const uint4 b1 = bnd[2 * v], b2 = bnd[2 * v + 1];
+            const unsigned B[9] = {b1.x, b1.y, b1.z, b1.w, b2.x, b2.y, b2.z, b2.w, r.x + r.y};
+            const unsigned first = next + base + carry + excl;
+            unsigned c = first;
+            for (int j = 0; j < 8; j++) {
+                if (B[j + 1] == B[j]) continue;
+                if (c < cap) {
+                    nd_r[c] = make_uint2(B[j], B[j + 1] - B[j]);
+                    nd_a[c] = make_uint4(0, 0, 0, make_meta((unsigned)l + 1, 1, 0));
+                    nd_b[c] = make_uint4(0, 0, 0, 0);
+                }
+                c++;
             }
-            c++;
+            uint4 bb = nd_b[v];
+            bb.w = first;
+            nd_b[v] = bb;
         }
-        uint4 bb = nd_b[v];
-        bb.w = first;
-        nd_b[v] = bb;
+        carry += tot;
     }
 }
 
@@ -861,14 +913,10 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     nk += 2;
     for (int l = 0; l <= kMaxLevel; l++) {
         k_topo_count<<<gmax, kT, 0, st>>>(l, A.skey, A.lcp, A.nd_a, A.nd_r, A.tmp_u32a, A.nd_bnd,
-                                          A.n_leaf, A.cap_nodes, S);
-        k_topo_count_big<<<gmax, kT, 0, st>>>(l, A.skey, A.nd_a, A.nd_r, A.tmp_u32a, A.nd_bnd,
-                                              A.n_leaf, A.cap_nodes, S);
-        nk += 2;
+                                          A.topo_bsum, A.n_leaf, A.cap_nodes, S);
+        nk++;
         if (l == kMaxLevel) break;
-        nk += scan_exclusive<unsigned>(A.tmp_u32a, A.tmp_u32b, &S->lvl_count[l], nullptr,
-                                       &S->lvl_count[l + 1], A.scan_tmp, st);
-        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.nd_bnd, A.nd_a, A.nd_b, A.nd_r, A.tmp_u32a, A.tmp_u32b,
+        k_topo_emit<<<gmax, kT, 0, st>>>(l, A.nd_bnd, A.nd_a, A.nd_b, A.nd_r, A.tmp_u32a, A.topo_bsum,
                                          A.nd_int, A.cap_nodes, S);
         nk++;
     }

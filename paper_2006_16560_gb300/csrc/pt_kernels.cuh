@@ -38,6 +38,7 @@ struct BuildArgs {
     float4 *nd_f;
     uint4 *nd_bnd;                   // 2 per node: child boundaries of split nodes (build only)
     unsigned *nd_int;                // per level from lvl_begin: its internal nodes (build only)
+    unsigned *topo_bsum;             // children counted per block of the topology grid (build only)
     unsigned char *lcp;              // n + 32 bytes: shared key digits of neighbours (build only)
     unsigned *tmp_u32a, *tmp_u32b;   // max(cap_nodes, n) each
     // groups
