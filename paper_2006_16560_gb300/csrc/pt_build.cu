@@ -9,7 +9,7 @@
 namespace pt {
 
 constexpr int kT = 256;
-constexpr unsigned kTopoBig = 256;    // nodes above this size get a warp in the topology count
+constexpr unsigned kTopoBig = 16;     // nodes above this size get a warp in the topology count
 
 // ---------------------------------------------------------------------------
 // Sets (clusters) and the root box
@@ -293,53 +293,42 @@ __global__ void __launch_bounds__(kT) k_lcp(const unsigned long long *skey, cons
     }
 }
 
-// Boundaries of the 8 key digits of level l+1 inside [b, b+c): B[k] is the
-// first position whose digit is >= k.  Nodes of up to 32 particles find
-// their children's starts by scanning lcp 16 bytes at a time; larger ones
-// bisect the keys (measured: the bisections win above ~32).
+// Boundaries of the 8 key digits of level l+1 inside [b, b+c), c <= kTopoBig:
+// B[k] is the first position whose digit is >= k, found by scanning lcp 16
+// bytes at a time for the children's starts.  (Larger nodes take a warp whose
+// lanes bisect the keys for the seven boundaries at once: measured faster
+// than one thread per node for every node above 16 particles.)
 __device__ __forceinline__ void child_bounds(const unsigned long long *skey, const unsigned char *lcp,
                                              unsigned b, unsigned c, int l, unsigned B[9]) {
     const int sh = 3 * (kBits - 1 - l);
     const unsigned e = b + c;
     B[0] = b;
     B[8] = e;
-    if (c <= 32) {
 #pragma unroll
-        for (unsigned k = 1; k < 8; k++) B[k] = e;
-        // children start in increasing digit order: a start with digit dg is
-        // the first position for every k <= dg not yet placed
-        auto place = [&](unsigned pos) {
-            const unsigned dg = (unsigned)(skey[pos] >> sh) & 7u;
+    for (unsigned k = 1; k < 8; k++) B[k] = e;
+    // children start in increasing digit order: a start with digit dg is
+    // the first position for every k <= dg not yet placed
+    auto place = [&](unsigned pos) {
+        const unsigned dg = (unsigned)(skey[pos] >> sh) & 7u;
 #pragma unroll
-            for (unsigned k = 1; k < 8; k++)
-                if (k <= dg && B[k] == e) B[k] = pos;
-        };
-        place(b);
-        const unsigned pat = (unsigned)l * 0x01010101u;
-        for (unsigned q = (b + 1) & ~15u; q < e; q += 16) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(lcp + q);
-            const unsigned words[4] = {w.x, w.y, w.z, w.w};
+        for (unsigned k = 1; k < 8; k++)
+            if (k <= dg && B[k] == e) B[k] = pos;
+    };
+    place(b);
+    const unsigned pat = (unsigned)l * 0x01010101u;
+    for (unsigned q = (b + 1) & ~15u; q < e; q += 16) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(lcp + q);
+        const unsigned words[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
-                unsigned eq = __vcmpeq4(words[t], pat);          // 0xff in each equal byte
-                while (eq) {
-                    const int bit = __ffs(eq) - 1;
-                    eq &= ~(0xffu << bit);
-                    const unsigned pos = q + 4u * t + (unsigned)(bit >> 3);
-                    if (pos > b && pos < e) place(pos);
-                }
+        for (int t = 0; t < 4; t++) {
+            unsigned eq = __vcmpeq4(words[t], pat);          // 0xff in each equal byte
+            while (eq) {
+                const int bit = __ffs(eq) - 1;
+                eq &= ~(0xffu << bit);
+                const unsigned pos = q + 4u * t + (unsigned)(bit >> 3);
+                if (pos > b && pos < e) place(pos);
             }
         }
-        return;
-    }
-    for (unsigned k = 1; k < 8; k++) {
-        unsigned lo = B[k - 1], hi = b + c;      // first p >= lo with digit >= k
-        while (lo < hi) {
-            unsigned mid = lo + ((hi - lo) >> 1);
-            unsigned dg = (unsigned)(skey[mid] >> sh) & 7u;
-            if (dg >= k) hi = mid; else lo = mid + 1;
-        }
-        B[k] = lo;
     }
 }
 
@@ -929,8 +918,12 @@ int build_launch(const BuildArgs &A, cudaStream_t st) {
     k_moments_leaves<<<gmax, kT, 0, st>>>(A.sp64, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,
                                           A.nd_f, A.ssc, A.sets, thr, A.tmp_u32a, A.cap_nodes, S);
     nk++;
+    // two blocks per SM: the kernel's 120 registers allow no more resident
+    // ones, and a level's internal nodes are few (the larger grid ran in
+    // waves of idle blocks)
+    const int mgrid = sm_count() * 2;
     for (int l = kMaxLevel - 1; l >= 0; l--, nk++)
-        k_moments_level<<<gmax, kT, 0, st>>>(l, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,
+        k_moments_level<<<mgrid, kT, 0, st>>>(l, A.sq, A.nd_a, A.nd_b, A.nd_r, A.nd_c, A.nd_q, A.nd_t,
                                              A.nd_f, A.sets, thr, A.nd_int, A.cap_nodes, S);
     // groups
     cudaMemsetAsync(A.gflag, 0, (size_t)n * sizeof(unsigned), st);
