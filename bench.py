@@ -596,7 +596,7 @@ def main():
                     help="targets of the direct-sum reference at N = 2^20 (tree-vs-direct error)")
     ap.add_argument("--tvd-sample-10m", type=int, default=1000,
                     help="targets of the direct-sum reference at N = 10^7")
-    ap.add_argument("--only-leg", choices=["orbit", "tidal"], default=None,
+    ap.add_argument("--only-leg", choices=["orbit", "tidal", "batch"], default=None,
                     help="run one widened leg alone on the headline set and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -611,7 +611,10 @@ def main():
         from paper_2006_16560_gb300 import inputs
         d = inputs.plummer(args.n, SEED, masses="kroupa")
         ctx = B.Context(local)
-        leg = orbit_leg(ctx, d, args.steps) if args.only_leg == "orbit" else tidal_leg(ctx, d, args.steps)
+        if args.only_leg == "batch":
+            leg = batch_leg(ctx, args.steps)
+        else:
+            leg = orbit_leg(ctx, d, args.steps) if args.only_leg == "orbit" else tidal_leg(ctx, d, args.steps)
         print(json.dumps({"leg": args.only_leg, **leg}), flush=True)
         ctx.close()
         return

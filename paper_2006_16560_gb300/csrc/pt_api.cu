@@ -863,6 +863,10 @@ int enqueue_batch(pt_tree *t, cudaStream_t st, bool host_io, bool want_nb) {
     WalkArgs W = walk_args(t);
     nk += walk_launch(W, 2, st);              // one pass (arrays sized before the capture)
     ForceArgs F = force_args(t, t->d_acc.as<double>(), t->d_pot.as<double>(), want_nb);
+    // this step's group count is on the device: a grid sized from the last
+    // step's, with head room (groups beyond it are taken from a counter)
+    const unsigned long long hint = t->h.ngroups ? t->h.ngroups + t->h.ngroups / 8 + 64 : 0;
+    F.direct_groups = (unsigned)std::min<unsigned long long>(hint, 0x7fffffffull);
     nk += force_launch(F, t->prm.precision, st);
     nk += force_reduce_launch(F, st);
     if (want_nb) {

@@ -724,12 +724,14 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
     const unsigned ng = A.st->ngroups;
     for (unsigned it = 0;; it++) {
         unsigned gi;
-        if (A.direct_groups) {                   // one group per CTA, in group order
-            if (it > 0 || blockIdx.x >= ng) break;
+        if (A.direct_groups && it == 0) {        // the CTA's own group, in group order
+            if (blockIdx.x >= ng) break;
             gi = blockIdx.x;
         } else {
+            // persistent CTAs, or groups beyond a grid sized from a count hint
+            if (A.direct_groups >= ng) break;
             __syncthreads();
-            if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+            if (threadIdx.x == 0) gsh = A.direct_groups + (unsigned)atomicAdd(&A.st->work[2], 1ull);
             __syncthreads();
             gi = gsh;
             if (gi >= ng) break;
@@ -975,12 +977,13 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     const unsigned ng = A.st->ngroups;
     for (unsigned it = 0;; it++) {
         unsigned g;
-        if (A.direct_groups) {                   // one group per CTA
-            if (it > 0 || blockIdx.x >= ng) break;
+        if (A.direct_groups && it == 0) {        // the CTA's own group
+            if (blockIdx.x >= ng) break;
             g = blockIdx.x;
         } else {
+            if (A.direct_groups >= ng) break;    // see the mixed kernel
             __syncthreads();
-            if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+            if (threadIdx.x == 0) gsh = A.direct_groups + (unsigned)atomicAdd(&A.st->work[2], 1ull);
             __syncthreads();
             g = gsh;
             if (g >= ng) break;

@@ -107,9 +107,12 @@ struct ForceArgs {
     int want_nb;
     uint2 *pairs;                    // (sorted i, sorted j)
     unsigned long long pair_cap;
-    // groups of the launch when it is one CTA per group (known to the host
-    // after the build), 0 for a persistent launch that takes groups from an
-    // atomic counter (graph-captured batches, where the count is on the device)
+    // CTAs of the launch, each first taking the group of its own index: the
+    // group count when the host knows it (after the build), else a hint (a
+    // batch's count from its previous step, with head room: the count is on
+    // the device when a step is enqueued or captured); groups beyond the grid
+    // go to CTAs that take them from an atomic counter.  0: a persistent
+    // launch taking every group from the counter.
     unsigned direct_groups;
     double4 *gpart;                  // per group: sum m phi / 2, sum m a
     double4 *red_e;                  // per reduction block: partial sums of gpart

@@ -176,3 +176,31 @@ def test_autotune_picks_a_candidate_and_caches(ctx):
         a, _, _ = T.force(0.4, c["r_in"], c["r_out"], order=2)
         e = rel_err(bt.acc[k].cpu().numpy(), a)
         assert np.percentile(e, 99) <= 1e-6
+
+
+def test_group_count_beyond_the_hint(ctx):
+    """A batch step sizes its force grid from the previous step's group count
+    (with head room); when a step has many more groups than that, the groups
+    beyond the grid are taken from a counter.  Here the previous step has
+    every cluster's particles coincident (one depth-capped leaf and one group
+    per cluster), the next one Plummer clusters: the results equal single-set
+    runs bit for bit, uncaptured and replayed from a graph captured on the
+    coincident step."""
+    cl = _clusters(700, [600, 1500, 3000])
+    prm = _params(B.PT_MIXED)
+    same = [dict(c, pos=np.zeros_like(c["pos"]) + 0.25) for c in cl]
+    singles = []
+    for c in cl:
+        p1 = B.Params(**{**prm.__dict__, "r_in": c["r_in"], "r_out": c["r_out"]})
+        g = run_gpu(ctx, c["pos"], c["mass"], p1, neighbours=False)
+        singles.append((g["acc"], g["pot"]))
+        g["tree"].free()
+    for flags in (0, B.PT_BATCH_GRAPH):
+        rc0, _, st0 = _run_batch(ctx, same, prm, flags=flags, nb=False)
+        assert rc0 == B.PT_OK, B.pt_last_error(ctx.h)
+        assert st0["groups"] == len(cl)
+        rc, res, st = _run_batch(ctx, cl, prm, flags=flags, nb=False)
+        assert rc == B.PT_OK, B.pt_last_error(ctx.h)
+        assert st["groups"] > len(cl) + len(cl) // 8 + 64    # more than the grid of the hint
+        for (a, p), r in zip(singles, res):
+            assert np.array_equal(r["acc"], a) and np.array_equal(r["pot"], p)

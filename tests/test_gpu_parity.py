@@ -470,3 +470,34 @@ def test_build_graph_replay_sees_new_data(ctx):
         assert np.array_equal(acc.cpu().numpy(), ref["acc"]), step
         assert np.array_equal(pot.cpu().numpy(), ref["pot"]), step
     t.free()
+
+
+@pytest.mark.parametrize("n_leaf", [1, 2, 16, 17, 32, 64])
+def test_topology_every_leaf_size(ctx, n_leaf):
+    """Leaf sizes on both sides of the topology kernel's thread / warp split
+    (nodes above 16 particles take a warp): the node set, boxes, moments,
+    groups and lists equal the oracle's, and the numbering is breadth-first
+    in key order with every internal node's children contiguous on the next
+    level, tiling its particle range in order.  Binaries from n_leaf 2 on (a
+    tight pair is then a leaf, summed from its particles); at n_leaf 1 a pair
+    that a cell face splits is combined from two child records whose COMs
+    carry the rounding of absolute float64 positions (~1e-16 against a
+    separation down to ~1e-9), which the quadrupole tolerance of the node
+    comparison does not cover, so n_leaf 1 takes a Plummer set."""
+    d = inputs.plummer_binaries(2048, 40 + n_leaf) if n_leaf > 1 else inputs.plummer(4096, 41)
+    p = c1_params(order=2, n_leaf=n_leaf, n_group=64)
+    g = run_gpu(ctx, d["pos"], d["mass"], p)
+    T = oracle.Tree(d["pos"], d["mass"], p.n_leaf, p.n_group)
+    check_structure(g, T, p)
+    nd = g["tree"].nodes()
+    lv, b, c = nd["level"], nd["begin"], nd["count"]
+    assert np.all(np.diff(lv) >= 0)
+    same = np.diff(lv) == 0
+    assert np.all(np.diff(b)[same] > 0)
+    for v in np.nonzero(nd["leaf"] == 0)[0]:
+        f, k = nd["first_child"][v], nd["nchild"][v]
+        assert 1 <= k <= 8
+        ch = np.arange(f, f + k)
+        assert np.all(lv[ch] == lv[v] + 1)
+        assert b[ch[0]] == b[v] and b[ch[-1]] + c[ch[-1]] == b[v] + c[v]
+        assert np.all(b[ch[1:]] == b[ch[:-1]] + c[ch[:-1]])
