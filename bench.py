@@ -541,8 +541,19 @@ def cpu_oracle_sample(pos, mass, nsample, seed=11):
     inter = st[0] + st[1]
     full_time = (t1 - t0) + (t2 - t1) * n / nsample
     full_inter = inter * n / nsample
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = _omp_threads()
     return full_inter / full_time, t2 - t0, threads, inter
+
+
+def _omp_threads(n=None):
+    """The OpenMP thread count of the oracle's runtime (libgomp, loaded with
+    the oracle library); with n, sets it and returns the previous count."""
+    import ctypes
+    g = ctypes.CDLL("libgomp.so.1")
+    prev = g.omp_get_max_threads()
+    if n is not None:
+        g.omp_set_num_threads(int(n))
+    return prev
 
 
 def reference_main(args, rank, world):
@@ -582,6 +593,8 @@ def main():
     ap.add_argument("--particles", "--n", dest="n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-sample", type=int, default=262144,
                     help="oracle targets per CPU sample (about 10 s on 16 host cores)")
+    ap.add_argument("--cpu-sample-1core", type=int, default=4096,
+                    help="oracle targets of the one-core CPU sample (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="skip the FP64, e2e and batch legs (profiling)")
@@ -783,6 +796,14 @@ def main():
                                 "sample": f"oracle tree build over all {n} particles + oracle tree force "
                                           f"on {args.cpu_sample} random targets ({si} interactions, "
                                           f"{secs:.1f} s), extrapolated to all targets"}
+        if args.cpu_sample_1core > 0:
+            prev = _omp_threads(1)
+            v1, secs1, _, si1 = cpu_oracle_sample(d["pos"], d["mass"], args.cpu_sample_1core, seed=12)
+            _omp_threads(prev)
+            line["cpu_baseline"]["one_core"] = {
+                "value": v1, "unit": "interactions/s",
+                "sample": f"the same on one core: {args.cpu_sample_1core} targets ({si1} interactions, "
+                          f"{secs1:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
