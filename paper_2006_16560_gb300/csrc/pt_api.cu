@@ -867,6 +867,7 @@ int enqueue_batch(pt_tree *t, cudaStream_t st, bool host_io, bool want_nb) {
     // step's, with head room (groups beyond it are taken from a counter)
     const unsigned long long hint = t->h.ngroups ? t->h.ngroups + t->h.ngroups / 8 + 64 : 0;
     F.direct_groups = (unsigned)std::min<unsigned long long>(hint, 0x7fffffffull);
+    F.count_hint = 1;
     nk += force_launch(F, t->prm.precision, st);
     nk += force_reduce_launch(F, st);
     if (want_nb) {

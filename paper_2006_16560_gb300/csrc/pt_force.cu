@@ -706,7 +706,7 @@ __device__ unsigned mixed_pass(const ForceArgs &A, unsigned g, const uint2 gr, u
     return 96;
 }
 
-template <int ORDER, bool NB, bool MD>
+template <int ORDER, bool NB, bool MD, bool TAIL>
 __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(ForceArgs A) {
     __shared__ ulonglong2 sP[kFWarps][5][kJ / 2];
     __shared__ float2 sF[kFWarps][3][4][32];
@@ -724,17 +724,31 @@ __global__ void __launch_bounds__(kFThreads, PT_FORCE_MIN_BLOCKS) k_force_mixed(
     const unsigned ng = A.st->ngroups;
     for (unsigned it = 0;; it++) {
         unsigned gi;
-        if (A.direct_groups && it == 0) {        // the CTA's own group, in group order
-            if (blockIdx.x >= ng) break;
-            gi = blockIdx.x;
+        if constexpr (!TAIL) {
+            if (A.direct_groups) {               // one group per CTA, in group order
+                if (it > 0 || blockIdx.x >= ng) break;
+                gi = blockIdx.x;
+            } else {                             // persistent CTAs
+                __syncthreads();
+                if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+                __syncthreads();
+                gi = gsh;
+                if (gi >= ng) break;
+            }
         } else {
-            // persistent CTAs, or groups beyond a grid sized from a count hint
-            if (A.direct_groups >= ng) break;
-            __syncthreads();
-            if (threadIdx.x == 0) gsh = A.direct_groups + (unsigned)atomicAdd(&A.st->work[2], 1ull);
-            __syncthreads();
-            gi = gsh;
-            if (gi >= ng) break;
+            // the CTA's own group first, then the groups beyond a grid sized
+            // from a count hint (a separate instantiation: the loop that may
+            // run again compiled the single-set kernel 2.4% slower)
+            if (it == 0 && A.direct_groups && blockIdx.x < ng) {
+                gi = blockIdx.x;
+            } else {
+                if (A.direct_groups >= ng) break;
+                __syncthreads();
+                if (threadIdx.x == 0) gsh = A.direct_groups + (unsigned)atomicAdd(&A.st->work[2], 1ull);
+                __syncthreads();
+                gi = gsh;
+                if (gi >= ng) break;
+            }
         }
         const unsigned g = A.gr_ord[gi];
         const uint2 gr = A.gr_r[g];
@@ -961,7 +975,7 @@ __device__ void group_pass_d(const ForceArgs &A, unsigned g, const uint2 gr, uns
         for (int c = 0; c < 4; c++) red[w][lane + 32 * s][c] = (s < NI) ? pa[s][c] : 0.0;
 }
 
-template <int ORDER, bool NB, bool MD>
+template <int ORDER, bool NB, bool MD, bool TAIL>
 __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     __shared__ double4 sA[kFWarps][kJD];
     __shared__ double4 sB[kFWarps][kJD];
@@ -977,16 +991,28 @@ __global__ void __launch_bounds__(kFThreads) k_force_fp64(ForceArgs A) {
     const unsigned ng = A.st->ngroups;
     for (unsigned it = 0;; it++) {
         unsigned g;
-        if (A.direct_groups && it == 0) {        // the CTA's own group
-            if (blockIdx.x >= ng) break;
-            g = blockIdx.x;
-        } else {
-            if (A.direct_groups >= ng) break;    // see the mixed kernel
-            __syncthreads();
-            if (threadIdx.x == 0) gsh = A.direct_groups + (unsigned)atomicAdd(&A.st->work[2], 1ull);
-            __syncthreads();
-            g = gsh;
-            if (g >= ng) break;
+        if constexpr (!TAIL) {
+            if (A.direct_groups) {               // one group per CTA
+                if (it > 0 || blockIdx.x >= ng) break;
+                g = blockIdx.x;
+            } else {
+                __syncthreads();
+                if (threadIdx.x == 0) gsh = (unsigned)atomicAdd(&A.st->work[2], 1ull);
+                __syncthreads();
+                g = gsh;
+                if (g >= ng) break;
+            }
+        } else {                                 // see the mixed kernel
+            if (it == 0 && A.direct_groups && blockIdx.x < ng) {
+                g = blockIdx.x;
+            } else {
+                if (A.direct_groups >= ng) break;
+                __syncthreads();
+                if (threadIdx.x == 0) gsh = A.direct_groups + (unsigned)atomicAdd(&A.st->work[2], 1ull);
+                __syncthreads();
+                g = gsh;
+                if (g >= ng) break;
+            }
         }
         const uint2 gr = A.gr_r[g];
         const Chg C = make_chg(A.sets[A.gr_a[g].w]);
@@ -1165,27 +1191,33 @@ __global__ void __launch_bounds__(1024) k_group_order(const uint2 *gr_r, unsigne
 // group by group, so kernels of other streams -- other batches of a server --
 // get SMs within a group's time instead of waiting for the whole launch),
 // else a persistent grid that takes groups from an atomic counter.
-int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
-    const int blocks = A.direct_groups ? (int)A.direct_groups : sm_count() * 8;
+template <bool TAIL>
+static void force_launch_t(const ForceArgs &A, int precision, int blocks, cudaStream_t st) {
     const bool md = A.massdep != 0;
     if (precision == 1) {
-        k_group_order<<<1, 1024, 0, st>>>(A.gr_r, A.gr_ord, A.st);
         if (A.order == 2) {
-            if (md) k_force_mixed<2, true, true><<<blocks, kFThreads, 0, st>>>(A);
-            else k_force_mixed<2, true, false><<<blocks, kFThreads, 0, st>>>(A);
+            if (md) k_force_mixed<2, true, true, TAIL><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_mixed<2, true, false, TAIL><<<blocks, kFThreads, 0, st>>>(A);
         } else {
-            if (md) k_force_mixed<0, true, true><<<blocks, kFThreads, 0, st>>>(A);
-            else k_force_mixed<0, true, false><<<blocks, kFThreads, 0, st>>>(A);
+            if (md) k_force_mixed<0, true, true, TAIL><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_mixed<0, true, false, TAIL><<<blocks, kFThreads, 0, st>>>(A);
         }
     } else {
         if (A.order == 2) {
-            if (md) k_force_fp64<2, true, true><<<blocks, kFThreads, 0, st>>>(A);
-            else k_force_fp64<2, true, false><<<blocks, kFThreads, 0, st>>>(A);
+            if (md) k_force_fp64<2, true, true, TAIL><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_fp64<2, true, false, TAIL><<<blocks, kFThreads, 0, st>>>(A);
         } else {
-            if (md) k_force_fp64<0, true, true><<<blocks, kFThreads, 0, st>>>(A);
-            else k_force_fp64<0, true, false><<<blocks, kFThreads, 0, st>>>(A);
+            if (md) k_force_fp64<0, true, true, TAIL><<<blocks, kFThreads, 0, st>>>(A);
+            else k_force_fp64<0, true, false, TAIL><<<blocks, kFThreads, 0, st>>>(A);
         }
     }
+}
+
+int force_launch(const ForceArgs &A, int precision, cudaStream_t st) {
+    const int blocks = A.direct_groups ? (int)A.direct_groups : sm_count() * 8;
+    if (precision == 1) k_group_order<<<1, 1024, 0, st>>>(A.gr_r, A.gr_ord, A.st);
+    if (A.count_hint && A.direct_groups) force_launch_t<true>(A, precision, blocks, st);
+    else force_launch_t<false>(A, precision, blocks, st);
     return precision == 1 ? 2 : 1;
 }
 

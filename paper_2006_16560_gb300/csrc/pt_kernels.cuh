@@ -114,6 +114,7 @@ struct ForceArgs {
     // go to CTAs that take them from an atomic counter.  0: a persistent
     // launch taking every group from the counter.
     unsigned direct_groups;
+    unsigned count_hint;             // 1: direct_groups is a hint (take groups beyond it)
     double4 *gpart;                  // per group: sum m phi / 2, sum m a
     double4 *red_e;                  // per reduction block: partial sums of gpart
     unsigned long long *red_c;       // per reduction block: cell and PP interaction counts
