@@ -69,3 +69,21 @@ def test_reference_arm_under_torchrun():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_thread_count():
+    """The one-core CPU sample sets the oracle's OpenMP runtime to one thread,
+    reports it, and the caller restores the previous count; the sample counts
+    the interactions it timed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2006_16560_gb300 import inputs
+    d = inputs.plummer(4096, 3)
+    v_all, _, thr_all, si_all = bench.cpu_oracle_sample(d["pos"], d["mass"], 256)
+    prev = bench._omp_threads(1)
+    try:
+        v1, _, thr1, si1 = bench.cpu_oracle_sample(d["pos"], d["mass"], 256)
+    finally:
+        bench._omp_threads(prev)
+    assert thr1 == 1 and bench._omp_threads() == prev == thr_all
+    assert v1 > 0 and v_all > 0 and si1 == si_all > 0       # same sample (seed), same work
