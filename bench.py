@@ -473,6 +473,31 @@ def c2_10m_leg(ctx, steps, flush):
     return rec, d, {"fp64": f64, "mixed": mx}
 
 
+def size_sweep_leg(ctx, steps, flush, sizes=(1 << 14, 1 << 16, 1 << 18, 1 << 22)):
+    """The headline workload (Kroupa Plummer, seed 2, the same tree
+    parameters, FP32-mixed, neighbour lists on) at other particle counts:
+    ms per step and interactions/s, timed like the headline."""
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+    rows = []
+    for n in sizes:
+        d = inputs.plummer(n, SEED, masses="kroupa")
+        pos, mass, out = _device_set(d, n)
+        holder = [None]
+        run_steps(ctx, holder, pos, mass, params(B.PT_MIXED), out, 2, flush)
+        times, st = run_steps(ctx, holder, pos, mass, params(B.PT_MIXED), out, steps, flush)
+        holder[0].free()
+        ms = statistics.mean(times)
+        inter = st["cell_interactions"] + st["pp_interactions"]
+        rows.append({"n": n, "ms_per_step": ms, "interactions_per_s": inter / (ms * 1e-3),
+                     "particles_per_s": n / (ms * 1e-3), "interactions_per_step": inter,
+                     "stage_ms": {"build": st["ms_build"], "walk": st["ms_walk"],
+                                  "force_kernel": st["ms_force"]}})
+    return {"workload": "Plummer N=2^14..2^22, Kroupa IMF, seed 2; quadrupole tree theta=0.3, n_leaf=16, "
+                        "n_group=64, r_out=0.003, r_in=0.0003; FP32-mixed, neighbour lists on",
+            "rows": rows}
+
+
 def binaries_leg(ctx, steps, flush):
     """Precision variant: N = 10^6 with every star in a primordial binary
     (500,000 pairs, a log-uniform in 0.005-50 AU, thermal e; seed 4) on the
@@ -593,6 +618,7 @@ def main():
     ap.add_argument("--particles", "--n", dest="n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-sample", type=int, default=262144,
                     help="oracle targets per CPU sample (about 10 s on 16 host cores)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 2^14..2^22 size sweep")
     ap.add_argument("--cpu-sample-1core", type=int, default=4096,
                     help="oracle targets of the one-core CPU sample (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -783,6 +809,8 @@ def main():
         line["c2_10m"], d10, big = c2_10m_leg(ctx, max(3, args.steps // 4), flush)
     if not args.no_binaries and not args.only_mixed:
         line["binaries_1m"] = binaries_leg(ctx, max(3, args.steps // 4), flush)
+    if not args.no_sweep and not args.only_mixed:
+        line["size_sweep"] = size_sweep_leg(ctx, max(3, args.steps // 2), flush)
     if rank == 0 and not args.no_cpu_baseline:
         # CPU oracle on the host cores: the direct-sum reference of the
         # tree-vs-direct error on sampled targets, then the timed baseline

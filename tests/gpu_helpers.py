@@ -7,11 +7,13 @@ import numpy as np
 from paper_2006_16560_gb300 import binding as B
 
 
-def run_gpu(ctx, pos, mass, params: B.Params, neighbours=True, device_buffers=True):
+def run_gpu(ctx, pos, mass, params: B.Params, neighbours=True, device_buffers=True, repeat=1):
     """Build + force through pt_tree_build / pt_longrange_force.
 
     Returns a dict with acc, pot (input order), CSR neighbours, stats and the
-    Tree (still alive, for introspection)."""
+    Tree (still alive, for introspection).  repeat > 1 calls the force that
+    many times on the tree (a tree's first walk sizes its lists in two passes;
+    later ones run in one pass into arrays sized from the last walk)."""
     import torch
     n = len(mass)
     if device_buffers:
@@ -23,11 +25,13 @@ def run_gpu(ctx, pos, mass, params: B.Params, neighbours=True, device_buffers=Tr
         cap = max(8 * n, 1024)
         nb_off = torch.empty((n + 1,), dtype=torch.int64, device="cuda") if neighbours else None
         nb_idx = torch.empty((cap,), dtype=torch.int32, device="cuda") if neighbours else None
-        total, st, rc = tree.force(acc, pot, nb_off, nb_idx, cap if neighbours else 0,
-                                   allow_capacity_error=True)
-        if rc == B.PT_ERR_CAPACITY:          # retry with the reported size
-            nb_idx = torch.empty((total,), dtype=torch.int32, device="cuda")
-            total, st, rc = tree.force(acc, pot, nb_off, nb_idx, total)
+        for _ in range(repeat):
+            total, st, rc = tree.force(acc, pot, nb_off, nb_idx, cap if neighbours else 0,
+                                       allow_capacity_error=True)
+            if rc == B.PT_ERR_CAPACITY:          # retry with the reported size
+                nb_idx = torch.empty((total,), dtype=torch.int32, device="cuda")
+                cap = total
+                total, st, rc = tree.force(acc, pot, nb_off, nb_idx, total)
         out = {"acc": acc.cpu().numpy(), "pot": pot.cpu().numpy()}
         if neighbours:
             out["nb_off"] = nb_off.cpu().numpy()

@@ -56,8 +56,13 @@ def check_structure(g, T, p):
     np.testing.assert_allclose(gn["mass"], on["mass"][order], rtol=1e-12, atol=0)
     scale = np.abs(on["com"]).max()
     np.testing.assert_allclose(gn["com"], on["com"][order], rtol=0, atol=1e-13 * scale)
+    # Q = 3T - tr(T) I, with T of size M * extent^2: float64 rounding of that
+    # size is more than 1e-9 |Q| for a nearly isotropic node (|Q| << |T|)
     qscale = np.abs(on["quad"][order]).max(axis=1, keepdims=True) + 1e-300
-    assert np.all(np.abs(gn["quad"] - on["quad"][order]) <= 1e-9 * qscale)
+    cell = tree.info()[1][3] / 2.0**21
+    ext2 = (((on["qmax"] - on["qmin"] + 1) * cell) ** 2).sum(axis=1)
+    tscale = (on["mass"] * ext2)[order][:, None]
+    assert np.all(np.abs(gn["quad"] - on["quad"][order]) <= 1e-9 * qscale + 1e-13 * tscale)
     gg, og = tree.groups(), T.groups()
     for k in ("begin", "count", "qmin", "qmax"):
         assert np.array_equal(gg[k], og[k]), k
@@ -501,3 +506,49 @@ def test_topology_every_leaf_size(ctx, n_leaf):
         assert np.all(lv[ch] == lv[v] + 1)
         assert b[ch[0]] == b[v] and b[ch[-1]] + c[ch[-1]] == b[v] + c[v]
         assert np.all(b[ch[1:]] == b[ch[:-1]] + c[ch[:-1]])
+
+
+def _later_walk_case(kind):
+    if kind == "plummer":
+        d = inputs.plummer(4096, 1)
+        return d["pos"], d["mass"], c1_params(order=2)
+    if kind == "mono":
+        d = inputs.plummer(4096, 5)
+        return d["pos"], d["mass"], c1_params(order=0, n_leaf=4, n_group=16)
+    if kind == "binaries":
+        d = inputs.plummer_binaries(2048, 44)
+        return d["pos"], d["mass"], c1_params(order=2, n_leaf=16, n_group=64)
+    if kind == "groups24":
+        d = inputs.plummer(6000, 324, masses="kroupa")
+        return d["pos"], d["mass"], c1_params(order=2, n_leaf=8, n_group=24)
+    r_out = 0.0016                                    # wide sparse groups
+    pos = inputs.wide_sparse_groups(r_out, 15, 3, 2)
+    mass = np.full(len(pos), 1.0 / len(pos))
+    return pos, mass, c1_params(order=2, n_leaf=4, n_group=64, r_out=r_out, r_in=0.1 * r_out, theta=0.5)
+
+
+@pytest.mark.parametrize("kind", ["plummer", "mono", "binaries", "groups24", "wide"])
+def test_later_walks_equal_the_oracle(ctx, kind):
+    """A tree's later walks run in one pass into arrays sized from the last
+    walk: on Plummer, monopole, binary, 24-target-group and wide sparse-group
+    sets every group's cell and PP lists equal the oracle's as sets, the
+    float64 forces match the oracle tree, the neighbour lists brute force, and
+    the lists equal those of the tree's first (two-pass) walk."""
+    pos, mass, p = _later_walk_case(kind)
+    T = oracle.Tree(pos, mass, p.n_leaf, p.n_group)
+    g1 = run_gpu(ctx, pos, mass, p)                  # first walk: two passes
+    st1 = g1["stats"]
+    co1, cells1, po1, pp1 = g1["tree"].lists(st1["cell_list_total"], st1["pp_list_total"])
+    g = run_gpu(ctx, pos, mass, p, repeat=3)         # later walks: one pass
+    check_structure(g, T, p)
+    st = g["stats"]
+    co, cells, po, pp = g["tree"].lists(st["cell_list_total"], st["pp_list_total"])
+    for k in range(len(co) - 1):
+        assert np.array_equal(np.sort(cells[co[k]:co[k + 1]]), np.sort(cells1[co1[k]:co1[k + 1]]))
+        assert np.array_equal(np.sort(pp[po[k]:po[k + 1]]), np.sort(pp1[po1[k]:po1[k + 1]]))
+    a, phi, _ = T.force(p.theta, p.r_in, p.r_out, order=p.order)
+    assert rel_err(g["acc"], a).max() <= FP64_TOL
+    assert (np.abs(g["pot"] - phi) / np.abs(phi)).max() <= FP64_TOL
+    check_neighbours(g, pos, p.r_out)
+    for k in ("cell_interactions", "pp_interactions"):
+        assert st[k] == st1[k]
