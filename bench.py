@@ -412,7 +412,7 @@ def tidal_leg(ctx, d, steps, n_bin=65536, order=3):
         a_meas = acc[n:].reshape(n_bin, 1 + P, 3)
         ctx.check(B.pt_tidal_tensor(ctx.h, order, n_bin, B._ptr(a_meas), B._ptr(dc), B._ptr(T)), "fit")
         return st.as_dict()
-    for _ in range(3):                     # the tree's build graph is captured on its third build
+    for _ in range(3):                     # the tree's build graph is captured on its second build
         step()
     times = []
     for _ in range(max(3, steps)):

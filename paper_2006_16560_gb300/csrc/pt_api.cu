@@ -412,7 +412,7 @@ int read_status(pt_tree *t) {
 }
 
 // Build over t->n particles in t->nsets sets; pos/mass are device pointers.
-// Enqueues the build between events ev[0] and ev[1]. Its ~145 short kernels
+// Enqueues the build between events ev[0] and ev[1]. Its ~105 short kernels
 // are bound by the host's launch rate, so a build whose arguments equal the
 // previous one's is captured into a CUDA graph (on the context's private
 // stream) and replayed from then on.
