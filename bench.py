@@ -484,6 +484,56 @@ def c2_10m_leg(ctx, steps, flush):
     return rec, d, {"fp64": f64, "mixed": mx}
 
 
+def n1mkb_leg(ctx, steps, flush):
+    """The paper's N1mkb model (Sec. 7.1.1, Table 2): 10^6 stars, all in
+    5 x 10^5 primordial binaries of the Kroupa (1995) period distribution
+    (Eq. 39; seed 12), r_out,ref = 0.00199039, r_out/r_in = 10, theta 0.3,
+    with mass-dependent changeover radii (Eq. 12, factors computed on the
+    device).  Mixed and FP64 step times, mixed vs FP64 error, and the fraction
+    of binaries closer than their pair radius r_out * max(s_i, s_j) whose
+    members are each other's neighbours (every one of them must be)."""
+    from paper_2006_16560_gb300 import binding as B
+    from paper_2006_16560_gb300 import inputs
+    d = inputs.kroupa95_binaries(500_000, 12)
+    n = len(d["mass"])
+    r_out = 0.199039e-2
+    kw = dict(theta=0.3, r_in=0.1 * r_out, r_out=r_out, n_leaf=16, n_group=64, order=2, mass_dependent=1)
+    pm, p64 = B.Params(precision=B.PT_MIXED, **kw), B.Params(precision=B.PT_FP64, **kw)
+    pos, mass, out = _device_set(d, n)
+    holder = [None]
+    run_steps(ctx, holder, pos, mass, pm, out, 2, flush)
+    times, st = run_steps(ctx, holder, pos, mass, pm, out, steps, flush)
+    mx = (out[0].cpu().numpy().copy(), out[1].cpu().numpy().copy())
+    off, idx = out[2].cpu().numpy(), out[3][: int(st["neighbours"])].cpu().numpy()
+    run_steps(ctx, holder, pos, mass, p64, out, 1, flush)
+    t64, st64 = run_steps(ctx, holder, pos, mass, p64, out, 2, flush)
+    f64 = (out[0].cpu().numpy(), out[1].cpu().numpy())
+    holder[0].free()
+    # pairs closer than their pair radius (Eq. 12 factors, with a margin for
+    # the device's cube root) must be neighbours of each other
+    m = d["mass"]
+    sfac = np.cbrt(np.maximum(1.0, m / m.mean()))
+    rij = r_out * np.maximum(sfac[0::2], sfac[1::2])
+    sep = np.linalg.norm(d["pos"][0::2] - d["pos"][1::2], axis=1)
+    must = np.nonzero(sep < 0.999 * rij)[0]
+    rows = np.repeat(np.arange(n), np.diff(off))
+    have = np.zeros(n, dtype=bool)
+    have[rows[idx == (rows ^ 1)]] = True
+    ms, ms64 = statistics.mean(times), statistics.mean(t64)
+    inter = st["cell_interactions"] + st["pp_interactions"]
+    return {"workload": "N1mkb: 5x10^5 Kroupa (1995) primordial binaries (10^6 stars, seed 12), r_out,ref = "
+                        "0.00199039, r_in = r_out/10, theta 0.3, n_leaf 16, n_group 64, quadrupole, mass-dependent "
+                        "radii (Eq. 12)",
+            "value": inter / (ms * 1e-3), "unit": "interactions/s", "ms_per_step": ms,
+            "stage_ms": {"build": st["ms_build"], "walk": st["ms_walk"], "force_kernel": st["ms_force"]},
+            "fp64_ms_per_step": ms64, "speedup_mixed_vs_fp64": ms64 / ms,
+            "interactions_per_step": inter, "pp_changeover_interactions": st["pp_changeover_interactions"],
+            "neighbours": int(st["neighbours"]), "neighbours_fp64": int(st64["neighbours"]),
+            "binaries_within_pair_radius": int(len(must)),
+            "companions_found": float(np.mean(have[2 * must] & have[2 * must + 1])) if len(must) else None,
+            "mixed_error_vs_fp64": _errors(mx[0], mx[1], f64[0], f64[1])}
+
+
 def size_sweep_leg(ctx, steps, flush, sizes=(1 << 14, 1 << 16, 1 << 18, 1 << 22)):
     """The headline workload (Kroupa Plummer, seed 2, the same tree
     parameters, FP32-mixed, neighbour lists on) at other particle counts:
@@ -630,6 +680,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=262144,
                     help="oracle targets per CPU sample (about 10 s on 16 host cores)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 2^14..2^22 size sweep")
+    ap.add_argument("--no-n1mkb", action="store_true",
+                    help="skip the N1mkb leg (Kroupa 1995 binaries, mass-dependent radii)")
     ap.add_argument("--cpu-sample-1core", type=int, default=4096,
                     help="oracle targets of the one-core CPU sample (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -820,6 +872,8 @@ def main():
         line["c2_10m"], d10, big = c2_10m_leg(ctx, max(3, args.steps // 4), flush)
     if not args.no_binaries and not args.only_mixed:
         line["binaries_1m"] = binaries_leg(ctx, max(3, args.steps // 4), flush)
+    if not args.no_n1mkb and not args.only_mixed:
+        line["n1mkb"] = n1mkb_leg(ctx, max(3, args.steps // 4), flush)
     if not args.no_sweep and not args.only_mixed:
         line["size_sweep"] = size_sweep_leg(ctx, max(3, args.steps // 2), flush)
     if rank == 0 and not args.no_cpu_baseline:
